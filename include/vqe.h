@@ -1,0 +1,230 @@
+/*
+ * vqe.h - C ABI of the GB300 state-vector VQE library (libvqe).
+ *
+ * The library evaluates the variational energy of Eq. 1,
+ *     E(theta) = <HF| U(theta)^dagger H U(theta) |HF>,
+ * and its gradient dE/dtheta_k, where
+ *   - H is the qubit Hamiltonian: a real-weighted sum of Pauli strings, as the
+ *     Jordan-Wigner mapping of Eq. 2 produces (Sec. 2.1.1);
+ *   - U(theta) = U_M ... U_1, U_k = exp(theta_k (T_k - T_k^dagger)), one
+ *     rotation per single or double excitation of the UCCSD ansatz (Sec. 2.1.2);
+ *   - |HF> is the Hartree-Fock reference bitstring of Eq. 1.
+ *
+ * Conventions shared by every call:
+ *   - Bit q of a basis index is qubit q; qubit q is spin orbital q (spatial
+ *     orbital q/2, alpha when q is even, beta when odd).
+ *   - A Pauli term is (x_mask, z_mask, coef): X where only x has bit q, Z where
+ *     only z has it, Y where both do, P|k> = i^{|x&z|} (-1)^{|k&z|} |k ^ x>.
+ *   - Excitations are int32 quadruples: {i, a, -1, -1} is the single
+ *     T = a+_a a_i; {i, j, a, b} is the double T = a+_a a+_b a_j a_i. Ladder
+ *     operators carry the sign (-1)^(occupied orbitals below their index).
+ *   - theta_k is the full rotation angle (no factor 1/2).
+ *   - n_qubits is 1..32.
+ *
+ * Memory ownership: create calls copy their host inputs and own device copies
+ * of the derived tables until the matching destroy call. theta, energies,
+ * gradients and the workspace are caller-owned device memory; the compute
+ * calls never allocate, so they can be enqueued on any stream. Every compute
+ * call is asynchronous on the given stream (a cudaStream_t; NULL is the legacy
+ * default stream) except where noted.
+ *
+ * Errors: every int-returning call returns VQE_OK (0) or a VQE_ERR_* code and
+ * sets a thread-local message readable with vqe_last_error(). Invalid
+ * arguments are rejected before anything is enqueued.
+ */
+#ifndef VQE_H
+#define VQE_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+enum {
+  VQE_OK = 0,
+  VQE_ERR_INVALID_ARG = 1,  /* bad size, mask bit >= n, index clash, NaN ... */
+  VQE_ERR_WORKSPACE = 2,    /* workspace pointer NULL/misaligned or too small */
+  VQE_ERR_CUDA = 3,         /* a CUDA runtime call failed (message has details) */
+  VQE_ERR_TIMEOUT = 4,      /* a bounded device wait gave up (status word set) */
+  VQE_ERR_NOT_REAL = 5,     /* a Pauli coefficient of the mapped H is not real */
+  VQE_ERR_UNSUPPORTED = 6,  /* valid request outside what this build implements */
+  VQE_ERR_NO_MEMORY = 7     /* create-time allocation failed */
+};
+
+typedef struct vqe_hamiltonian_s* vqe_hamiltonian_t;
+typedef struct vqe_ansatz_s* vqe_ansatz_t;
+typedef struct vqe_batch_s* vqe_batch_t;
+typedef void* vqe_stream_t;
+
+/* Library version as 10000*major + 100*minor + patch. */
+int vqe_version(void);
+
+/*
+ * Process-wide switches, for verification only (0 = normal operation):
+ *   VQE_FLAG_FORCE_COMPLEX   evaluate E and g with complex amplitudes and full
+ *                            complex coefficients instead of the real path;
+ *   VQE_FLAG_FORCE_STREAMING never use the shared-memory-resident kernel.
+ * Returns the previous flags. Not thread-safe against concurrent compute calls.
+ */
+enum { VQE_FLAG_FORCE_COMPLEX = 1, VQE_FLAG_FORCE_STREAMING = 2 };
+int vqe_set_flags(int flags);
+
+/* Message of the last failed call on this thread ("" if none). */
+const char* vqe_last_error(void);
+
+/*
+ * Jordan-Wigner mapping of Eq. 2 (Sec. 2.1.1), host only, synchronous.
+ *   H = c0 + sum_{pq,s} h[p*n_s+q] a+_{ps} a_{qs}
+ *          + 1/2 sum_{pqrs,s,t} eri[((p*n_s+q)*n_s+r)*n_s+s] a+_{ps} a+_{rt} a_{st} a_{qs}
+ * with eri in chemists' order (pq|rs) and spin orbital (p, s) = qubit 2p+s.
+ * Terms with equal masks are merged; |coef| < drop_tol are dropped. Output is
+ * sorted by (x_mask, z_mask). If capacity is smaller than the term count,
+ * nothing is written to the arrays, *n_out receives the count and the call
+ * returns VQE_ERR_INVALID_ARG (query with capacity 0 and NULL arrays).
+ * Returns VQE_ERR_NOT_REAL if the mapped coefficients are not real (the
+ * integrals were not symmetric).
+ */
+int vqe_jordan_wigner(int n_spatial, const double* h, const double* eri, double c0,
+                      double drop_tol, int64_t capacity, uint64_t* x_out,
+                      uint64_t* z_out, double* c_out, int64_t* n_out);
+
+/*
+ * Qubit Hamiltonian from host arrays of n_terms Pauli terms (Eq. 1's H after
+ * the mapping of Sec. 2.1.1). Equal (x, z) are merged, |coef| < drop_tol
+ * dropped, and terms grouped by x_mask. Each group's terms are folded into
+ * per-pattern coefficient tables: for the pattern u of the source index on
+ * the group's X bits (up to 4 bits), and the terms' Z bits outside them.
+ * The Hamiltonian is flagged real when every folded coefficient
+ * c * i^{|x&z|} is real; then all amplitudes stay real and kernels skip the
+ * (identically zero) imaginary arithmetic. Synchronous; allocates device memory.
+ */
+int vqe_create_hamiltonian(int n_qubits, int64_t n_terms, const uint64_t* x_masks,
+                           const uint64_t* z_masks, const double* coefs,
+                           double drop_tol, vqe_hamiltonian_t* out);
+
+/* Counts after merging/dropping; is_real as described above. Any out may be NULL. */
+int vqe_hamiltonian_info(vqe_hamiltonian_t h, int* n_qubits, int64_t* n_terms,
+                         int64_t* n_groups, int* is_real);
+
+void vqe_destroy_hamiltonian(vqe_hamiltonian_t h);
+
+/*
+ * Ansatz U(theta) (Sec. 2.1.2) on n_qubits from the reference bitstring
+ * hf_bits and n_exc excitations (host array of 4*n_exc int32, see above).
+ * Indices must lie in [0, n_qubits) and be distinct within an excitation.
+ * The reachable sector is fixed here: popcount(hf_bits) electrons, and, when
+ * every excitation conserves the alpha/beta counts, the reference's
+ * (N_alpha, N_beta). Amplitudes outside it are exactly zero for every theta,
+ * and no energy or gradient depends on them, so kernels touch only the
+ * sector. Synchronous; allocates device memory.
+ */
+int vqe_create_ansatz(int n_qubits, uint64_t hf_bits, int32_t n_exc,
+                      const int32_t* excitations, vqe_ansatz_t* out);
+
+/* Sector dimension, parameter count and number of (gate, amplitude-pair) units. */
+int vqe_ansatz_info(vqe_ansatz_t a, int* n_qubits, int32_t* n_params,
+                    int64_t* sector_dim, int64_t* n_pairs);
+
+void vqe_destroy_ansatz(vqe_ansatz_t a);
+
+/*
+ * Bytes of device workspace a call needs for this pair, by mode:
+ *   VQE_WS_ENERGY (vqe_energy), VQE_WS_GRAD (vqe_energy_grad, vqe_state),
+ *   VQE_WS_COMPLEX (vqe_apply_hamiltonian, or any call while
+ *   VQE_FLAG_FORCE_COMPLEX is set); modes may be OR-ed.
+ * It holds two 2^n state vectors (|psi> or |phi>, and |lambda>), of which only
+ * the sector's entries are touched, plus reduction partials. The workspace
+ * must be 256-byte aligned.
+ * The first call for a (Hamiltonian, sector) pair builds that pair's
+ * connectivity table (synchronous, allocates); call it before any stream
+ * capture. Returns 0 and sets the error message on failure.
+ */
+enum { VQE_WS_ENERGY = 0, VQE_WS_GRAD = 1, VQE_WS_COMPLEX = 2 };
+size_t vqe_workspace_bytes(vqe_hamiltonian_t h, vqe_ansatz_t a, int mode);
+
+/*
+ * E(theta) of Eq. 1 into energy_dev[0]. theta_dev: n_params device doubles.
+ */
+int vqe_energy(vqe_hamiltonian_t h, vqe_ansatz_t a, const double* theta_dev,
+               double* energy_dev, void* workspace, size_t workspace_bytes,
+               vqe_stream_t stream);
+
+/*
+ * E(theta) and grad_dev[k] = dE/dtheta_k by one forward sweep, one H|psi>, and
+ * one reverse (adjoint) sweep that un-applies each gate to both |phi> and
+ * |lambda> = H|psi> while reducing g_k = 2 Re <lambda| T_k - T_k^dagger |phi>.
+ */
+int vqe_energy_grad(vqe_hamiltonian_t h, vqe_ansatz_t a, const double* theta_dev,
+                    double* energy_dev, double* grad_dev, void* workspace,
+                    size_t workspace_bytes, vqe_stream_t stream);
+
+/*
+ * psi(theta) = U(theta)|HF> as a full 2^n complex128 vector (interleaved
+ * re, im) in psi_out_dev; every entry, inside the sector or not, is written.
+ */
+int vqe_state(vqe_ansatz_t a, vqe_hamiltonian_t h, const double* theta_dev,
+              double* psi_out_dev, void* workspace, size_t workspace_bytes,
+              vqe_stream_t stream);
+
+/*
+ * lambda = H psi restricted to the ansatz's sector, for a caller-given full
+ * 2^n complex128 vector psi_dev that vanishes outside the sector. lam_out_dev
+ * (2^n complex128) receives lambda on the sector and 0 elsewhere;
+ * energy_dev[0] receives Re <psi|H|psi>.
+ */
+int vqe_apply_hamiltonian(vqe_hamiltonian_t h, vqe_ansatz_t a, const double* psi_dev,
+                          double* lam_out_dev, double* energy_dev, void* workspace,
+                          size_t workspace_bytes, vqe_stream_t stream);
+
+/*
+ * A batch of independent instances (the paper runs hundreds of independent
+ * simulation jobs over geometries and molecules, abstract and Sec. 4),
+ * evaluated by one launch for instances that fit shared memory, and by
+ * per-instance streaming passes otherwise. hams/ansatze: n_inst handles (they may repeat) that must
+ * outlive the batch. Synchronous; allocates the batch's device descriptors.
+ */
+int vqe_create_batch(int n_inst, const vqe_hamiltonian_t* hams,
+                     const vqe_ansatz_t* ansatze, vqe_batch_t* out);
+
+/* Largest n_params over the batch (the minimum leading dimension of theta). */
+int32_t vqe_batch_max_params(vqe_batch_t b);
+
+size_t vqe_batch_workspace_bytes(vqe_batch_t b, int with_grad);
+
+/*
+ * Energies (and gradients when grads_dev != NULL) of every instance.
+ * theta_dev: row i holds instance i's n_params angles at theta_dev + i*ld_theta.
+ * grads_dev: row i at grads_dev + i*ld_grad. energies_dev: n_inst doubles.
+ */
+int vqe_batch_energy_grad(vqe_batch_t b, const double* theta_dev, int64_t ld_theta,
+                          double* energies_dev, double* grads_dev, int64_t ld_grad,
+                          void* workspace, size_t workspace_bytes, vqe_stream_t stream);
+
+/*
+ * Same as vqe_batch_energy_grad with HOST arrays: copies theta host->device,
+ * runs, copies energies and gradients device->host, and synchronises the
+ * stream before returning. Uses the workspace for the staged copies too
+ * (vqe_batch_host_workspace_bytes).
+ */
+size_t vqe_batch_host_workspace_bytes(vqe_batch_t b, int with_grad);
+int vqe_batch_energy_grad_host(vqe_batch_t b, const double* theta_host, int64_t ld_theta,
+                               double* energies_host, double* grads_host, int64_t ld_grad,
+                               void* workspace, size_t workspace_bytes, vqe_stream_t stream);
+
+void vqe_destroy_batch(vqe_batch_t b);
+
+/*
+ * Algorithmic work of one energy(+gradient) evaluation, counted exactly on the
+ * host from the tables: FP64 flops (an FMA counts 2) and the bytes of state
+ * vector a streaming implementation must move. Used for roofline reports.
+ */
+int vqe_work_estimate(vqe_hamiltonian_t h, vqe_ansatz_t a, int with_grad,
+                      double* fp64_flops, double* state_bytes);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* VQE_H */

@@ -1,0 +1,258 @@
+"""Python binding of libvqe: argument marshalling only.
+
+Every computation runs in the CUDA library; torch supplies device memory and
+the current stream. Names follow include/vqe.h.
+"""
+import ctypes
+
+import numpy as np
+import torch
+
+from . import _native
+
+VQE_WS_ENERGY, VQE_WS_GRAD, VQE_WS_COMPLEX = 0, 1, 2
+VQE_FLAG_FORCE_COMPLEX, VQE_FLAG_FORCE_STREAMING = 1, 2
+
+
+class VQEError(RuntimeError):
+    def __init__(self, code, msg):
+        super().__init__(f"libvqe error {code}: {msg}")
+        self.code = code
+
+
+def _lib():
+    return _native.load()
+
+
+def _check(rc):
+    if rc != 0:
+        raise VQEError(rc, _lib().vqe_last_error().decode(errors="replace"))
+
+
+def _ptr(a):
+    if a is None:
+        return None
+    if isinstance(a, torch.Tensor):
+        return ctypes.c_void_p(a.data_ptr())
+    return a.ctypes.data_as(ctypes.c_void_p)
+
+
+def _stream(stream=None):
+    s = stream if stream is not None else torch.cuda.current_stream()
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def set_flags(flags: int) -> int:
+    return _lib().vqe_set_flags(int(flags))
+
+
+def jordan_wigner(n_spatial, h, eri, c0=0.0, drop_tol=1e-14):
+    """Pauli sum (x_masks, z_masks, coefs) of Eq. 2's Hamiltonian (library's own mapping)."""
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    eri = np.ascontiguousarray(eri, dtype=np.float64)
+    n = ctypes.c_int64(0)
+    lib = _lib()
+    rc = lib.vqe_jordan_wigner(int(n_spatial), _ptr(h), _ptr(eri), float(c0), float(drop_tol), 0,
+                               None, None, None, ctypes.byref(n))
+    if rc not in (0, 1):
+        _check(rc)
+    cnt = n.value
+    xs = np.zeros(cnt, dtype=np.uint64)
+    zs = np.zeros(cnt, dtype=np.uint64)
+    cs = np.zeros(cnt, dtype=np.float64)
+    _check(lib.vqe_jordan_wigner(int(n_spatial), _ptr(h), _ptr(eri), float(c0), float(drop_tol), cnt,
+                                 _ptr(xs), _ptr(zs), _ptr(cs), ctypes.byref(n)))
+    return xs, zs, cs
+
+
+class Hamiltonian:
+    """Qubit Hamiltonian handle (vqe_create_hamiltonian)."""
+
+    def __init__(self, n_qubits, x_masks, z_masks, coefs, drop_tol=0.0):
+        xs = np.ascontiguousarray(x_masks, dtype=np.uint64)
+        zs = np.ascontiguousarray(z_masks, dtype=np.uint64)
+        cs = np.ascontiguousarray(coefs, dtype=np.float64)
+        if not (len(xs) == len(zs) == len(cs)):
+            raise ValueError("mask and coefficient arrays differ in length")
+        self._lib = _lib()
+        h = ctypes.c_void_p()
+        _check(self._lib.vqe_create_hamiltonian(int(n_qubits), len(xs), _ptr(xs), _ptr(zs), _ptr(cs),
+                                                float(drop_tol), ctypes.byref(h)))
+        self.handle = h
+        self.n_qubits = int(n_qubits)
+
+    @classmethod
+    def from_integrals(cls, n_spatial, h, eri, c0=0.0, drop_tol=1e-14):
+        xs, zs, cs = jordan_wigner(n_spatial, h, eri, c0, drop_tol)
+        return cls(2 * n_spatial, xs, zs, cs, drop_tol)
+
+    @classmethod
+    def from_problem(cls, problem, drop_tol=1e-14):
+        return cls.from_integrals(problem.n_spatial, problem.h, problem.eri, problem.c0, drop_tol)
+
+    def info(self):
+        n = ctypes.c_int()
+        t = ctypes.c_int64()
+        g = ctypes.c_int64()
+        r = ctypes.c_int()
+        _check(self._lib.vqe_hamiltonian_info(self.handle, ctypes.byref(n), ctypes.byref(t), ctypes.byref(g),
+                                              ctypes.byref(r)))
+        return {"n_qubits": n.value, "n_terms": t.value, "n_groups": g.value, "is_real": bool(r.value)}
+
+    def __del__(self):
+        h = getattr(self, "handle", None)
+        if h is not None and h.value:
+            self._lib.vqe_destroy_hamiltonian(h)
+            self.handle = None
+
+
+class Ansatz:
+    """UCCSD-type ansatz handle (vqe_create_ansatz)."""
+
+    def __init__(self, n_qubits, hf_bits, excitations):
+        exc = np.ascontiguousarray(np.asarray(excitations, dtype=np.int32).reshape(-1, 4))
+        self._lib = _lib()
+        a = ctypes.c_void_p()
+        _check(self._lib.vqe_create_ansatz(int(n_qubits), int(hf_bits), len(exc), _ptr(exc), ctypes.byref(a)))
+        self.handle = a
+        self.n_qubits = int(n_qubits)
+        self.n_params = len(exc)
+        self.excitations = exc
+
+    def info(self):
+        n = ctypes.c_int()
+        m = ctypes.c_int32()
+        d = ctypes.c_int64()
+        p = ctypes.c_int64()
+        _check(self._lib.vqe_ansatz_info(self.handle, ctypes.byref(n), ctypes.byref(m), ctypes.byref(d),
+                                         ctypes.byref(p)))
+        return {"n_qubits": n.value, "n_params": m.value, "sector_dim": d.value, "n_pairs": p.value}
+
+    def __del__(self):
+        a = getattr(self, "handle", None)
+        if a is not None and a.value:
+            self._lib.vqe_destroy_ansatz(a)
+            self.handle = None
+
+
+def workspace_bytes(h: Hamiltonian, a: Ansatz, mode=VQE_WS_GRAD) -> int:
+    nb = _lib().vqe_workspace_bytes(h.handle, a.handle, int(mode))
+    if nb == 0:
+        msg = _lib().vqe_last_error().decode(errors="replace")
+        if msg:
+            raise VQEError(-1, msg)
+    return int(nb)
+
+
+def alloc_workspace(nbytes, device="cuda"):
+    return torch.empty(max(int(nbytes), 256), dtype=torch.uint8, device=device)
+
+
+def _as_theta(theta, device):
+    if not isinstance(theta, torch.Tensor):
+        theta = torch.as_tensor(np.asarray(theta, dtype=np.float64))
+    return theta.to(device=device, dtype=torch.float64).contiguous()
+
+
+def energy(h, a, theta, workspace=None, stream=None, device="cuda"):
+    theta = _as_theta(theta, device)
+    if workspace is None:
+        workspace = alloc_workspace(workspace_bytes(h, a, VQE_WS_ENERGY), theta.device)
+    e = torch.empty(1, dtype=torch.float64, device=theta.device)
+    _check(_lib().vqe_energy(h.handle, a.handle, _ptr(theta), _ptr(e), _ptr(workspace), workspace.numel(),
+                             _stream(stream)))
+    return e[0]
+
+
+def energy_grad(h, a, theta, workspace=None, stream=None, device="cuda"):
+    theta = _as_theta(theta, device)
+    if workspace is None:
+        workspace = alloc_workspace(workspace_bytes(h, a, VQE_WS_GRAD), theta.device)
+    e = torch.empty(1, dtype=torch.float64, device=theta.device)
+    g = torch.empty(max(a.n_params, 1), dtype=torch.float64, device=theta.device)
+    _check(_lib().vqe_energy_grad(h.handle, a.handle, _ptr(theta), _ptr(e), _ptr(g), _ptr(workspace),
+                                  workspace.numel(), _stream(stream)))
+    return e[0], g[:a.n_params]
+
+
+def state(a, h, theta, workspace=None, stream=None, device="cuda"):
+    """psi(theta) as a full 2^n complex128 vector."""
+    theta = _as_theta(theta, device)
+    if workspace is None:
+        workspace = alloc_workspace(workspace_bytes(h, a, VQE_WS_GRAD), theta.device)
+    out = torch.empty(2 * (1 << a.n_qubits), dtype=torch.float64, device=theta.device)
+    _check(_lib().vqe_state(a.handle, h.handle, _ptr(theta), _ptr(out), _ptr(workspace), workspace.numel(),
+                            _stream(stream)))
+    return torch.view_as_complex(out.view(-1, 2))
+
+
+def apply_hamiltonian(h, a, psi, workspace=None, stream=None):
+    """(H psi restricted to the ansatz sector, Re <psi|H|psi>) for a complex128 psi."""
+    psi = psi.to(dtype=torch.complex128).contiguous()
+    if workspace is None:
+        workspace = alloc_workspace(workspace_bytes(h, a, VQE_WS_COMPLEX), psi.device)
+    lam = torch.empty_like(psi)
+    e = torch.empty(1, dtype=torch.float64, device=psi.device)
+    _check(_lib().vqe_apply_hamiltonian(h.handle, a.handle, _ptr(torch.view_as_real(psi)),
+                                        _ptr(torch.view_as_real(lam)), _ptr(e), _ptr(workspace),
+                                        workspace.numel(), _stream(stream)))
+    return lam, e[0]
+
+
+def work_estimate(h, a, with_grad=True):
+    f = ctypes.c_double()
+    b = ctypes.c_double()
+    _check(_lib().vqe_work_estimate(h.handle, a.handle, int(bool(with_grad)), ctypes.byref(f), ctypes.byref(b)))
+    return f.value, b.value
+
+
+class Batch:
+    """Independent instances evaluated together (vqe_create_batch)."""
+
+    def __init__(self, hams, ansatze):
+        if len(hams) != len(ansatze):
+            raise ValueError("hams and ansatze differ in length")
+        self._lib = _lib()
+        self.hams = list(hams)
+        self.ansatze = list(ansatze)
+        hs = (ctypes.c_void_p * len(hams))(*[h.handle.value for h in hams])
+        As = (ctypes.c_void_p * len(ansatze))(*[a.handle.value for a in ansatze])
+        b = ctypes.c_void_p()
+        _check(self._lib.vqe_create_batch(len(hams), hs, As, ctypes.byref(b)))
+        self.handle = b
+        self.n_inst = len(hams)
+        self.max_params = int(self._lib.vqe_batch_max_params(b))
+
+    def workspace_bytes(self, with_grad=True):
+        return int(self._lib.vqe_batch_workspace_bytes(self.handle, int(bool(with_grad))))
+
+    def host_workspace_bytes(self, with_grad=True):
+        return int(self._lib.vqe_batch_host_workspace_bytes(self.handle, int(bool(with_grad))))
+
+    def energy_grad(self, theta, energies=None, grads=None, workspace=None, stream=None, with_grad=True):
+        """theta: (n_inst, ld) float64 CUDA tensor. Returns (energies, grads)."""
+        assert theta.dtype == torch.float64 and theta.is_cuda and theta.is_contiguous()
+        dev = theta.device
+        if energies is None:
+            energies = torch.empty(self.n_inst, dtype=torch.float64, device=dev)
+        if with_grad and grads is None:
+            grads = torch.empty(self.n_inst, max(self.max_params, 1), dtype=torch.float64, device=dev)
+        if workspace is None:
+            workspace = alloc_workspace(self.workspace_bytes(with_grad), dev)
+        _check(self._lib.vqe_batch_energy_grad(
+            self.handle, _ptr(theta), theta.shape[1], _ptr(energies), _ptr(grads) if with_grad else None,
+            grads.shape[1] if with_grad else 0, _ptr(workspace), workspace.numel(), _stream(stream)))
+        return energies, grads
+
+    def energy_grad_host(self, theta_host, energies_host, grads_host, workspace, stream=None):
+        """Host arrays in and out (copies inside the call; synchronises the stream)."""
+        _check(self._lib.vqe_batch_energy_grad_host(
+            self.handle, _ptr(theta_host), theta_host.shape[1], _ptr(energies_host), _ptr(grads_host),
+            grads_host.shape[1] if grads_host is not None else 0, _ptr(workspace), workspace.numel(),
+            _stream(stream)))
+
+    def __del__(self):
+        b = getattr(self, "handle", None)
+        if b is not None and b.value:
+            self._lib.vqe_destroy_batch(b)
+            self.handle = None

@@ -1,0 +1,969 @@
+// Host side of libvqe: argument validation, the Jordan-Wigner mapping of Eq. 2,
+// X-mask grouping and folding of the Pauli sum, excitation records, sector and
+// pair lists, the connectivity table, workspace layout and kernel dispatch.
+#include <algorithm>
+#include <cmath>
+#include <complex>
+#include <cstdio>
+#include <cstring>
+#include <map>
+#include <memory>
+#include <mutex>
+#include <string>
+#include <thread>
+#include <tuple>
+#include <unordered_map>
+#include <vector>
+
+#include <cuda_runtime.h>
+
+#include "../../include/vqe.h"
+#include "vqe_internal.h"
+
+using vqe::GateRec;
+using vqe::GroupRec;
+using vqe::InstDesc;
+using cplx = std::complex<double>;
+
+namespace {
+
+thread_local std::string g_err;
+int g_flags = 0;
+
+int fail(int code, const std::string& msg) {
+  g_err = msg;
+  return code;
+}
+
+int cuda_fail(cudaError_t e, const char* what) {
+  return fail(VQE_ERR_CUDA, std::string(what) + ": " + cudaGetErrorString(e));
+}
+
+inline int pc32(uint32_t v) { return __builtin_popcount(v); }
+inline int pc64(uint64_t v) { return __builtin_popcountll(v); }
+
+template <typename T>
+int upload(const std::vector<T>& v, T** out) {
+  *out = nullptr;
+  if (v.empty()) return VQE_OK;
+  cudaError_t e = cudaMalloc(reinterpret_cast<void**>(out), v.size() * sizeof(T));
+  if (e != cudaSuccess) {
+    *out = nullptr;
+    return fail(VQE_ERR_NO_MEMORY, std::string("cudaMalloc: ") + cudaGetErrorString(e));
+  }
+  e = cudaMemcpy(*out, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy");
+  return VQE_OK;
+}
+
+void dfree(void* p) {
+  if (p) cudaFree(p);
+}
+
+size_t align256(size_t v) { return (v + 255) & ~size_t(255); }
+
+// Run f(lo, hi) over [0, n) on up to hardware_concurrency threads.
+template <typename F>
+void parallel_for(int64_t n, F f) {
+  int nt = int(std::thread::hardware_concurrency());
+  if (nt < 1) nt = 1;
+  if (nt > 32) nt = 32;
+  if (n < 4096 || nt == 1) {
+    f(int64_t(0), n);
+    return;
+  }
+  std::vector<std::thread> ts;
+  const int64_t chunk = (n + nt - 1) / nt;
+  for (int t = 0; t < nt; ++t) {
+    const int64_t lo = t * chunk, hi = std::min(n, lo + chunk);
+    if (lo >= hi) break;
+    ts.emplace_back([=]() { f(lo, hi); });
+  }
+  for (auto& t : ts) t.join();
+}
+
+// ------------------------------------------------------------------ Pauli algebra
+// A Pauli string P(x, z) = i^{|x&z|} X^x Z^z. Product rule:
+// P(x1,z1) P(x2,z2) = i^{|x1&z1| + |x2&z2| + 2|z1&x2| - |x&z|} P(x, z), x = x1^x2, z = z1^z2.
+struct PTerm {
+  uint64_t x, z;
+  cplx c;
+};
+
+inline PTerm pmul(const PTerm& a, const PTerm& b) {
+  const uint64_t x = a.x ^ b.x, z = a.z ^ b.z;
+  int ph = pc64(a.x & a.z) + pc64(b.x & b.z) + 2 * pc64(a.z & b.x) - pc64(x & z);
+  ph = ((ph % 4) + 4) % 4;
+  static const cplx ipow[4] = {cplx(1, 0), cplx(0, 1), cplx(-1, 0), cplx(0, -1)};
+  return PTerm{x, z, a.c * b.c * ipow[ph]};
+}
+
+// Jordan-Wigner ladder operator of spin orbital p as two Pauli strings:
+// a_p = (P(p, <p) + i P(p, <p|p)) / 2, a+_p = (P(p, <p) - i P(p, <p|p)) / 2.
+inline void ladder(int p, bool dagger, PTerm out[2]) {
+  const uint64_t bit = uint64_t(1) << p, below = bit - 1;
+  out[0] = PTerm{bit, below, cplx(0.5, 0.0)};
+  out[1] = PTerm{bit, below | bit, cplx(0.0, dagger ? -0.5 : 0.5)};
+}
+
+// Adds coef * (product of ladder ops, leftmost first) into acc.
+void add_ladder_product(std::unordered_map<uint64_t, cplx>& acc, double coef, const int* orb,
+                        const bool* dag, int nops) {
+  PTerm f[4][2];
+  for (int i = 0; i < nops; ++i) ladder(orb[i], dag[i], f[i]);
+  for (int choice = 0; choice < (1 << nops); ++choice) {
+    PTerm t{0, 0, cplx(coef, 0.0)};
+    for (int i = 0; i < nops; ++i) t = pmul(t, f[i][(choice >> i) & 1]);
+    if (t.c == cplx(0, 0)) continue;
+    acc[(t.x << 32) | t.z] += t.c;
+  }
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ handles
+struct vqe_hamiltonian_s {
+  int n = 0;
+  std::vector<uint64_t> x, z;
+  std::vector<double> c;
+  std::vector<GroupRec> groups;
+  std::vector<uint32_t> emask;
+  std::vector<cplx> cvals;
+  int is_real = 1;
+  GroupRec* d_groups = nullptr;
+  uint32_t* d_emask = nullptr;
+  double* d_vals = nullptr;
+  double2* d_cvals = nullptr;
+  struct Ell {
+    int W = 0;
+    bool use_ell = false;
+    uint32_t* d_ell = nullptr;
+    int64_t nnz = 0;                  // connected (output, group) pairs
+    double extra_adds = 0;            // sum over nnz of (entries - 1)
+  };
+  std::mutex mu;
+  std::map<std::tuple<int, int, int>, Ell> ells;
+  ~vqe_hamiltonian_s() {
+    dfree(d_groups);
+    dfree(d_emask);
+    dfree(d_vals);
+    dfree(d_cvals);
+    for (auto& kv : ells) dfree(kv.second.d_ell);
+  }
+};
+
+struct vqe_ansatz_s {
+  int n = 0, M = 0;
+  uint64_t hf = 0;
+  int n_elec = 0, n_alpha = -1;
+  std::vector<int32_t> exc;
+  std::vector<GateRec> gates;
+  std::vector<int64_t> pair_off;
+  std::vector<uint32_t> pairs;
+  std::vector<uint32_t> sector;
+  std::vector<int32_t> nb_rows;
+  GateRec* d_gates = nullptr;
+  int64_t* d_pair_off = nullptr;
+  uint32_t* d_pairs = nullptr;
+  uint32_t* d_sector = nullptr;
+  int32_t* d_nb_rows = nullptr;
+  std::tuple<int, int, int> key() const { return std::make_tuple(n, n_elec, n_alpha); }
+  ~vqe_ansatz_s() {
+    dfree(d_gates);
+    dfree(d_pair_off);
+    dfree(d_pairs);
+    dfree(d_sector);
+    dfree(d_nb_rows);
+  }
+};
+
+struct vqe_batch_s {
+  int n_inst = 0;
+  int32_t max_params = 0;
+  std::vector<vqe_hamiltonian_t> hams;
+  std::vector<vqe_ansatz_t> ans;
+  std::vector<InstDesc> descs;          // host copies, device pointers inside
+  std::vector<int> resident[2];         // instance indices per mode (0 real, 1 complex)
+  std::vector<int> streaming[2];
+  InstDesc* d_res[2] = {nullptr, nullptr};
+  size_t res_smem[2] = {0, 0};
+  ~vqe_batch_s() {
+    dfree(d_res[0]);
+    dfree(d_res[1]);
+  }
+};
+
+namespace {
+
+const vqe_hamiltonian_s::Ell* get_ell(vqe_hamiltonian_t h, vqe_ansatz_t a, int* err) {
+  *err = VQE_OK;
+  std::lock_guard<std::mutex> lock(h->mu);
+  auto it = h->ells.find(a->key());
+  if (it != h->ells.end()) return &it->second;
+  vqe_hamiltonian_s::Ell e;
+  const int64_t D = int64_t(a->sector.size());
+  const int G = int(h->groups.size());
+  const int ne = a->n_elec, na = a->n_alpha;
+  auto inside = [ne, na](uint32_t k) {
+    return pc32(k) == ne && (na < 0 || pc32(k & 0x55555555u) == na);
+  };
+  // group order inside a row: by entry count, then pattern bits, then index, so
+  // that lanes of a warp meet groups of the same shape at the same slot.
+  std::vector<int> order(G);
+  for (int g = 0; g < G; ++g) order[g] = g;
+  std::stable_sort(order.begin(), order.end(), [&](int p, int q) {
+    const int ep = h->groups[p].eend - h->groups[p].ebeg, eq = h->groups[q].eend - h->groups[q].ebeg;
+    if (ep != eq) return ep < eq;
+    return h->groups[p].ubits < h->groups[q].ubits;
+  });
+  // row lengths
+  std::vector<int32_t> len(D, 0);
+  const double cost = double(D) * double(G);
+  if (cost <= 4.0e9 && G > 0) {
+    parallel_for(D, [&](int64_t lo, int64_t hi) {
+      for (int64_t r = lo; r < hi; ++r) {
+        const uint32_t k = a->sector[r];
+        int c = 0;
+        for (int g = 0; g < G; ++g) c += inside(k ^ h->groups[g].x);
+        len[r] = c;
+      }
+    });
+    int W = 0;
+    int64_t nnz = 0;
+    for (int64_t r = 0; r < D; ++r) {
+      W = std::max(W, int(len[r]));
+      nnz += len[r];
+    }
+    e.nnz = nnz;
+    const double bytes = double(W) * double(D) * 4.0;
+    if (bytes <= 2.0e9) {
+      std::vector<uint32_t> ell(size_t(W) * size_t(D), vqe::kEllPad);
+      std::vector<double> extra(D, 0.0);
+      parallel_for(D, [&](int64_t lo, int64_t hi) {
+        for (int64_t r = lo; r < hi; ++r) {
+          const uint32_t k = a->sector[r];
+          int j = 0;
+          double ex = 0;
+          for (int oi = 0; oi < G; ++oi) {
+            const int g = order[oi];
+            if (inside(k ^ h->groups[g].x)) {
+              ell[size_t(j) * size_t(D) + size_t(r)] = uint32_t(g);
+              ex += h->groups[g].eend - h->groups[g].ebeg - 1;
+              ++j;
+            }
+          }
+          extra[r] = ex;
+        }
+      });
+      for (int64_t r = 0; r < D; ++r) e.extra_adds += extra[r];
+      e.W = W;
+      e.use_ell = true;
+      int rc = upload(ell, &e.d_ell);
+      if (rc != VQE_OK) {
+        *err = rc;
+        return nullptr;
+      }
+    }
+  }
+  if (!e.use_ell) {
+    // scan mode: count work on a sample only when the exact count is too costly
+    e.nnz = 0;
+    e.extra_adds = 0;
+    const int64_t step = std::max<int64_t>(1, D / 4096);
+    int64_t sampled = 0;
+    double nnz = 0, ex = 0;
+    for (int64_t r = 0; r < D; r += step) {
+      const uint32_t k = a->sector[r];
+      for (int g = 0; g < G; ++g)
+        if (inside(k ^ h->groups[g].x)) {
+          nnz += 1;
+          ex += h->groups[g].eend - h->groups[g].ebeg - 1;
+        }
+      ++sampled;
+    }
+    if (sampled > 0) {
+      e.nnz = int64_t(nnz * double(D) / double(sampled));
+      e.extra_adds = ex * double(D) / double(sampled);
+    }
+  }
+  auto res = h->ells.emplace(a->key(), e);
+  return &res.first->second;
+}
+
+InstDesc make_desc(vqe_hamiltonian_t h, vqe_ansatz_t a, const vqe_hamiltonian_s::Ell* e, int64_t inst) {
+  InstDesc d;
+  std::memset(&d, 0, sizeof(d));
+  d.n = a->n;
+  d.M = a->M;
+  d.hf = uint32_t(a->hf);
+  d.D = int64_t(a->sector.size());
+  d.sector = a->d_sector;
+  d.gates = a->d_gates;
+  d.pair_off = a->d_pair_off;
+  d.pairs = a->d_pairs;
+  d.G = int(h->groups.size());
+  d.W = e->use_ell ? e->W : 0;
+  d.groups = h->d_groups;
+  d.emask = h->d_emask;
+  d.vals = h->d_vals;
+  d.cvals = h->d_cvals;
+  d.ell = e->d_ell;
+  d.inst = inst;
+  return d;
+}
+
+bool use_real() { return (g_flags & VQE_FLAG_FORCE_COMPLEX) == 0; }
+
+size_t resident_bytes(vqe_ansatz_t a, bool real) {
+  return vqe::resident_smem_bytes(a->n, a->M, int64_t(a->pairs.size()), real);
+}
+
+bool resident_ok(vqe_ansatz_t a, const vqe_hamiltonian_s::Ell* e, bool real) {
+  if (g_flags & VQE_FLAG_FORCE_STREAMING) return false;
+  if (!e->use_ell) return false;
+  int dev = 0, optin = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return false;
+  if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
+    return false;
+  return resident_bytes(a, real) <= size_t(optin);
+}
+
+struct WsLayout {
+  size_t psi, lam, cs, epart, gpart, total;
+};
+
+WsLayout ws_layout(vqe_ansatz_t a, bool complex_amp, bool with_grad) {
+  WsLayout L;
+  const size_t amp = complex_amp ? 16 : 8;
+  const size_t vec = align256((size_t(1) << a->n) * amp);
+  L.psi = 0;
+  L.lam = vec;
+  L.cs = 2 * vec;
+  L.epart = L.cs + align256(size_t(std::max(a->M, 1)) * 16);
+  L.gpart = L.epart + align256(size_t(vqe::kMaxPartials) * 8);
+  L.total = L.gpart + (with_grad ? align256(size_t(std::max(a->M, 1)) * vqe::kMaxPartials * 8) : 0);
+  return L;
+}
+
+vqe::StreamBuffers buffers(void* ws, const WsLayout& L) {
+  char* b = static_cast<char*>(ws);
+  vqe::StreamBuffers s;
+  s.psi = b + L.psi;
+  s.lam = b + L.lam;
+  s.cs = reinterpret_cast<double2*>(b + L.cs);
+  s.epart = reinterpret_cast<double*>(b + L.epart);
+  s.gpart = reinterpret_cast<double*>(b + L.gpart);
+  return s;
+}
+
+vqe::StreamPlan plan(vqe_ansatz_t a, const vqe_hamiltonian_s::Ell* e) {
+  vqe::StreamPlan p;
+  p.pair_off_host = a->pair_off.data();
+  p.d_nb_rows = a->d_nb_rows;
+  p.n_elec = a->n_elec;
+  p.n_alpha = a->n_alpha;
+  p.use_ell = e->use_ell;
+  return p;
+}
+
+int check_ws(void* ws, size_t have, size_t need) {
+  if (need == 0) return VQE_OK;
+  if (ws == nullptr) return fail(VQE_ERR_WORKSPACE, "workspace is NULL");
+  if (reinterpret_cast<uintptr_t>(ws) % 256 != 0) return fail(VQE_ERR_WORKSPACE, "workspace not 256-byte aligned");
+  if (have < need)
+    return fail(VQE_ERR_WORKSPACE, "workspace too small: need " + std::to_string(need) + " bytes, got " +
+                                       std::to_string(have));
+  return VQE_OK;
+}
+
+int check_pair(vqe_hamiltonian_t h, vqe_ansatz_t a) {
+  if (!h || !a) return fail(VQE_ERR_INVALID_ARG, "NULL handle");
+  if (h->n != a->n) return fail(VQE_ERR_INVALID_ARG, "Hamiltonian and ansatz qubit counts differ");
+  return VQE_OK;
+}
+
+// dynamic shared memory opt-in, cached per device and mode
+int ensure_smem(size_t smem, bool real) {
+  static std::mutex mu;
+  static std::map<std::pair<int, int>, size_t> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  std::lock_guard<std::mutex> lock(mu);
+  auto key = std::make_pair(dev, real ? 1 : 0);
+  auto it = done.find(key);
+  if (it != done.end() && it->second >= smem) return VQE_OK;
+  e = vqe::set_resident_smem_limit(smem, real);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute");
+  done[key] = smem;
+  return VQE_OK;
+}
+
+int run_single(vqe_hamiltonian_t h, vqe_ansatz_t a, const double* theta, double* energy, double* grad,
+               void* ws, size_t ws_bytes, cudaStream_t stream, bool with_grad) {
+  int rc = check_pair(h, a);
+  if (rc) return rc;
+  if ((!theta && a->M > 0) || !energy || (with_grad && !grad && a->M > 0))
+    return fail(VQE_ERR_INVALID_ARG, "NULL device pointer");
+  const auto* e = get_ell(h, a, &rc);
+  if (!e) return rc;
+  const bool real = use_real();
+  InstDesc d = make_desc(h, a, e, 0);
+  if (resident_ok(a, e, real)) {
+    const size_t smem = resident_bytes(a, real);
+    if ((rc = ensure_smem(smem, real))) return rc;
+    cudaError_t ce = vqe::launch_resident(nullptr, &d, 1, smem, real, with_grad, theta, 0, energy, grad, 0,
+                                          stream);
+    if (ce != cudaSuccess) return cuda_fail(ce, "resident kernel launch");
+    return VQE_OK;
+  }
+  const WsLayout L = ws_layout(a, !real, with_grad);
+  if ((rc = check_ws(ws, ws_bytes, L.total))) return rc;
+  cudaError_t ce = vqe::stream_energy_grad(d, plan(a, e), buffers(ws, L), real, with_grad, theta, energy,
+                                           grad, stream);
+  if (ce != cudaSuccess) return cuda_fail(ce, "streaming launch");
+  return VQE_OK;
+}
+
+}  // namespace
+
+// ------------------------------------------------------------------ C ABI
+extern "C" {
+
+int vqe_version(void) { return 100; }
+
+int vqe_set_flags(int flags) {
+  const int old = g_flags;
+  g_flags = flags;
+  return old;
+}
+
+const char* vqe_last_error(void) { return g_err.c_str(); }
+
+int vqe_jordan_wigner(int n_spatial, const double* h, const double* eri, double c0, double drop_tol,
+                      int64_t capacity, uint64_t* x_out, uint64_t* z_out, double* c_out, int64_t* n_out) {
+  if (n_spatial < 1 || n_spatial > 16) return fail(VQE_ERR_INVALID_ARG, "n_spatial must be 1..16");
+  if (!h || !eri || !n_out) return fail(VQE_ERR_INVALID_ARG, "NULL input");
+  if (!(drop_tol >= 0.0) || !std::isfinite(c0)) return fail(VQE_ERR_INVALID_ARG, "bad drop_tol or c0");
+  const int ns = n_spatial;
+  std::unordered_map<uint64_t, cplx> acc;
+  acc.reserve(size_t(1) << 20);
+  if (c0 != 0.0) acc[0] += cplx(c0, 0.0);
+  for (int p = 0; p < ns; ++p)
+    for (int q = 0; q < ns; ++q) {
+      const double v = h[p * ns + q];
+      if (!std::isfinite(v)) return fail(VQE_ERR_INVALID_ARG, "non-finite h");
+      if (v == 0.0) continue;
+      for (int s = 0; s < 2; ++s) {
+        const int orb[2] = {2 * p + s, 2 * q + s};
+        const bool dag[2] = {true, false};
+        add_ladder_product(acc, v, orb, dag, 2);
+      }
+    }
+  for (int p = 0; p < ns; ++p)
+    for (int q = 0; q < ns; ++q)
+      for (int r = 0; r < ns; ++r)
+        for (int s = 0; s < ns; ++s) {
+          const double v = eri[((p * ns + q) * ns + r) * ns + s];
+          if (!std::isfinite(v)) return fail(VQE_ERR_INVALID_ARG, "non-finite eri");
+          if (v == 0.0) continue;
+          for (int sg = 0; sg < 2; ++sg)
+            for (int tau = 0; tau < 2; ++tau) {
+              const int P = 2 * p + sg, Q = 2 * q + sg, R = 2 * r + tau, S = 2 * s + tau;
+              if (P == R || Q == S) continue;  // a+_P a+_P = 0 and a_Q a_Q = 0
+              const int orb[4] = {P, R, S, Q};
+              const bool dag[4] = {true, true, false, false};
+              add_ladder_product(acc, 0.5 * v, orb, dag, 4);
+            }
+        }
+  std::vector<std::pair<uint64_t, double>> terms;
+  terms.reserve(acc.size());
+  for (const auto& kv : acc) {
+    const cplx c = kv.second;
+    if (std::fabs(c.imag()) > 1e-10 * std::max(1.0, std::fabs(c.real())))
+      return fail(VQE_ERR_NOT_REAL, "mapped coefficient has an imaginary part; integrals not symmetric?");
+    if (std::fabs(c.real()) < drop_tol || c.real() == 0.0) continue;
+    terms.emplace_back(kv.first, c.real());
+  }
+  std::sort(terms.begin(), terms.end(),
+            [](const std::pair<uint64_t, double>& a, const std::pair<uint64_t, double>& b) { return a.first < b.first; });
+  *n_out = int64_t(terms.size());
+  if (capacity < int64_t(terms.size()) || !x_out || !z_out || !c_out)
+    return fail(VQE_ERR_INVALID_ARG, "capacity too small: need " + std::to_string(terms.size()));
+  for (size_t i = 0; i < terms.size(); ++i) {
+    x_out[i] = terms[i].first >> 32;
+    z_out[i] = terms[i].first & 0xFFFFFFFFull;
+    c_out[i] = terms[i].second;
+  }
+  return VQE_OK;
+}
+
+int vqe_create_hamiltonian(int n_qubits, int64_t n_terms, const uint64_t* xs, const uint64_t* zs,
+                           const double* cs, double drop_tol, vqe_hamiltonian_t* out) {
+  if (!out) return fail(VQE_ERR_INVALID_ARG, "NULL out");
+  *out = nullptr;
+  if (n_qubits < 1 || n_qubits > vqe::kMaxQubits) return fail(VQE_ERR_INVALID_ARG, "n_qubits must be 1..32");
+  if (n_terms < 1) return fail(VQE_ERR_INVALID_ARG, "n_terms must be >= 1");
+  if (!xs || !zs || !cs) return fail(VQE_ERR_INVALID_ARG, "NULL term array");
+  if (!(drop_tol >= 0.0) || !std::isfinite(drop_tol)) return fail(VQE_ERR_INVALID_ARG, "bad drop_tol");
+  const uint64_t full = (n_qubits == 64) ? ~0ull : ((uint64_t(1) << n_qubits) - 1);
+  std::map<std::pair<uint64_t, uint64_t>, double> merged;
+  for (int64_t t = 0; t < n_terms; ++t) {
+    if ((xs[t] & ~full) || (zs[t] & ~full))
+      return fail(VQE_ERR_INVALID_ARG, "term " + std::to_string(t) + " has a mask bit >= n_qubits");
+    if (!std::isfinite(cs[t])) return fail(VQE_ERR_INVALID_ARG, "non-finite coefficient");
+    merged[std::make_pair(xs[t], zs[t])] += cs[t];
+  }
+  std::unique_ptr<vqe_hamiltonian_s> H(new vqe_hamiltonian_s);
+  H->n = n_qubits;
+  for (const auto& kv : merged) {
+    if (std::fabs(kv.second) < drop_tol || kv.second == 0.0) continue;
+    H->x.push_back(kv.first.first);
+    H->z.push_back(kv.first.second);
+    H->c.push_back(kv.second);
+  }
+  // group by x (merged is sorted by x then z)
+  static const cplx ipow[4] = {cplx(1, 0), cplx(0, 1), cplx(-1, 0), cplx(0, -1)};
+  size_t t = 0;
+  while (t < H->x.size()) {
+    size_t t1 = t;
+    while (t1 < H->x.size() && H->x[t1] == H->x[t]) ++t1;
+    const uint32_t x = uint32_t(H->x[t]);
+    GroupRec g;
+    std::memset(&g, 0, sizeof(g));
+    g.x = x;
+    const uint32_t xsel = (pc32(x) <= vqe::kMaxPatternBits) ? x : 0u;
+    int pos[4] = {0, 0, 0, 0}, ub = 0;
+    for (int q = 0; q < 32; ++q)
+      if ((xsel >> q) & 1u) pos[ub++] = q;
+    g.ubits = ub;
+    g.upos = 0;
+    for (int j = 0; j < ub; ++j) g.upos |= uint32_t(pos[j]) << (8 * j);
+    const int nu = 1 << ub;
+    std::map<uint32_t, std::vector<cplx>> entries;  // z outside the pattern bits -> table
+    for (size_t i = t; i < t1; ++i) {
+      const uint32_t z = uint32_t(H->z[i]);
+      const cplx cp = H->c[i] * ipow[pc32(x & z) & 3];
+      auto& tab = entries[z & ~xsel];
+      if (tab.empty()) tab.assign(nu, cplx(0, 0));
+      for (int u = 0; u < nu; ++u) {
+        uint32_t bits = 0;
+        for (int j = 0; j < ub; ++j)
+          if ((u >> j) & 1) bits |= 1u << pos[j];
+        tab[u] += (pc32(bits & z) & 1) ? -cp : cp;
+      }
+    }
+    g.ebeg = int32_t(H->emask.size());
+    g.vbeg = int32_t(H->cvals.size());
+    for (const auto& kv : entries) {
+      H->emask.push_back(kv.first);
+      for (int u = 0; u < nu; ++u) H->cvals.push_back(kv.second[u]);
+    }
+    g.eend = int32_t(H->emask.size());
+    H->groups.push_back(g);
+    t = t1;
+  }
+  std::vector<double> vals(H->cvals.size());
+  std::vector<double2> cv(H->cvals.size());
+  H->is_real = 1;
+  for (size_t i = 0; i < H->cvals.size(); ++i) {
+    vals[i] = H->cvals[i].real();
+    cv[i] = make_double2(H->cvals[i].real(), H->cvals[i].imag());
+    if (H->cvals[i].imag() != 0.0) H->is_real = 0;
+  }
+  if (H->groups.empty()) {
+    // H = 0 after dropping: keep one empty identity group so tables are non-empty
+    GroupRec g;
+    std::memset(&g, 0, sizeof(g));
+    g.ebeg = 0;
+    g.eend = 1;
+    g.vbeg = 0;
+    H->emask.push_back(0);
+    H->cvals.push_back(cplx(0, 0));
+    vals.push_back(0.0);
+    cv.push_back(make_double2(0.0, 0.0));
+    H->groups.push_back(g);
+  }
+  int rc;
+  if ((rc = upload(H->groups, &H->d_groups))) return rc;
+  if ((rc = upload(H->emask, &H->d_emask))) return rc;
+  if ((rc = upload(vals, &H->d_vals))) return rc;
+  if ((rc = upload(cv, &H->d_cvals))) return rc;
+  *out = H.release();
+  return VQE_OK;
+}
+
+int vqe_hamiltonian_info(vqe_hamiltonian_t h, int* n_qubits, int64_t* n_terms, int64_t* n_groups,
+                         int* is_real) {
+  if (!h) return fail(VQE_ERR_INVALID_ARG, "NULL handle");
+  if (n_qubits) *n_qubits = h->n;
+  if (n_terms) *n_terms = int64_t(h->x.size());
+  if (n_groups) *n_groups = h->x.empty() ? 0 : int64_t(h->groups.size());
+  if (is_real) *is_real = h->is_real;
+  return VQE_OK;
+}
+
+void vqe_destroy_hamiltonian(vqe_hamiltonian_t h) { delete h; }
+
+int vqe_create_ansatz(int n_qubits, uint64_t hf_bits, int32_t n_exc, const int32_t* exc,
+                      vqe_ansatz_t* out) {
+  if (!out) return fail(VQE_ERR_INVALID_ARG, "NULL out");
+  *out = nullptr;
+  if (n_qubits < 1 || n_qubits > vqe::kMaxQubits) return fail(VQE_ERR_INVALID_ARG, "n_qubits must be 1..32");
+  const uint64_t full = (uint64_t(1) << n_qubits) - 1;
+  if (hf_bits & ~full) return fail(VQE_ERR_INVALID_ARG, "hf_bits has a bit >= n_qubits");
+  if (n_exc < 0 || (n_exc > 0 && !exc)) return fail(VQE_ERR_INVALID_ARG, "bad excitation list");
+  std::unique_ptr<vqe_ansatz_s> A(new vqe_ansatz_s);
+  A->n = n_qubits;
+  A->M = n_exc;
+  A->hf = hf_bits;
+  A->exc.assign(exc, exc + 4 * size_t(n_exc));
+  A->n_elec = pc64(hf_bits);
+  bool spin_ok = true;
+  for (int m = 0; m < n_exc; ++m) {
+    const int32_t* e = exc + 4 * m;
+    const bool single = e[2] < 0;
+    int orb[4];
+    int nops;
+    if (single) {
+      if (e[3] >= 0) return fail(VQE_ERR_INVALID_ARG, "single excitation needs {i, a, -1, -1}");
+      orb[0] = e[1];  // a+_a
+      orb[1] = e[0];  // a_i
+      nops = 2;
+    } else {
+      orb[0] = e[2];  // a+_a
+      orb[1] = e[3];  // a+_b
+      orb[2] = e[1];  // a_j
+      orb[3] = e[0];  // a_i
+      nops = 4;
+    }
+    uint32_t flip = 0;
+    for (int i = 0; i < nops; ++i) {
+      if (orb[i] < 0 || orb[i] >= n_qubits)
+        return fail(VQE_ERR_INVALID_ARG, "excitation " + std::to_string(m) + " index out of range");
+      if (flip & (1u << orb[i]))
+        return fail(VQE_ERR_INVALID_ARG, "excitation " + std::to_string(m) + " repeats an index");
+      flip |= 1u << orb[i];
+    }
+    const uint32_t occ = single ? (1u << e[0]) : ((1u << e[0]) | (1u << e[1]));
+    const uint32_t vir = flip & ~occ;
+    if (pc32(occ & 0x55555555u) != pc32(vir & 0x55555555u)) spin_ok = false;
+    // sign of T on k0 = occ, applying the rightmost factor first
+    uint32_t k = occ;
+    int par = 0;
+    uint32_t pmask = 0;
+    for (int i = nops - 1; i >= 0; --i) {
+      const uint32_t bit = 1u << orb[i], below = bit - 1;
+      par ^= pc32(k & below) & 1;
+      pmask ^= below;
+      k ^= bit;
+    }
+    GateRec g;
+    g.flip = flip;
+    g.par = pmask & ~flip;
+    g.sign0 = par ? -1 : 1;
+    g.pad = 0;
+    A->gates.push_back(g);
+  }
+  A->n_alpha = spin_ok ? pc32(uint32_t(hf_bits) & 0x55555555u) : -1;
+  // sector enumeration
+  const int n = n_qubits;
+  auto subsets = [](uint32_t pool, int c, std::vector<uint32_t>& outv) {
+    std::vector<int> bits;
+    for (int q = 0; q < 32; ++q)
+      if ((pool >> q) & 1u) bits.push_back(q);
+    const int m = int(bits.size());
+    outv.clear();
+    if (c < 0 || c > m) return;
+    if (c == 0) {
+      outv.push_back(0);
+      return;
+    }
+    uint64_t v = (uint64_t(1) << c) - 1;
+    const uint64_t lim = uint64_t(1) << m;
+    while (v < lim) {
+      uint32_t w = 0;
+      for (int j = 0; j < m; ++j)
+        if ((v >> j) & 1) w |= 1u << bits[j];
+      outv.push_back(w);
+      const uint64_t t = v | (v - 1);
+      v = (t + 1) | (((~t & (t + 1)) - 1) >> (__builtin_ctzll(v) + 1));
+    }
+  };
+  const uint32_t all = uint32_t(full);
+  const uint32_t even = all & 0x55555555u, odd = all & 0xAAAAAAAAu;
+  auto enumerate = [&](uint32_t fixed_occ, uint32_t fixed_all, std::vector<uint32_t>& outv) {
+    // states k with k & fixed_all == fixed_occ and the sector's counts
+    outv.clear();
+    const uint32_t free_bits = all & ~fixed_all;
+    if (A->n_alpha >= 0) {
+      const int ca = A->n_alpha - pc32(fixed_occ & even);
+      const int cb = (A->n_elec - A->n_alpha) - pc32(fixed_occ & odd);
+      std::vector<uint32_t> pa, pb;
+      subsets(free_bits & even, ca, pa);
+      subsets(free_bits & odd, cb, pb);
+      outv.reserve(pa.size() * pb.size());
+      for (uint32_t u : pa)
+        for (uint32_t w : pb) outv.push_back(fixed_occ | u | w);
+    } else {
+      std::vector<uint32_t> pf;
+      subsets(free_bits, A->n_elec - pc32(fixed_occ), pf);
+      for (uint32_t u : pf) outv.push_back(fixed_occ | u);
+    }
+    std::sort(outv.begin(), outv.end());
+  };
+  enumerate(0, 0, A->sector);
+  (void)n;
+  // pair lists: lower states (occupied i,j; empty a,b) of each gate
+  A->pair_off.assign(size_t(n_exc) + 1, 0);
+  std::vector<std::vector<uint32_t>> per(n_exc);
+  parallel_for(n_exc, [&](int64_t lo, int64_t hi) {
+    for (int64_t m = lo; m < hi; ++m) {
+      const int32_t* e = exc + 4 * m;
+      const uint32_t occ = (e[2] < 0) ? (1u << e[0]) : ((1u << e[0]) | (1u << e[1]));
+      enumerate(occ, A->gates[m].flip, per[m]);
+    }
+  });
+  for (int m = 0; m < n_exc; ++m) A->pair_off[m + 1] = A->pair_off[m] + int64_t(per[m].size());
+  A->pairs.resize(size_t(A->pair_off[n_exc]));
+  for (int m = 0; m < n_exc; ++m)
+    std::copy(per[m].begin(), per[m].end(), A->pairs.begin() + A->pair_off[m]);
+  A->nb_rows.resize(size_t(n_exc) + 1);
+  for (int m = 0; m < n_exc; ++m) A->nb_rows[m] = vqe::stream_grid(A->pair_off[m + 1] - A->pair_off[m]);
+  A->nb_rows[n_exc] = vqe::stream_grid(int64_t(A->sector.size()));
+  int rc;
+  if ((rc = upload(A->gates, &A->d_gates))) return rc;
+  if ((rc = upload(A->pair_off, &A->d_pair_off))) return rc;
+  if ((rc = upload(A->pairs, &A->d_pairs))) return rc;
+  if ((rc = upload(A->sector, &A->d_sector))) return rc;
+  if ((rc = upload(A->nb_rows, &A->d_nb_rows))) return rc;
+  if (A->pairs.empty()) {
+    // keep a valid (never read) pair pointer for kernels
+    std::vector<uint32_t> one(1, 0);
+    if ((rc = upload(one, &A->d_pairs))) return rc;
+  }
+  *out = A.release();
+  return VQE_OK;
+}
+
+int vqe_ansatz_info(vqe_ansatz_t a, int* n_qubits, int32_t* n_params, int64_t* sector_dim, int64_t* n_pairs) {
+  if (!a) return fail(VQE_ERR_INVALID_ARG, "NULL handle");
+  if (n_qubits) *n_qubits = a->n;
+  if (n_params) *n_params = a->M;
+  if (sector_dim) *sector_dim = int64_t(a->sector.size());
+  if (n_pairs) *n_pairs = int64_t(a->pairs.size());
+  return VQE_OK;
+}
+
+void vqe_destroy_ansatz(vqe_ansatz_t a) { delete a; }
+
+size_t vqe_workspace_bytes(vqe_hamiltonian_t h, vqe_ansatz_t a, int mode) {
+  if (check_pair(h, a)) return 0;
+  int rc = VQE_OK;
+  if (!get_ell(h, a, &rc)) return 0;
+  const bool cplx_amp = (mode & VQE_WS_COMPLEX) || !use_real();
+  return ws_layout(a, cplx_amp, (mode & VQE_WS_GRAD) != 0).total;
+}
+
+int vqe_energy(vqe_hamiltonian_t h, vqe_ansatz_t a, const double* theta, double* energy, void* ws,
+               size_t ws_bytes, vqe_stream_t stream) {
+  return run_single(h, a, theta, energy, nullptr, ws, ws_bytes, static_cast<cudaStream_t>(stream), false);
+}
+
+int vqe_energy_grad(vqe_hamiltonian_t h, vqe_ansatz_t a, const double* theta, double* energy, double* grad,
+                    void* ws, size_t ws_bytes, vqe_stream_t stream) {
+  return run_single(h, a, theta, energy, grad, ws, ws_bytes, static_cast<cudaStream_t>(stream), true);
+}
+
+int vqe_state(vqe_ansatz_t a, vqe_hamiltonian_t h, const double* theta, double* psi_out, void* ws,
+              size_t ws_bytes, vqe_stream_t stream) {
+  int rc = check_pair(h, a);
+  if (rc) return rc;
+  if ((!theta && a->M > 0) || !psi_out) return fail(VQE_ERR_INVALID_ARG, "NULL device pointer");
+  const auto* e = get_ell(h, a, &rc);
+  if (!e) return rc;
+  const WsLayout L = ws_layout(a, false, false);
+  if ((rc = check_ws(ws, ws_bytes, L.total))) return rc;
+  InstDesc d = make_desc(h, a, e, 0);
+  cudaError_t ce = vqe::stream_state(d, plan(a, e), buffers(ws, L), theta, psi_out,
+                                     static_cast<cudaStream_t>(stream));
+  if (ce != cudaSuccess) return cuda_fail(ce, "state launch");
+  return VQE_OK;
+}
+
+int vqe_apply_hamiltonian(vqe_hamiltonian_t h, vqe_ansatz_t a, const double* psi, double* lam_out,
+                          double* energy, void* ws, size_t ws_bytes, vqe_stream_t stream) {
+  int rc = check_pair(h, a);
+  if (rc) return rc;
+  if (!psi || !lam_out || !energy) return fail(VQE_ERR_INVALID_ARG, "NULL device pointer");
+  const auto* e = get_ell(h, a, &rc);
+  if (!e) return rc;
+  const WsLayout L = ws_layout(a, true, false);
+  if ((rc = check_ws(ws, ws_bytes, L.total))) return rc;
+  InstDesc d = make_desc(h, a, e, 0);
+  cudaError_t ce = vqe::stream_apply_h(d, plan(a, e), buffers(ws, L), psi, lam_out, energy,
+                                       static_cast<cudaStream_t>(stream));
+  if (ce != cudaSuccess) return cuda_fail(ce, "apply_hamiltonian launch");
+  return VQE_OK;
+}
+
+int vqe_create_batch(int n_inst, const vqe_hamiltonian_t* hams, const vqe_ansatz_t* ans, vqe_batch_t* out) {
+  if (!out) return fail(VQE_ERR_INVALID_ARG, "NULL out");
+  *out = nullptr;
+  if (n_inst < 1 || !hams || !ans) return fail(VQE_ERR_INVALID_ARG, "bad batch arrays");
+  std::unique_ptr<vqe_batch_s> B(new vqe_batch_s);
+  B->n_inst = n_inst;
+  for (int i = 0; i < n_inst; ++i) {
+    int rc = check_pair(hams[i], ans[i]);
+    if (rc) return fail(rc, "instance " + std::to_string(i) + ": " + g_err);
+    const auto* e = get_ell(hams[i], ans[i], &rc);
+    if (!e) return rc;
+    B->hams.push_back(hams[i]);
+    B->ans.push_back(ans[i]);
+    B->descs.push_back(make_desc(hams[i], ans[i], e, i));
+    B->max_params = std::max(B->max_params, ans[i]->M);
+    for (int mode = 0; mode < 2; ++mode) {
+      const bool real = mode == 0;
+      if (resident_ok(ans[i], e, real)) {
+        B->resident[mode].push_back(i);
+        B->res_smem[mode] = std::max(B->res_smem[mode], resident_bytes(ans[i], real));
+      } else {
+        B->streaming[mode].push_back(i);
+      }
+    }
+  }
+  for (int mode = 0; mode < 2; ++mode) {
+    std::vector<InstDesc> v;
+    for (int i : B->resident[mode]) v.push_back(B->descs[i]);
+    int rc = upload(v, &B->d_res[mode]);
+    if (rc) return rc;
+  }
+  *out = B.release();
+  return VQE_OK;
+}
+
+int32_t vqe_batch_max_params(vqe_batch_t b) { return b ? b->max_params : 0; }
+
+size_t vqe_batch_workspace_bytes(vqe_batch_t b, int with_grad) {
+  if (!b) return 0;
+  const int mode = use_real() ? 0 : 1;
+  size_t need = 0;
+  for (int i : b->streaming[mode]) need = std::max(need, ws_layout(b->ans[i], mode == 1, with_grad != 0).total);
+  return need;
+}
+
+static int batch_run(vqe_batch_t b, const double* theta, int64_t ld_theta, double* energies, double* grads,
+                     int64_t ld_grad, void* ws, size_t ws_bytes, cudaStream_t stream) {
+  if (!b) return fail(VQE_ERR_INVALID_ARG, "NULL batch");
+  const bool with_grad = grads != nullptr;
+  if (!theta || !energies) return fail(VQE_ERR_INVALID_ARG, "NULL device pointer");
+  if (ld_theta < b->max_params || (with_grad && ld_grad < b->max_params))
+    return fail(VQE_ERR_INVALID_ARG, "leading dimension smaller than max params");
+  const bool real = use_real();
+  const int mode = real ? 0 : 1;
+  int rc;
+  if (!b->resident[mode].empty()) {
+    if ((rc = ensure_smem(b->res_smem[mode], real))) return rc;
+    cudaError_t ce = vqe::launch_resident(b->d_res[mode], nullptr, int(b->resident[mode].size()),
+                                          b->res_smem[mode], real, with_grad, theta, ld_theta, energies,
+                                          grads, ld_grad, stream);
+    if (ce != cudaSuccess) return cuda_fail(ce, "batched resident launch");
+  }
+  if (!b->streaming[mode].empty()) {
+    const size_t need = vqe_batch_workspace_bytes(b, with_grad);
+    if ((rc = check_ws(ws, ws_bytes, need))) return rc;
+    for (int i : b->streaming[mode]) {
+      vqe_ansatz_t a = b->ans[i];
+      int rc2 = VQE_OK;
+      const auto* e = get_ell(b->hams[i], a, &rc2);
+      if (!e) return rc2;
+      const WsLayout L = ws_layout(a, !real, with_grad);
+      cudaError_t ce = vqe::stream_energy_grad(b->descs[i], plan(a, e), buffers(ws, L), real, with_grad,
+                                               theta + int64_t(i) * ld_theta, energies + i,
+                                               with_grad ? grads + int64_t(i) * ld_grad : nullptr, stream);
+      if (ce != cudaSuccess) return cuda_fail(ce, "batched streaming launch");
+    }
+  }
+  return VQE_OK;
+}
+
+int vqe_batch_energy_grad(vqe_batch_t b, const double* theta, int64_t ld_theta, double* energies,
+                          double* grads, int64_t ld_grad, void* ws, size_t ws_bytes, vqe_stream_t stream) {
+  return batch_run(b, theta, ld_theta, energies, grads, ld_grad, ws, ws_bytes,
+                   static_cast<cudaStream_t>(stream));
+}
+
+size_t vqe_batch_host_workspace_bytes(vqe_batch_t b, int with_grad) {
+  if (!b) return 0;
+  const size_t io = align256(size_t(b->n_inst) * size_t(std::max(b->max_params, 1)) * 8) +
+                    align256(size_t(b->n_inst) * 8) +
+                    (with_grad ? align256(size_t(b->n_inst) * size_t(std::max(b->max_params, 1)) * 8) : 0);
+  return io + vqe_batch_workspace_bytes(b, with_grad);
+}
+
+int vqe_batch_energy_grad_host(vqe_batch_t b, const double* theta_host, int64_t ld_theta, double* energies_host,
+                               double* grads_host, int64_t ld_grad, void* ws, size_t ws_bytes,
+                               vqe_stream_t stream_) {
+  if (!b) return fail(VQE_ERR_INVALID_ARG, "NULL batch");
+  cudaStream_t stream = static_cast<cudaStream_t>(stream_);
+  const bool with_grad = grads_host != nullptr;
+  if (!theta_host || !energies_host) return fail(VQE_ERR_INVALID_ARG, "NULL host pointer");
+  const int64_t Mx = std::max(b->max_params, 1);
+  if (ld_theta < b->max_params || (with_grad && ld_grad < b->max_params))
+    return fail(VQE_ERR_INVALID_ARG, "leading dimension smaller than max params");
+  const size_t need = vqe_batch_host_workspace_bytes(b, with_grad);
+  int rc = check_ws(ws, ws_bytes, need);
+  if (rc) return rc;
+  char* base = static_cast<char*>(ws);
+  double* d_theta = reinterpret_cast<double*>(base);
+  size_t off = align256(size_t(b->n_inst) * size_t(Mx) * 8);
+  double* d_e = reinterpret_cast<double*>(base + off);
+  off += align256(size_t(b->n_inst) * 8);
+  double* d_g = nullptr;
+  if (with_grad) {
+    d_g = reinterpret_cast<double*>(base + off);
+    off += align256(size_t(b->n_inst) * size_t(Mx) * 8);
+  }
+  cudaError_t ce = cudaMemcpy2DAsync(d_theta, size_t(Mx) * 8, theta_host, size_t(ld_theta) * 8,
+                                     size_t(b->max_params) * 8, size_t(b->n_inst), cudaMemcpyHostToDevice,
+                                     stream);
+  if (ce != cudaSuccess) return cuda_fail(ce, "theta upload");
+  rc = batch_run(b, d_theta, Mx, d_e, d_g, Mx, base + off, ws_bytes - off, stream);
+  if (rc) return rc;
+  ce = cudaMemcpyAsync(energies_host, d_e, size_t(b->n_inst) * 8, cudaMemcpyDeviceToHost, stream);
+  if (ce != cudaSuccess) return cuda_fail(ce, "energy download");
+  if (with_grad) {
+    ce = cudaMemcpy2DAsync(grads_host, size_t(ld_grad) * 8, d_g, size_t(Mx) * 8, size_t(b->max_params) * 8,
+                           size_t(b->n_inst), cudaMemcpyDeviceToHost, stream);
+    if (ce != cudaSuccess) return cuda_fail(ce, "gradient download");
+  }
+  ce = cudaStreamSynchronize(stream);
+  if (ce != cudaSuccess) return cuda_fail(ce, "stream synchronize");
+  return VQE_OK;
+}
+
+void vqe_destroy_batch(vqe_batch_t b) { delete b; }
+
+int vqe_work_estimate(vqe_hamiltonian_t h, vqe_ansatz_t a, int with_grad, double* flops, double* bytes) {
+  int rc = check_pair(h, a);
+  if (rc) return rc;
+  const auto* e = get_ell(h, a, &rc);
+  if (!e) return rc;
+  const double P = double(a->pairs.size());
+  const double D = double(a->sector.size());
+  // forward rotation 6 flops/pair; H psi: 2 per connected (output, group) plus
+  // the table adds, 2 per output for <psi|lambda>; adjoint 16 flops/pair.
+  double f = 6.0 * P + 2.0 * double(e->nnz) + e->extra_adds + 2.0 * D;
+  // compulsory state traffic (real amplitudes): 4 amplitude moves per pair
+  // forward, psi read + lambda written once on the sector, 8 moves per pair adjoint.
+  double by = 32.0 * P + 16.0 * D;
+  if (with_grad) {
+    f += 16.0 * P;
+    by += 64.0 * P;
+  }
+  if (flops) *flops = f;
+  if (bytes) *bytes = by;
+  return VQE_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,518 @@
+// CUDA kernels of libvqe for sm_103a: the hot path of E(theta) (Eq. 1) and its
+// adjoint gradient.
+//
+//   a1  |HF>                      : the reference bitstring of Eq. 1
+//   a2  psi <- U_M ... U_1 psi     : UCCSD excitation rotations (Sec. 2.1.2)
+//   a3  lambda = H psi, E = <psi|lambda> : Pauli sum grouped by X mask
+//   a4  reverse sweep              : g_k = 2 Re <lambda|A_k|phi>, then
+//                                    phi <- U_k^dagger phi, lambda <- U_k^dagger lambda
+//
+// psi(theta) is real for every theta (real rotations of a real bitstring), so
+// the REAL instantiation stores amplitudes as doubles and folds only the real
+// part of each Pauli coefficient c * i^{|x&z|}; the imaginary part of H psi
+// does not enter E or g. The complex instantiation (double2) computes the same
+// quantities with complex amplitudes and full complex coefficients.
+//
+// Every reduction is deterministic: fixed work assignment, fixed shuffle
+// trees, fixed summation order of partials.
+#include <cuda_runtime.h>
+
+#include "vqe_internal.h"
+
+namespace vqe {
+namespace {
+
+__device__ __forceinline__ int parity32(uint32_t v) { return __popc(v) & 1; }
+
+// v with its sign bit flipped when s == 1 (integer pipe, no FP64 op).
+__device__ __forceinline__ double sflip(double v, int s) {
+  return __hiloint2double(__double2hiint(v) ^ (s << 31), __double2loint(v));
+}
+__device__ __forceinline__ double2 sflip(double2 v, int s) {
+  return make_double2(sflip(v.x, s), sflip(v.y, s));
+}
+
+__device__ __forceinline__ uint32_t pattern_of(uint32_t src, uint32_t upos, int ubits) {
+  uint32_t u = 0;
+#pragma unroll
+  for (int j = 0; j < kMaxPatternBits; ++j)
+    if (j < ubits) u |= ((src >> ((upos >> (8 * j)) & 31u)) & 1u) << j;
+  return u;
+}
+
+__device__ __forceinline__ GroupRec load_group(const GroupRec* p) {
+  const int4* q = reinterpret_cast<const int4*>(p);
+  const int4 a = __ldg(q);
+  const int4 b = __ldg(q + 1);
+  GroupRec g;
+  g.x = uint32_t(a.x);
+  g.upos = uint32_t(a.y);
+  g.ebeg = a.z;
+  g.eend = a.w;
+  g.vbeg = b.x;
+  g.ubits = b.y;
+  g.pad0 = g.pad1 = 0;
+  return g;
+}
+
+__device__ __forceinline__ GateRec load_gate(const GateRec* p) {
+  const int4 a = __ldg(reinterpret_cast<const int4*>(p));
+  GateRec r;
+  r.flip = uint32_t(a.x);
+  r.par = uint32_t(a.y);
+  r.sign0 = a.z;
+  r.pad = 0;
+  return r;
+}
+
+// ---------------------------------------------------------------- amplitude algebra
+template <bool REAL> struct Amp;
+
+template <> struct Amp<true> {
+  typedef double T;
+  typedef double C;  // coefficient type
+  static __device__ __forceinline__ T zero() { return 0.0; }
+  static __device__ __forceinline__ T unit() { return 1.0; }
+  static __device__ __forceinline__ C coef(const InstDesc& d, int64_t slot) { return __ldg(d.vals + slot); }
+  // acc += f * p
+  static __device__ __forceinline__ void mac(T& acc, C f, T p) { acc = fma(f, p, acc); }
+  // Re(conj(a) * b)
+  static __device__ __forceinline__ double redot(T a, T b) { return a * b; }
+  // (c a - ss b, ss a + c b)
+  static __device__ __forceinline__ void rot(T& a, T& b, double c, double ss) {
+    const T a0 = a;
+    a = fma(-ss, b, c * a0);
+    b = fma(ss, a0, c * b);
+  }
+  static __device__ __forceinline__ double2 to_c(T a) { return make_double2(a, 0.0); }
+  static __device__ __forceinline__ T from_c(double2 a) { return a.x; }
+};
+
+template <> struct Amp<false> {
+  typedef double2 T;
+  typedef double2 C;
+  static __device__ __forceinline__ T zero() { return make_double2(0.0, 0.0); }
+  static __device__ __forceinline__ T unit() { return make_double2(1.0, 0.0); }
+  static __device__ __forceinline__ C coef(const InstDesc& d, int64_t slot) { return __ldg(d.cvals + slot); }
+  static __device__ __forceinline__ void mac(T& acc, C f, T p) {
+    acc.x = fma(f.x, p.x, fma(-f.y, p.y, acc.x));
+    acc.y = fma(f.x, p.y, fma(f.y, p.x, acc.y));
+  }
+  static __device__ __forceinline__ double redot(T a, T b) { return fma(a.x, b.x, a.y * b.y); }
+  static __device__ __forceinline__ void rot(T& a, T& b, double c, double ss) {
+    const T a0 = a;
+    a.x = fma(-ss, b.x, c * a0.x);
+    a.y = fma(-ss, b.y, c * a0.y);
+    b.x = fma(ss, a0.x, c * b.x);
+    b.y = fma(ss, a0.y, c * b.y);
+  }
+  static __device__ __forceinline__ double2 to_c(T a) { return a; }
+  static __device__ __forceinline__ T from_c(double2 a) { return a; }
+};
+
+// Folded coefficient f_g(src) of a group (see GroupRec).
+template <bool REAL>
+__device__ __forceinline__ typename Amp<REAL>::C group_coef(const InstDesc& d, const GroupRec& g,
+                                                            uint32_t src) {
+  typedef Amp<REAL> A;
+  const uint32_t u = pattern_of(src, g.upos, g.ubits);
+  const int64_t base = int64_t(g.vbeg) + u;
+  typename A::C f = sflip(A::coef(d, base), parity32(src & __ldg(d.emask + g.ebeg)));
+  for (int e = g.ebeg + 1, j = 1; e < g.eend; ++e, ++j) {
+    const typename A::C v = sflip(A::coef(d, base + (int64_t(j) << g.ubits)),
+                                  parity32(src & __ldg(d.emask + e)));
+    if constexpr (REAL) {
+      f += v;
+    } else {
+      f.x += v.x;
+      f.y += v.y;
+    }
+  }
+  return f;
+}
+
+__device__ __forceinline__ bool in_sector(uint32_t k, int n_elec, int n_alpha) {
+  if (__popc(k) != n_elec) return false;
+  return n_alpha < 0 || __popc(k & 0x55555555u) == n_alpha;
+}
+
+// Deterministic block sum; the result is valid in thread 0.
+__device__ double block_sum(double v, double* red) {
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  __syncthreads();
+  if (lane == 0) red[w] = v;
+  __syncthreads();
+  double s = 0.0;
+  if (threadIdx.x == 0)
+    for (int i = 0; i < int(blockDim.x >> 5); ++i) s += red[i];
+  return s;
+}
+
+// ---------------------------------------------------------------- resident kernel
+// One CTA evaluates one instance with psi and lambda in shared memory: HF init,
+// forward sweep, H psi with the energy, and the reverse sweep with per-pair
+// gradient contributions that are summed per gate in pair order at the end.
+template <bool REAL>
+__global__ void __launch_bounds__(kResidentThreads, 1)
+k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double* __restrict__ theta,
+           int64_t ld_theta, double* __restrict__ energy, double* __restrict__ grad, int64_t ld_grad,
+           int with_grad) {
+  typedef Amp<REAL> A;
+  typedef typename A::T T;
+  extern __shared__ __align__(16) unsigned char smem[];
+  const InstDesc& d = descs ? descs[blockIdx.x] : one;
+  const int tid = threadIdx.x, bs = blockDim.x;
+  const int n = d.n, M = d.M;
+  const uint32_t dim = 1u << n;
+  const int64_t D = d.D;
+  const int64_t P = d.pair_off[M];
+  T* psi = reinterpret_cast<T*>(smem);
+  T* lam = psi + dim;
+  double2* cs = reinterpret_cast<double2*>(lam + dim);
+  double* gbuf = reinterpret_cast<double*>(cs + M);
+  double* red = gbuf + P;
+  const int64_t row = d.inst;
+  const double* th = theta + row * ld_theta;
+
+  for (int m = tid; m < M; m += bs) {
+    double s, c;
+    sincos(th[m], &s, &c);
+    cs[m] = make_double2(c, s);
+  }
+  for (uint32_t k = tid; k < dim; k += bs) {
+    psi[k] = A::zero();
+    lam[k] = A::zero();
+  }
+  __syncthreads();
+  if (tid == 0) psi[d.hf] = A::unit();
+  __syncthreads();
+
+  // a2: forward sweep
+  for (int m = 0; m < M; ++m) {
+    const GateRec gr = load_gate(d.gates + m);
+    const int64_t p0 = __ldg(d.pair_off + m), p1 = __ldg(d.pair_off + m + 1);
+    const double2 c_s = cs[m];
+    const int s0 = gr.sign0 < 0;
+    for (int64_t p = p0 + tid; p < p1; p += bs) {
+      const uint32_t k = __ldg(d.pairs + p);
+      const uint32_t k2 = k ^ gr.flip;
+      const double ss = sflip(c_s.y, parity32(k & gr.par) ^ s0);
+      T a = psi[k], b = psi[k2];
+      A::rot(a, b, c_s.x, ss);
+      psi[k] = a;
+      psi[k2] = b;
+    }
+    __syncthreads();
+  }
+
+  // a3: lambda = H psi on the sector, E = <psi|lambda>
+  double e_part = 0.0;
+  for (int64_t r = tid; r < D; r += bs) {
+    const uint32_t k = __ldg(d.sector + r);
+    T acc = A::zero();
+    for (int j = 0; j < d.W; ++j) {
+      const uint32_t gi = __ldg(d.ell + int64_t(j) * D + r);
+      if (gi == kEllPad) break;
+      const GroupRec g = load_group(d.groups + gi);
+      const uint32_t src = k ^ g.x;
+      A::mac(acc, group_coef<REAL>(d, g, src), psi[src]);
+    }
+    lam[k] = acc;
+    e_part += A::redot(psi[k], acc);
+  }
+  const double e_tot = block_sum(e_part, red);
+  if (tid == 0) energy[row] = e_tot;
+  __syncthreads();
+
+  if (!with_grad) return;
+
+  // a4: reverse sweep
+  for (int m = M - 1; m >= 0; --m) {
+    const GateRec gr = load_gate(d.gates + m);
+    const int64_t p0 = __ldg(d.pair_off + m), p1 = __ldg(d.pair_off + m + 1);
+    const double2 c_s = cs[m];
+    const int s0 = gr.sign0 < 0;
+    for (int64_t p = p0 + tid; p < p1; p += bs) {
+      const uint32_t k = __ldg(d.pairs + p);
+      const uint32_t k2 = k ^ gr.flip;
+      const int sb = parity32(k & gr.par) ^ s0;
+      const double ss = sflip(c_s.y, sb);
+      T pa = psi[k], pb = psi[k2], la = lam[k], lb = lam[k2];
+      gbuf[p] = sflip(A::redot(lb, pa) - A::redot(la, pb), sb);
+      A::rot(pa, pb, c_s.x, -ss);
+      A::rot(la, lb, c_s.x, -ss);
+      psi[k] = pa;
+      psi[k2] = pb;
+      lam[k] = la;
+      lam[k2] = lb;
+    }
+    __syncthreads();
+  }
+  double* g_out = grad + row * ld_grad;
+  for (int m = tid; m < M; m += bs) {
+    const int64_t p0 = __ldg(d.pair_off + m), p1 = __ldg(d.pair_off + m + 1);
+    double s = 0.0;
+    for (int64_t p = p0; p < p1; ++p) s += gbuf[p];
+    g_out[m] = 2.0 * s;
+  }
+}
+
+// ---------------------------------------------------------------- streaming kernels
+__global__ void k_trig(const double* __restrict__ theta, int M, double2* __restrict__ cs) {
+  const int m = blockIdx.x * blockDim.x + threadIdx.x;
+  if (m < M) {
+    double s, c;
+    sincos(theta[m], &s, &c);
+    cs[m] = make_double2(c, s);
+  }
+}
+
+template <bool REAL>
+__global__ void k_init_sector(const uint32_t* __restrict__ sector, int64_t D, uint32_t hf,
+                              typename Amp<REAL>::T* __restrict__ psi) {
+  typedef Amp<REAL> A;
+  for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < D;
+       r += int64_t(gridDim.x) * blockDim.x) {
+    const uint32_t k = __ldg(sector + r);
+    psi[k] = (k == hf) ? A::unit() : A::zero();
+  }
+}
+
+template <bool REAL>
+__global__ void k_gate_fwd(const uint32_t* __restrict__ pairs, int64_t P, const GateRec* __restrict__ gate,
+                           const double2* __restrict__ cs, typename Amp<REAL>::T* __restrict__ psi) {
+  typedef Amp<REAL> A;
+  typedef typename A::T T;
+  const GateRec gr = load_gate(gate);
+  const double2 c_s = __ldg(cs);
+  const int s0 = gr.sign0 < 0;
+  for (int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; p < P;
+       p += int64_t(gridDim.x) * blockDim.x) {
+    const uint32_t k = __ldg(pairs + p);
+    const uint32_t k2 = k ^ gr.flip;
+    const double ss = sflip(c_s.y, parity32(k & gr.par) ^ s0);
+    T a = psi[k], b = psi[k2];
+    A::rot(a, b, c_s.x, ss);
+    psi[k] = a;
+    psi[k2] = b;
+  }
+}
+
+// lambda = H psi on the sector; per-block energy partials.
+template <bool REAL, bool ELL>
+__global__ void __launch_bounds__(kStreamThreads)
+k_hpsi(const InstDesc d, int n_elec, int n_alpha, const typename Amp<REAL>::T* __restrict__ psi,
+       typename Amp<REAL>::T* __restrict__ lam, double* __restrict__ epart) {
+  typedef Amp<REAL> A;
+  typedef typename A::T T;
+  __shared__ double red[32];
+  double e_part = 0.0;
+  for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < d.D;
+       r += int64_t(gridDim.x) * blockDim.x) {
+    const uint32_t k = __ldg(d.sector + r);
+    T acc = A::zero();
+    if (ELL) {
+      for (int j = 0; j < d.W; ++j) {
+        const uint32_t gi = __ldg(d.ell + int64_t(j) * d.D + r);
+        if (gi == kEllPad) break;
+        const GroupRec g = load_group(d.groups + gi);
+        const uint32_t src = k ^ g.x;
+        A::mac(acc, group_coef<REAL>(d, g, src), psi[src]);
+      }
+    } else {
+      for (int gi = 0; gi < d.G; ++gi) {
+        const GroupRec g = load_group(d.groups + gi);
+        const uint32_t src = k ^ g.x;
+        if (!in_sector(src, n_elec, n_alpha)) continue;
+        A::mac(acc, group_coef<REAL>(d, g, src), psi[src]);
+      }
+    }
+    lam[k] = acc;
+    e_part += A::redot(psi[k], acc);
+  }
+  const double s = block_sum(e_part, red);
+  if (threadIdx.x == 0) epart[blockIdx.x] = s;
+}
+
+template <bool REAL>
+__global__ void __launch_bounds__(kStreamThreads)
+k_gate_adj(const uint32_t* __restrict__ pairs, int64_t P, const GateRec* __restrict__ gate,
+           const double2* __restrict__ cs, typename Amp<REAL>::T* __restrict__ phi,
+           typename Amp<REAL>::T* __restrict__ lam, double* __restrict__ gpart) {
+  typedef Amp<REAL> A;
+  typedef typename A::T T;
+  __shared__ double red[32];
+  const GateRec gr = load_gate(gate);
+  const double2 c_s = __ldg(cs);
+  const int s0 = gr.sign0 < 0;
+  double acc = 0.0;
+  for (int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; p < P;
+       p += int64_t(gridDim.x) * blockDim.x) {
+    const uint32_t k = __ldg(pairs + p);
+    const uint32_t k2 = k ^ gr.flip;
+    const int sb = parity32(k & gr.par) ^ s0;
+    const double ss = sflip(c_s.y, sb);
+    T pa = phi[k], pb = phi[k2], la = lam[k], lb = lam[k2];
+    acc += sflip(A::redot(lb, pa) - A::redot(la, pb), sb);
+    A::rot(pa, pb, c_s.x, -ss);
+    A::rot(la, lb, c_s.x, -ss);
+    phi[k] = pa;
+    phi[k2] = pb;
+    lam[k] = la;
+    lam[k2] = lb;
+  }
+  const double s = block_sum(acc, red);
+  if (threadIdx.x == 0) gpart[blockIdx.x] = s;
+}
+
+// Sums nb[i] partials of row i (row i at part + i*kMaxPartials) in a fixed
+// order: lane-strided sequential sums, then a fixed shuffle tree.
+__global__ void k_finalize(const double* __restrict__ part, const int32_t* __restrict__ nb_rows,
+                           int rows, double scale, double* __restrict__ out) {
+  const int row = blockIdx.x;
+  if (row >= rows) return;
+  const int nb = nb_rows[row];
+  const double* p = part + int64_t(row) * kMaxPartials;
+  double s = 0.0;
+  for (int i = threadIdx.x; i < nb; i += 32) s += p[i];
+#pragma unroll
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if (threadIdx.x == 0) out[row] = scale * s;
+}
+
+template <bool REAL>
+__global__ void k_scatter_out(const uint32_t* __restrict__ sector, int64_t D,
+                              const typename Amp<REAL>::T* __restrict__ v, double2* __restrict__ out) {
+  for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < D;
+       r += int64_t(gridDim.x) * blockDim.x) {
+    const uint32_t k = __ldg(sector + r);
+    out[k] = Amp<REAL>::to_c(v[k]);
+  }
+}
+
+__global__ void k_gather_in(const uint32_t* __restrict__ sector, int64_t D, const double2* __restrict__ in,
+                            double2* __restrict__ v) {
+  for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < D;
+       r += int64_t(gridDim.x) * blockDim.x) {
+    const uint32_t k = __ldg(sector + r);
+    v[k] = in[k];
+  }
+}
+
+}  // namespace
+
+// ---------------------------------------------------------------- launchers
+cudaError_t set_resident_smem_limit(size_t smem, bool real) {
+  if (real)
+    return cudaFuncSetAttribute(k_resident<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  return cudaFuncSetAttribute(k_resident<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+}
+
+cudaError_t launch_resident(const InstDesc* d_descs, const InstDesc* one, int n_inst, size_t smem,
+                            bool real, bool with_grad, const double* theta, int64_t ld_theta,
+                            double* energy, double* grad, int64_t ld_grad, cudaStream_t stream) {
+  InstDesc dummy = {};
+  const InstDesc& o = one ? *one : dummy;
+  if (real)
+    k_resident<true><<<n_inst, kResidentThreads, smem, stream>>>(d_descs, o, theta, ld_theta, energy,
+                                                                 grad, ld_grad, with_grad ? 1 : 0);
+  else
+    k_resident<false><<<n_inst, kResidentThreads, smem, stream>>>(d_descs, o, theta, ld_theta, energy,
+                                                                  grad, ld_grad, with_grad ? 1 : 0);
+  return cudaGetLastError();
+}
+
+namespace {
+template <bool REAL>
+cudaError_t stream_forward(const InstDesc& d, const StreamPlan& sp, const StreamBuffers& b,
+                           const double* theta, cudaStream_t stream) {
+  typedef typename Amp<REAL>::T T;
+  T* psi = static_cast<T*>(b.psi);
+  const int nt = kStreamThreads;
+  if (d.M > 0) k_trig<<<(d.M + 255) / 256, 256, 0, stream>>>(theta, d.M, b.cs);
+  k_init_sector<REAL><<<stream_grid(d.D), nt, 0, stream>>>(d.sector, d.D, d.hf, psi);
+  for (int m = 0; m < d.M; ++m) {
+    const int64_t p0 = sp.pair_off_host[m], p1 = sp.pair_off_host[m + 1];
+    if (p1 > p0)
+      k_gate_fwd<REAL><<<stream_grid(p1 - p0), nt, 0, stream>>>(d.pairs + p0, p1 - p0, d.gates + m,
+                                                                b.cs + m, psi);
+  }
+  return cudaGetLastError();
+}
+
+template <bool REAL>
+cudaError_t stream_hpsi(const InstDesc& d, const StreamPlan& sp, const StreamBuffers& b,
+                        double* energy, cudaStream_t stream) {
+  typedef typename Amp<REAL>::T T;
+  const T* psi = static_cast<const T*>(b.psi);
+  T* lam = static_cast<T*>(b.lam);
+  const int grid = stream_grid(d.D);
+  if (sp.use_ell)
+    k_hpsi<REAL, true><<<grid, kStreamThreads, 0, stream>>>(d, sp.n_elec, sp.n_alpha, psi, lam, b.epart);
+  else
+    k_hpsi<REAL, false><<<grid, kStreamThreads, 0, stream>>>(d, sp.n_elec, sp.n_alpha, psi, lam, b.epart);
+  k_finalize<<<1, 32, 0, stream>>>(b.epart, sp.d_nb_rows + d.M, 1, 1.0, energy);
+  return cudaGetLastError();
+}
+
+template <bool REAL>
+cudaError_t stream_adjoint(const InstDesc& d, const StreamPlan& sp, const StreamBuffers& b,
+                           double* grad, cudaStream_t stream) {
+  typedef typename Amp<REAL>::T T;
+  T* phi = static_cast<T*>(b.psi);
+  T* lam = static_cast<T*>(b.lam);
+  for (int m = d.M - 1; m >= 0; --m) {
+    const int64_t p0 = sp.pair_off_host[m], p1 = sp.pair_off_host[m + 1];
+    double* gp = b.gpart + int64_t(m) * kMaxPartials;
+    k_gate_adj<REAL><<<stream_grid(p1 - p0), kStreamThreads, 0, stream>>>(
+        d.pairs + p0, p1 - p0, d.gates + m, b.cs + m, phi, lam, gp);
+  }
+  if (d.M > 0) k_finalize<<<d.M, 32, 0, stream>>>(b.gpart, sp.d_nb_rows, d.M, 2.0, grad);
+  return cudaGetLastError();
+}
+}  // namespace
+
+cudaError_t stream_energy_grad(const InstDesc& d, const StreamPlan& sp, const StreamBuffers& b,
+                               bool real, bool with_grad, const double* theta, double* energy,
+                               double* grad, cudaStream_t stream) {
+  cudaError_t e;
+  if (real) {
+    if ((e = stream_forward<true>(d, sp, b, theta, stream)) != cudaSuccess) return e;
+    if ((e = stream_hpsi<true>(d, sp, b, energy, stream)) != cudaSuccess) return e;
+    if (with_grad) return stream_adjoint<true>(d, sp, b, grad, stream);
+  } else {
+    if ((e = stream_forward<false>(d, sp, b, theta, stream)) != cudaSuccess) return e;
+    if ((e = stream_hpsi<false>(d, sp, b, energy, stream)) != cudaSuccess) return e;
+    if (with_grad) return stream_adjoint<false>(d, sp, b, grad, stream);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t stream_state(const InstDesc& d, const StreamPlan& sp, const StreamBuffers& b,
+                         const double* theta, double* psi_out, cudaStream_t stream) {
+  cudaError_t e = stream_forward<true>(d, sp, b, theta, stream);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(psi_out, 0, (size_t(1) << d.n) * sizeof(double2), stream);
+  if (e != cudaSuccess) return e;
+  k_scatter_out<true><<<stream_grid(d.D), kStreamThreads, 0, stream>>>(
+      d.sector, d.D, static_cast<const double*>(b.psi), reinterpret_cast<double2*>(psi_out));
+  return cudaGetLastError();
+}
+
+cudaError_t stream_apply_h(const InstDesc& d, const StreamPlan& sp, const StreamBuffers& b,
+                           const double* psi_in, double* lam_out, double* energy,
+                           cudaStream_t stream) {
+  k_gather_in<<<stream_grid(d.D), kStreamThreads, 0, stream>>>(
+      d.sector, d.D, reinterpret_cast<const double2*>(psi_in), static_cast<double2*>(b.psi));
+  cudaError_t e = stream_hpsi<false>(d, sp, b, energy, stream);
+  if (e != cudaSuccess) return e;
+  e = cudaMemsetAsync(lam_out, 0, (size_t(1) << d.n) * sizeof(double2), stream);
+  if (e != cudaSuccess) return e;
+  k_scatter_out<false><<<stream_grid(d.D), kStreamThreads, 0, stream>>>(
+      d.sector, d.D, static_cast<const double2*>(b.lam), reinterpret_cast<double2*>(lam_out));
+  return cudaGetLastError();
+}
+
+}  // namespace vqe

@@ -1,0 +1,337 @@
+"""Parity of the CUDA path (through the C ABI) against the CPU oracle.
+
+Bar: |dE| <= 1e-10 Ha and |dg_k| <= 1e-9 for every compared component, on the
+same seeded inputs. The oracle evaluates Eq. 2 from the integrals by literal
+ladder operators (not the library's Jordan-Wigner list) unless a test feeds a
+random Pauli sum, where it applies the Pauli strings explicitly.
+"""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+import paper_2311_01242_gb300 as vq
+
+pytestmark = pytest.mark.gpu
+
+E_TOL = 1e-10
+G_TOL = 1e-9
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _lib():
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    vq.build()
+    vq.load()
+    yield
+    vq.set_flags(0)
+
+
+def gpu_eg(problem, exc, theta, drop_tol=1e-14, flags=0):
+    old = vq.set_flags(flags)
+    try:
+        H = vq.Hamiltonian.from_problem(problem, drop_tol)
+        A = vq.Ansatz(problem.n_qubits, synth.hf_bitstring(problem.n_elec), exc)
+        e, g = vq.energy_grad(H, A, torch.as_tensor(theta, dtype=torch.float64).cuda())
+        torch.cuda.synchronize()
+        return float(e), g.cpu().numpy()
+    finally:
+        vq.set_flags(old)
+
+
+def oracle_eg(problem, exc, theta, indices=None, full=None):
+    model = oracle.EnergyModel.from_problem(problem, full=full)
+    return oracle.gradient_direct(model, synth.hf_bitstring(problem.n_elec), exc, theta, indices)
+
+
+# ------------------------------------------------------------------ small chemistry
+def test_config0_energy_gradient():
+    w = synth.config0()
+    p, exc, th = w.problems[0], w.excitations[0], w.thetas[0]
+    e_o, g_o = oracle_eg(p, exc, th)
+    for flags in (0, vq.VQE_FLAG_FORCE_STREAMING, vq.VQE_FLAG_FORCE_COMPLEX,
+                  vq.VQE_FLAG_FORCE_COMPLEX | vq.VQE_FLAG_FORCE_STREAMING):
+        e, g = gpu_eg(p, exc, th, flags=flags)
+        assert abs(e - e_o) <= E_TOL, flags
+        assert np.abs(g - g_o).max() <= G_TOL, flags
+
+
+def test_config0_bfgs_on_gpu_reaches_exact_energy():
+    import scipy.optimize as so
+    w = synth.config0()
+    p, exc = w.problems[0], w.excitations[0]
+    H = vq.Hamiltonian.from_problem(p)
+    A = vq.Ansatz(4, 3, exc)
+    ws = vq.alloc_workspace(vq.workspace_bytes(H, A))
+
+    def fun(t):
+        e, g = vq.energy_grad(H, A, torch.as_tensor(t).cuda(), workspace=ws)
+        return float(e), g.cpu().numpy()
+
+    e0 = oracle.exact_ground_energy(p)
+    best = min(so.minimize(fun, x0, jac=True, method="BFGS", options={"gtol": 1e-10}).fun
+               for x0 in (np.zeros(3), w.thetas[0], np.array([0.5, -0.5, 1.0])))
+    assert abs(best - e0) < 1e-8
+
+
+@pytest.mark.parametrize("seed,n_s,n_elec", [(101, 3, 2), (102, 4, 3), (103, 4, 4), (104, 5, 4),
+                                             (105, 6, 6)])
+def test_random_problems_resident_and_streaming(seed, n_s, n_elec):
+    rng = np.random.default_rng(seed)
+    p = synth.random_problem(rng, n_s, n_elec, 3)
+    exc = synth.uccsd_pool(2 * n_s, n_elec)
+    exc = exc[rng.permutation(len(exc))]
+    th = rng.normal(0, 0.3, size=len(exc))
+    e_o, g_o = oracle_eg(p, exc, th)
+    for flags in (0, vq.VQE_FLAG_FORCE_STREAMING):
+        e, g = gpu_eg(p, exc, th, flags=flags)
+        assert abs(e - e_o) <= E_TOL
+        assert np.abs(g - g_o).max() <= G_TOL
+
+
+def test_real_and_complex_paths_agree_bitwise_on_energy():
+    rng = np.random.default_rng(7)
+    p = synth.random_problem(rng, 5, 5, 4)
+    exc = synth.uccsd_pool(10, 5)
+    th = rng.normal(0, 0.2, size=len(exc))
+    for stream_flag in (0, vq.VQE_FLAG_FORCE_STREAMING):
+        e_r, g_r = gpu_eg(p, exc, th, flags=stream_flag)
+        e_c, g_c = gpu_eg(p, exc, th, flags=stream_flag | vq.VQE_FLAG_FORCE_COMPLEX)
+        assert abs(e_r - e_c) <= 1e-13
+        assert np.abs(g_r - g_c).max() <= 1e-13
+
+
+# ------------------------------------------------------------------ the 12-qubit scan, batched
+def test_config1_batch_energies_and_sampled_gradients():
+    w = synth.config1()
+    exc = w.excitations[0]
+    hams = [vq.Hamiltonian.from_problem(p) for p in w.problems]
+    A = vq.Ansatz(12, synth.hf_bitstring(6), exc)
+    B = vq.Batch(hams, [A] * len(hams))
+    theta = torch.as_tensor(np.stack(w.thetas)).cuda().contiguous()
+    e, g = B.energy_grad(theta)
+    torch.cuda.synchronize()
+    e, g = e.cpu().numpy(), g.cpu().numpy()
+    hf = synth.hf_bitstring(6)
+    for i in range(0, 64, 9):
+        model = oracle.EnergyModel.from_problem(w.problems[i])
+        if i in (0, 63):
+            e_o, g_o = oracle.gradient_direct(model, hf, exc, w.thetas[i])
+            assert np.abs(g[i] - g_o).max() <= G_TOL
+        else:
+            e_o = oracle.energy(model, hf, exc, w.thetas[i])
+        assert abs(e[i] - e_o) <= E_TOL, i
+    # batched result equals the single-instance result
+    for i in (0, 31, 63):
+        e1, g1 = vq.energy_grad(hams[i], A, theta[i])
+        assert abs(float(e1) - e[i]) <= 1e-14
+        assert np.abs(g1.cpu().numpy() - g[i]).max() <= 1e-14
+
+
+def test_batch_host_entry_matches_device_entry():
+    w = synth.config1(8)
+    hams = [vq.Hamiltonian.from_problem(p) for p in w.problems]
+    A = vq.Ansatz(12, synth.hf_bitstring(6), w.excitations[0])
+    B = vq.Batch(hams, [A] * len(hams))
+    th = np.ascontiguousarray(np.stack(w.thetas))
+    e_d, g_d = B.energy_grad(torch.as_tensor(th).cuda())
+    ws = vq.alloc_workspace(B.host_workspace_bytes(True))
+    e_h = np.zeros(8)
+    g_h = np.zeros((8, B.max_params))
+    B.energy_grad_host(th, e_h, g_h, ws)
+    assert np.array_equal(e_h, e_d.cpu().numpy())
+    assert np.array_equal(g_h, g_d.cpu().numpy()[:, :B.max_params])
+
+
+# ------------------------------------------------------------------ uneven batch sizes
+def test_config2_instances_mixed_sizes():
+    picks = {}
+    ns, _ = synth.configs.config2_sizes()
+    for j in range(256):
+        n = int(ns[j])
+        if n not in picks:
+            picks[n] = j
+    assert set(picks) == {14, 16, 18, 20}
+    insts = [synth.config2_instance(picks[n]) for n in (14, 16)]
+    hams, ans, ths = [], [], []
+    for p, exc, th in insts:
+        hams.append(vq.Hamiltonian.from_problem(p))
+        ans.append(vq.Ansatz(p.n_qubits, synth.hf_bitstring(p.n_elec), exc))
+        ths.append(th)
+    B = vq.Batch(hams, ans)
+    ld = B.max_params
+    theta = np.zeros((len(insts), ld))
+    for i, th in enumerate(ths):
+        theta[i, :len(th)] = th
+    e, g = B.energy_grad(torch.as_tensor(theta).cuda())
+    e, g = e.cpu().numpy(), g.cpu().numpy()
+    rng = np.random.default_rng(0)
+    for i, (p, exc, th) in enumerate(insts):
+        idx = sorted(rng.choice(len(exc), size=6, replace=False).tolist())
+        e_o, g_o = oracle_eg(p, exc, th, indices=idx, full=False)
+        assert abs(e[i] - e_o) <= E_TOL
+        assert np.abs(g[i][idx] - g_o).max() <= G_TOL
+
+
+@pytest.mark.parametrize("n", [18, 20])
+def test_config2_large_instances_energy_and_sampled_gradient(n):
+    ns, _ = synth.configs.config2_sizes()
+    j = int(np.nonzero(ns == n)[0][0])
+    p, exc, th = synth.config2_instance(j)
+    e, g = gpu_eg(p, exc, th)
+    M = len(exc)
+    idx = [M - 40, M - 2, M - 1] if n == 18 else [M - 2, M - 1]
+    e_o, g_o = oracle_eg(p, exc, th, indices=idx, full=False)
+    assert abs(e - e_o) <= E_TOL
+    assert np.abs(g[idx] - g_o).max() <= G_TOL
+
+
+# ------------------------------------------------------------------ row-level checks
+@pytest.mark.parametrize("n_s,n_elec", [(2, 2), (4, 3), (6, 6), (7, 7)])
+def test_state_matches_oracle_and_sector(n_s, n_elec):
+    rng = np.random.default_rng(n_s * 10 + n_elec)
+    n = 2 * n_s
+    exc = synth.uccsd_pool(n, n_elec)
+    exc = exc[rng.integers(0, len(exc), size=min(300, 3 * len(exc)))]
+    th = rng.normal(0, 0.5, size=len(exc))
+    hf = synth.hf_bitstring(n_elec)
+    p = synth.random_problem(rng, n_s, n_elec, 2)
+    H = vq.Hamiltonian.from_problem(p)
+    A = vq.Ansatz(n, hf, exc)
+    psi = vq.state(A, H, th).cpu().numpy()
+    ref = oracle.prepare_state(n, hf, exc, th)
+    assert np.abs(psi - ref).max() <= 1e-12
+    assert abs(np.linalg.norm(psi) - 1.0) <= 1e-12
+    na, nb = synth.spin_counts(n_elec)
+    inside = np.zeros(1 << n, dtype=bool)
+    inside[oracle.sector_basis(n, na, nb).astype(np.int64)] = True
+    assert np.all(psi[~inside] == 0.0)
+
+
+def _sector_state(rng, n, n_elec, complex_amp=True):
+    na, nb = synth.spin_counts(n_elec)
+    basis = oracle.sector_basis(n, na, nb).astype(np.int64)
+    psi = np.zeros(1 << n, dtype=complex)
+    v = rng.normal(size=len(basis)) + (1j * rng.normal(size=len(basis)) if complex_amp else 0)
+    psi[basis] = v / np.linalg.norm(v)
+    return psi, basis
+
+
+@pytest.mark.parametrize("n,T,maxw", [(8, 60, None), (10, 200, 4), (12, 400, 6)])
+def test_apply_hamiltonian_random_pauli_sum(n, T, maxw):
+    """lambda = H psi on the sector for arbitrary Pauli sums (Y phases, wide X masks)."""
+    rng = np.random.default_rng(n + T)
+    xs, zs, cs = synth.random_pauli_terms(rng, n, T, max_weight=maxw)
+    n_elec = n // 2
+    psi, basis = _sector_state(rng, n, n_elec)
+    exc = synth.uccsd_pool(n, n_elec)[:3]
+    H = vq.Hamiltonian(n, xs, zs, cs)
+    A = vq.Ansatz(n, synth.hf_bitstring(n_elec), exc)
+    lam, e = vq.apply_hamiltonian(H, A, torch.as_tensor(psi).cuda())
+    lam = lam.cpu().numpy()
+    ref = oracle.pauli_sum_apply(xs, zs, cs, psi)
+    assert np.abs(lam[basis] - ref[basis]).max() <= 1e-12
+    outside = np.ones(1 << n, dtype=bool)
+    outside[basis] = False
+    assert np.all(lam[outside] == 0)
+    assert abs(float(e) - np.vdot(psi, ref).real) <= E_TOL
+
+
+@pytest.mark.parametrize("n,T", [(8, 80), (10, 150)])
+def test_energy_gradient_random_pauli_sum(n, T):
+    rng = np.random.default_rng(3 * n + T)
+    xs, zs, cs = synth.random_pauli_terms(rng, n, T, max_weight=5)
+    n_elec = n // 2
+    exc = synth.uccsd_pool(n, n_elec)
+    th = rng.normal(0, 0.4, size=len(exc))
+    hf = synth.hf_bitstring(n_elec)
+    model = oracle.EnergyModel.from_pauli(n, xs, zs, cs)
+    e_o, g_o = oracle.gradient_direct(model, hf, exc, th)
+    H = vq.Hamiltonian(n, xs, zs, cs)
+    A = vq.Ansatz(n, hf, exc)
+    for flags in (0, vq.VQE_FLAG_FORCE_STREAMING, vq.VQE_FLAG_FORCE_COMPLEX):
+        old = vq.set_flags(flags)
+        try:
+            e, g = vq.energy_grad(H, A, th)
+        finally:
+            vq.set_flags(old)
+        assert abs(float(e) - e_o) <= E_TOL
+        assert np.abs(g.cpu().numpy() - g_o).max() <= G_TOL
+
+
+# ------------------------------------------------------------------ edge cases
+def test_no_excitations_gives_hf_energy():
+    p = synth.random_problem(np.random.default_rng(5), 4, 4, 3)
+    H = vq.Hamiltonian.from_problem(p)
+    A = vq.Ansatz(8, 15, np.zeros((0, 4), dtype=np.int32))
+    e = float(vq.energy(H, A, np.zeros(0)))
+    e_o = oracle.energy(oracle.EnergyModel.from_problem(p), 15, [], [])
+    assert abs(e - e_o) <= E_TOL
+
+
+def test_identity_only_hamiltonian_and_dropped_terms():
+    n = 6
+    A = vq.Ansatz(n, 7, synth.uccsd_pool(n, 3))
+    th = np.random.default_rng(1).normal(size=A.n_params)
+    H = vq.Hamiltonian(n, [0], [0], [2.5])
+    e, g = vq.energy_grad(H, A, th)
+    assert abs(float(e) - 2.5) <= 1e-12 and np.abs(g.cpu().numpy()).max() <= 1e-12
+    H0 = vq.Hamiltonian(n, [3, 3], [0, 0], [1e-20, -1e-20], drop_tol=1e-16)
+    e0, g0 = vq.energy_grad(H0, A, th)
+    assert float(e0) == 0.0 and np.all(g0.cpu().numpy() == 0.0)
+
+
+def test_non_spin_conserving_excitations_use_number_sector():
+    rng = np.random.default_rng(9)
+    p = synth.random_problem(rng, 3, 2, 2)
+    exc = np.array([[0, 3, -1, -1], [1, 2, -1, -1], [0, 1, 4, 5], [0, 4, -1, -1]], dtype=np.int32)
+    th = rng.normal(size=4)
+    model = oracle.EnergyModel.from_problem(p, full=True)
+    e_o, g_o = oracle.gradient_direct(model, 3, exc, th)
+    for flags in (0, vq.VQE_FLAG_FORCE_STREAMING):
+        e, g = gpu_eg(p, exc, th, flags=flags)
+        assert abs(e - e_o) <= E_TOL and np.abs(g - g_o).max() <= G_TOL
+
+
+def test_unsorted_double_indices_follow_operator_order():
+    """{i, j, a, b} is T = a+_a a+_b a_j a_i as given, also when i > j or a > b."""
+    rng = np.random.default_rng(12)
+    p = synth.random_problem(rng, 3, 2, 2)
+    exc = np.array([[1, 0, 2, 3], [0, 1, 5, 4], [1, 0, 3, 2]], dtype=np.int32)
+    th = rng.normal(size=3)
+    e_o, g_o = oracle.gradient_direct(oracle.EnergyModel.from_problem(p), 3, exc, th)
+    e, g = gpu_eg(p, exc, th)
+    assert abs(e - e_o) <= E_TOL and np.abs(g - g_o).max() <= G_TOL
+
+
+def test_invalid_arguments_raise():
+    with pytest.raises(vq.VQEError):
+        vq.Hamiltonian(4, [1 << 4], [0], [1.0])
+    with pytest.raises(vq.VQEError):
+        vq.Ansatz(4, 3, [[0, 0, -1, -1]])
+    H = vq.Hamiltonian(4, [0], [1], [1.0])
+    A = vq.Ansatz(6, 3, [[0, 2, -1, -1]])
+    with pytest.raises(vq.VQEError):
+        vq.energy(H, A, np.zeros(1))
+    A4 = vq.Ansatz(4, 3, [[0, 2, -1, -1]])
+    with pytest.raises(vq.VQEError):
+        vq.set_flags(vq.VQE_FLAG_FORCE_STREAMING)
+        try:
+            vq.api._check(vq.load().vqe_energy(H.handle, A4.handle, None, None, None, 0, None))
+        finally:
+            vq.set_flags(0)
+
+
+def test_autograd_function():
+    w = synth.config0()
+    p, exc, th = w.problems[0], w.excitations[0], w.thetas[0]
+    H = vq.Hamiltonian.from_problem(p)
+    A = vq.Ansatz(4, 3, exc)
+    t = torch.as_tensor(th).cuda().requires_grad_(True)
+    e = vq.vqe_energy(t, H, A)
+    (3.0 * e).backward()
+    e_o, g_o = oracle_eg(p, exc, th)
+    assert abs(float(e) - e_o) <= E_TOL
+    assert np.abs(t.grad.cpu().numpy() - 3.0 * g_o).max() <= 3 * G_TOL

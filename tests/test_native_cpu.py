@@ -1,0 +1,100 @@
+"""Host-side checks of libvqe that need no GPU: the library builds and loads,
+exports every function include/vqe.h declares, its Jordan-Wigner mapping agrees
+with the oracle's independent one, and it rejects bad arguments."""
+import ctypes
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+from paper_2311_01242_gb300 import _native, api
+
+
+@pytest.fixture(scope="module")
+def lib():
+    _native.build()
+    return _native.load()
+
+
+def test_exports_every_declared_symbol(lib):
+    names = _native.declared_symbols()
+    assert len(names) >= 20
+    for name in names:
+        assert hasattr(lib, name), name
+    assert set(names) == set(_native.PROTOTYPES), set(names) ^ set(_native.PROTOTYPES)
+
+
+def test_version_and_error_message(lib):
+    assert lib.vqe_version() >= 100
+    assert isinstance(lib.vqe_last_error(), bytes)
+
+
+@pytest.mark.parametrize("seed,n_s,n_elec", [(0, 2, 2), (1, 3, 2), (2, 4, 4), (3, 6, 6)])
+def test_jordan_wigner_matches_oracle(lib, seed, n_s, n_elec):
+    prob = synth.random_problem(np.random.default_rng(seed), n_s, n_elec, 3)
+    x1, z1, c1 = api.jordan_wigner(prob.n_spatial, prob.h, prob.eri)
+    x2, z2, c2 = oracle.jordan_wigner(prob)
+    assert np.array_equal(x1, x2) and np.array_equal(z1, z2)
+    assert np.abs(c1 - c2).max() < 1e-12
+
+
+def test_jordan_wigner_config1_and_drop(lib):
+    prob = synth.config1(1).problems[0]
+    x1, z1, c1 = api.jordan_wigner(prob.n_spatial, prob.h, prob.eri)
+    x2, z2, c2 = oracle.jordan_wigner(prob)
+    assert len(x1) == len(x2) == 1819 and len(set(x1.tolist())) == 286
+    assert np.abs(c1 - c2).max() < 1e-12
+    xd, zd, cd = api.jordan_wigner(prob.n_spatial, prob.h, prob.eri, 0.0, 1e-2)
+    keep = np.abs(c2) >= 1e-2
+    assert np.array_equal(xd, x2[keep]) and np.array_equal(zd, z2[keep])
+
+
+def test_jordan_wigner_constant_and_capacity(lib):
+    prob = synth.config0().problems[0]
+    x, z, c = api.jordan_wigner(2, prob.h, prob.eri, c0=1.25)
+    x0, z0, c0 = api.jordan_wigner(2, prob.h, prob.eri, c0=0.0)
+    ident = (x == 0) & (z == 0)
+    ident0 = (x0 == 0) & (z0 == 0)
+    assert abs(c[ident][0] - c0[ident0][0] - 1.25) < 1e-14
+    n = ctypes.c_int64(0)
+    h = np.ascontiguousarray(prob.h)
+    e = np.ascontiguousarray(prob.eri)
+    rc = lib.vqe_jordan_wigner(2, api._ptr(h), api._ptr(e), 0.0, 0.0, 3, None, None, None, ctypes.byref(n))
+    assert rc == 1 and n.value == len(x0)
+
+
+def test_jordan_wigner_rejects_bad_input(lib):
+    n = ctypes.c_int64(0)
+    h = np.zeros((2, 2))
+    e = np.zeros((2, 2, 2, 2))
+    assert lib.vqe_jordan_wigner(0, api._ptr(h), api._ptr(e), 0.0, 0.0, 0, None, None, None,
+                                 ctypes.byref(n)) == 1
+    hn = h.copy()
+    hn[0, 1] = np.nan
+    assert lib.vqe_jordan_wigner(2, api._ptr(hn), api._ptr(e), 0.0, 0.0, 0, None, None, None,
+                                 ctypes.byref(n)) == 1
+    assert b"non-finite" in lib.vqe_last_error()
+    # an antisymmetric one-body matrix maps to imaginary coefficients
+    ha = np.array([[0.0, 1.0], [-1.0, 0.0]])
+    assert lib.vqe_jordan_wigner(2, api._ptr(ha), api._ptr(e), 0.0, 0.0, 0, None, None, None,
+                                 ctypes.byref(n)) == 5
+
+
+def test_create_rejects_invalid_arguments_before_device_work(lib):
+    h = ctypes.c_void_p()
+    xs = np.array([1 << 5], dtype=np.uint64)
+    zs = np.array([0], dtype=np.uint64)
+    cs = np.array([1.0])
+    assert lib.vqe_create_hamiltonian(4, 1, api._ptr(xs), api._ptr(zs), api._ptr(cs), 0.0,
+                                      ctypes.byref(h)) == 1
+    assert b"mask bit" in lib.vqe_last_error()
+    assert lib.vqe_create_hamiltonian(33, 1, api._ptr(xs), api._ptr(zs), api._ptr(cs), 0.0,
+                                      ctypes.byref(h)) == 1
+    a = ctypes.c_void_p()
+    exc = np.array([[0, 1, 1, 2]], dtype=np.int32)
+    assert lib.vqe_create_ansatz(4, 3, 1, api._ptr(exc), ctypes.byref(a)) == 1
+    assert b"repeats" in lib.vqe_last_error()
+    exc = np.array([[0, 7, -1, -1]], dtype=np.int32)
+    assert lib.vqe_create_ansatz(4, 3, 1, api._ptr(exc), ctypes.byref(a)) == 1
+    assert lib.vqe_create_ansatz(4, 1 << 6, 0, None, ctypes.byref(a)) == 1
