@@ -216,6 +216,29 @@ int vqe_batch_energy_grad_host(vqe_batch_t b, const double* theta_host, int64_t 
 void vqe_destroy_batch(vqe_batch_t b);
 
 /*
+ * Energy (and gradient when grad_dev != NULL) with no device allocation at all.
+ * The paper has no counterpart; this exists for callers that may not call
+ * cudaMalloc: code that runs inside another framework whose allocator owns the
+ * device memory (a raw allocation would escape its pool and its accounting),
+ * or a service whose device-memory budget is fixed when the process starts.
+ * The caller passes theta, the energy and the gradient as for vqe_energy_grad;
+ * the scratch comes from one static device array of VQE_NOALLOC_SCRATCH_BYTES
+ * that every GPU loading this library keeps until the process exits.
+ * Limit: instances whose streaming workspace (two 2^n vectors of 8-byte real
+ * amplitudes, the cos/sin table and 8 KiB of partials per parameter) exceeds
+ * that size are rejected with VQE_ERR_INVALID_ARG and a message; for example
+ * 18 qubits with 512 parameters fits, 20 qubits does not.
+ * The first call on each device looks up the array's device address (with the
+ * device current); make that first call before any stream capture. All calls
+ * share the array and it keeps the last call's contents; each call writes every
+ * scratch entry it reads, so nothing needs clearing, but calls that overlap on
+ * the GPU (other streams or threads) race on it. Asynchronous on `stream`.
+ */
+#define VQE_NOALLOC_SCRATCH_BYTES (16u * 1024u * 1024u)
+int vqe_energy_grad_noalloc(vqe_hamiltonian_t h, vqe_ansatz_t a, const double* theta_dev,
+                            double* energy_dev, double* grad_dev, vqe_stream_t stream);
+
+/*
  * Algorithmic work of one energy(+gradient) evaluation, counted exactly on the
  * host from the tables: FP64 flops (an FMA counts 2) and the bytes of state
  * vector a streaming implementation must move. Used for roofline reports.

@@ -427,6 +427,33 @@ int run_single(vqe_hamiltonian_t h, vqe_ansatz_t a, const double* theta, double*
 
 }  // namespace
 
+namespace vqe {
+
+// Descriptor, streaming plan and scratch layout for vqe_energy_grad_noalloc:
+// scan-mode H psi (no connectivity table is built or used), real amplitudes
+// unless complex arithmetic is forced. Allocates no device memory.
+int prepare_noalloc(vqe_hamiltonian_s* h, vqe_ansatz_s* a, bool with_grad, InstDesc* d, StreamPlan* sp,
+                    bool* real, size_t off[5], size_t* need) {
+  const int rc = check_pair(h, a);
+  if (rc) return rc;
+  *real = use_real();
+  const vqe_hamiltonian_s::Ell none;
+  *d = make_desc(h, a, &none, 0);
+  *sp = plan(a, &none);
+  const WsLayout L = ws_layout(a, !*real, with_grad);
+  off[0] = L.psi;
+  off[1] = L.lam;
+  off[2] = L.cs;
+  off[3] = L.epart;
+  off[4] = L.gpart;
+  *need = L.total;
+  return VQE_OK;
+}
+
+int set_error(int code, const char* msg) { return fail(code, msg); }
+
+}  // namespace vqe
+
 // ------------------------------------------------------------------ C ABI
 extern "C" {
 

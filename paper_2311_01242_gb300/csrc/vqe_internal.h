@@ -2,8 +2,12 @@
 // (vqe_kernels.cu) of libvqe. Not part of the C ABI.
 #pragma once
 
+#include <cstddef>
 #include <cstdint>
 #include <cuda_runtime.h>
+
+struct vqe_hamiltonian_s;
+struct vqe_ansatz_s;
 
 namespace vqe {
 
@@ -104,5 +108,10 @@ cudaError_t stream_state(const InstDesc& d, const StreamPlan& sp, const StreamBu
 cudaError_t stream_apply_h(const InstDesc& d, const StreamPlan& sp, const StreamBuffers& b,
                            const double* psi_in, double* lam_out, double* energy,
                            cudaStream_t stream);
+
+// Host helpers for the allocation-free entry point (vqe_static.cu).
+int prepare_noalloc(vqe_hamiltonian_s* h, vqe_ansatz_s* a, bool with_grad, InstDesc* d, StreamPlan* sp,
+                    bool* real, size_t off[5], size_t* need);
+int set_error(int code, const char* msg);
 
 }  // namespace vqe
