@@ -183,6 +183,7 @@ struct vqe_batch_s {
   std::vector<vqe_hamiltonian_t> hams;
   std::vector<vqe_ansatz_t> ans;
   std::vector<InstDesc> descs;          // host copies, device pointers inside
+  std::vector<InstDesc> res_descs[2];   // resident descriptors per mode, staging fields set
   std::vector<int> resident[2];         // instance indices per mode (0 real, 1 complex)
   std::vector<int> streaming[2];
   InstDesc* d_res[2] = {nullptr, nullptr};
@@ -309,23 +310,36 @@ InstDesc make_desc(vqe_hamiltonian_t h, vqe_ansatz_t a, const vqe_hamiltonian_s:
   d.cvals = h->d_cvals;
   d.ell = e->d_ell;
   d.inst = inst;
+  d.E = int32_t(h->emask.size());
+  d.S = int32_t(h->cvals.size());
+  d.stage_tables = 0;
+  d.sweep_threads = 128;
   return d;
 }
 
 bool use_real() { return (g_flags & VQE_FLAG_FORCE_COMPLEX) == 0; }
 
-size_t resident_bytes(vqe_ansatz_t a, bool real) {
-  return vqe::resident_smem_bytes(a->n, a->M, int64_t(a->pairs.size()), real);
-}
-
-bool resident_ok(vqe_ansatz_t a, const vqe_hamiltonian_s::Ell* e, bool real) {
+// Whether an instance fits the shared-memory-resident kernel in this mode; if
+// so, sets the shared-memory bytes and the descriptor's staging/sweep fields.
+bool resident_fit(vqe_ansatz_t a, const vqe_hamiltonian_s::Ell* e, bool real, InstDesc* d, size_t* smem) {
   if (g_flags & VQE_FLAG_FORCE_STREAMING) return false;
-  if (!e->use_ell) return false;
+  if (!e->use_ell || a->n > 16) return false;
+  if (a->pairs.size() > (size_t(1) << 24) || d->S > (1 << 24) || d->G > (1 << 20)) return false;
   int dev = 0, optin = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return false;
   if (cudaDeviceGetAttribute(&optin, cudaDevAttrMaxSharedMemoryPerBlockOptin, dev) != cudaSuccess)
     return false;
-  return resident_bytes(a, real) <= size_t(optin);
+  const int P = int(a->pairs.size());
+  for (int stage = 1; stage >= 0; --stage) {
+    const vqe::ResidentLayout L = vqe::resident_layout(a->n, a->M, P, d->G, d->E, d->S, real, stage != 0);
+    if (L.total <= uint32_t(optin)) {
+      d->stage_tables = stage;
+      d->sweep_threads = 128;
+      *smem = L.total;
+      return true;
+    }
+  }
+  return false;
 }
 
 struct WsLayout {
@@ -409,8 +423,8 @@ int run_single(vqe_hamiltonian_t h, vqe_ansatz_t a, const double* theta, double*
   if (!e) return rc;
   const bool real = use_real();
   InstDesc d = make_desc(h, a, e, 0);
-  if (resident_ok(a, e, real)) {
-    const size_t smem = resident_bytes(a, real);
+  size_t smem = 0;
+  if (resident_fit(a, e, real, &d, &smem)) {
     if ((rc = ensure_smem(smem, real))) return rc;
     cudaError_t ce = vqe::launch_resident(nullptr, &d, 1, smem, real, with_grad, theta, 0, energy, grad, 0,
                                           stream);
@@ -851,18 +865,19 @@ int vqe_create_batch(int n_inst, const vqe_hamiltonian_t* hams, const vqe_ansatz
     B->max_params = std::max(B->max_params, ans[i]->M);
     for (int mode = 0; mode < 2; ++mode) {
       const bool real = mode == 0;
-      if (resident_ok(ans[i], e, real)) {
+      InstDesc d = B->descs.back();
+      size_t smem = 0;
+      if (resident_fit(ans[i], e, real, &d, &smem)) {
         B->resident[mode].push_back(i);
-        B->res_smem[mode] = std::max(B->res_smem[mode], resident_bytes(ans[i], real));
+        B->res_descs[mode].push_back(d);
+        B->res_smem[mode] = std::max(B->res_smem[mode], smem);
       } else {
         B->streaming[mode].push_back(i);
       }
     }
   }
   for (int mode = 0; mode < 2; ++mode) {
-    std::vector<InstDesc> v;
-    for (int i : B->resident[mode]) v.push_back(B->descs[i]);
-    int rc = upload(v, &B->d_res[mode]);
+    int rc = upload(B->res_descs[mode], &B->d_res[mode]);
     if (rc) return rc;
   }
   *out = B.release();

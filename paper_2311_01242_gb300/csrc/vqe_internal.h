@@ -61,12 +61,46 @@ struct InstDesc {
   const uint32_t* ell;       // [W][D] column-major: groups connected to each output
   // row of this instance in the caller's theta / energy / gradient arrays
   int64_t inst;
+  int32_t E, S;              // folded entries and value slots of the Hamiltonian
+  int32_t stage_tables;      // resident kernel: copy the group tables to shared memory
+  int32_t sweep_threads;     // resident kernel: threads that run the gate sweeps
 };
 
-// Shared-memory bytes the resident kernel needs for an instance.
-inline size_t resident_smem_bytes(int n, int M, int64_t total_pairs, bool real) {
-  size_t amp = real ? 8 : 16;
-  return 2 * (size_t(1) << n) * amp + size_t(total_pairs) * 8 + size_t(M) * 16 + 64 * 8;
+// Shared-memory layout of the resident kernel (byte offsets), computed the same
+// way on the host (to size the launch) and on the device (to carve it).
+struct ResidentLayout {
+  uint32_t psi, lam, cs, gates, poff, pairs, uni, red, total;
+};
+
+__host__ __device__ inline uint32_t align_up(uint32_t v, uint32_t a) { return (v + a - 1) / a * a; }
+
+// Table part of the union region: groups, then entry masks, then values.
+__host__ __device__ inline uint32_t staged_table_bytes(int G, int E, int S, bool real) {
+  return uint32_t(G) * 32u + align_up(uint32_t(E) * 4u, 16u) + uint32_t(S) * (real ? 8u : 16u);
+}
+
+__host__ __device__ inline ResidentLayout resident_layout(int n, int M, int P, int G, int E, int S,
+                                                          bool real, bool stage) {
+  ResidentLayout L;
+  const uint32_t amp = real ? 8u : 16u, dim = 1u << n;
+  L.psi = 0;
+  L.lam = dim * amp;
+  uint32_t o = 2u * dim * amp;
+  L.cs = align_up(o, 16u);
+  o = L.cs + uint32_t(M) * 16u;
+  L.gates = align_up(o, 16u);
+  o = L.gates + uint32_t(M) * 16u;
+  L.poff = o;
+  o += uint32_t(M + 1) * 4u;
+  L.pairs = align_up(o, 16u);
+  o = L.pairs + uint32_t(P) * 4u;
+  L.uni = align_up(o, 16u);
+  const uint32_t gb = uint32_t(P) * 8u;  // per-pair gradient contributions (reverse sweep)
+  const uint32_t tb = stage ? staged_table_bytes(G, E, S, real) : 0u;  // tables (H psi)
+  o = L.uni + (gb > tb ? gb : tb);
+  L.red = align_up(o, 16u);
+  L.total = L.red + 64u * 8u;
+  return L;
 }
 
 // Kernel launchers (vqe_kernels.cu). All are asynchronous on `stream`.

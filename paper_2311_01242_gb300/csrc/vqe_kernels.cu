@@ -151,9 +151,55 @@ __device__ double block_sum(double v, double* red) {
 }
 
 // ---------------------------------------------------------------- resident kernel
-// One CTA evaluates one instance with psi and lambda in shared memory: HF init,
-// forward sweep, H psi with the energy, and the reverse sweep with per-pair
-// gradient contributions that are summed per gate in pair order at the end.
+// Folded group coefficient from explicit tables (shared or global memory).
+template <bool REAL>
+__device__ __forceinline__ typename Amp<REAL>::C group_coef_tab(const GroupRec& g, const uint32_t* emask,
+                                                                const typename Amp<REAL>::C* vals,
+                                                                uint32_t src) {
+  typedef typename Amp<REAL>::C C;
+  const uint32_t u = pattern_of(src, g.upos, g.ubits);
+  const C* vp = vals + g.vbeg + u;
+  C f = sflip(vp[0], parity32(src & emask[g.ebeg]));
+  for (int e = g.ebeg + 1, j = 1; e < g.eend; ++e, ++j) {
+    const C v = sflip(vp[j << g.ubits], parity32(src & emask[e]));
+    if constexpr (REAL) {
+      f += v;
+    } else {
+      f.x += v.x;
+      f.y += v.y;
+    }
+  }
+  return f;
+}
+
+__device__ __forceinline__ GroupRec load_group_any(const GroupRec* p) {
+  const int4* q = reinterpret_cast<const int4*>(p);
+  const int4 a = q[0];
+  const int4 b = q[1];
+  GroupRec g;
+  g.x = uint32_t(a.x);
+  g.upos = uint32_t(a.y);
+  g.ebeg = a.z;
+  g.eend = a.w;
+  g.vbeg = b.x;
+  g.ubits = b.y;
+  g.pad0 = g.pad1 = 0;
+  return g;
+}
+
+__device__ __forceinline__ void sweep_barrier(int nthreads) {
+  asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
+}
+
+// One CTA evaluates one instance with psi and lambda in shared memory: HF
+// init, forward sweep, H psi with the energy, and the reverse sweep with
+// per-pair gradient contributions summed per gate in pair order at the end.
+// Gate records, cos/sin, pair offsets and pair lists are staged in shared
+// memory first. The sweeps run on the first `sweep_threads` threads (one warp
+// per SM sub-partition or more) with a named barrier between gates; the
+// instance's pairs are dealt round-robin over those warps. The H psi tables
+// are staged into the region the reverse sweep later uses for its per-pair
+// contributions, when they fit.
 template <bool REAL>
 __global__ void __launch_bounds__(kResidentThreads, 1)
 k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double* __restrict__ theta,
@@ -161,26 +207,42 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
            int with_grad) {
   typedef Amp<REAL> A;
   typedef typename A::T T;
+  typedef typename A::C C;
   extern __shared__ __align__(16) unsigned char smem[];
-  const InstDesc& d = descs ? descs[blockIdx.x] : one;
+  InstDesc d;
+  if (descs) {
+    d = descs[blockIdx.x];
+  } else {
+    d = one;
+  }
   const int tid = threadIdx.x, bs = blockDim.x;
-  const int n = d.n, M = d.M;
+  const int n = d.n, M = d.M, G = d.G, W = d.W;
   const uint32_t dim = 1u << n;
-  const int64_t D = d.D;
-  const int64_t P = d.pair_off[M];
-  T* psi = reinterpret_cast<T*>(smem);
-  T* lam = psi + dim;
-  double2* cs = reinterpret_cast<double2*>(lam + dim);
-  double* gbuf = reinterpret_cast<double*>(cs + M);
-  double* red = gbuf + P;
+  const int D = int(d.D);
+  const int P = int(d.pair_off[M]);
+  const bool stage = d.stage_tables != 0;
+  const int sw = d.sweep_threads;
+  const ResidentLayout L = resident_layout(n, M, P, G, d.E, d.S, REAL, stage);
+  T* psi = reinterpret_cast<T*>(smem + L.psi);
+  T* lam = reinterpret_cast<T*>(smem + L.lam);
+  double2* cs = reinterpret_cast<double2*>(smem + L.cs);
+  GateRec* gates = reinterpret_cast<GateRec*>(smem + L.gates);
+  int32_t* poff = reinterpret_cast<int32_t*>(smem + L.poff);
+  uint32_t* pairs = reinterpret_cast<uint32_t*>(smem + L.pairs);
+  double* gbuf = reinterpret_cast<double*>(smem + L.uni);
+  double* red = reinterpret_cast<double*>(smem + L.red);
   const int64_t row = d.inst;
   const double* th = theta + row * ld_theta;
 
+  // stage ansatz tables, clear the state
   for (int m = tid; m < M; m += bs) {
     double s, c;
     sincos(th[m], &s, &c);
     cs[m] = make_double2(c, s);
+    gates[m] = load_gate(d.gates + m);
   }
+  for (int m = tid; m <= M; m += bs) poff[m] = int32_t(__ldg(d.pair_off + m));
+  for (int p = tid; p < P; p += bs) pairs[p] = __ldg(d.pairs + p);
   for (uint32_t k = tid; k < dim; k += bs) {
     psi[k] = A::zero();
     lam[k] = A::zero();
@@ -189,35 +251,62 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
   if (tid == 0) psi[d.hf] = A::unit();
   __syncthreads();
 
+  // lane-interleaved position of this thread in the sweep: consecutive pairs go
+  // to consecutive warps so every sub-partition gets FP64 work on small gates
+  const int swarps = sw >> 5;
+  const int spos = (tid & 31) * swarps + (tid >> 5);
+
   // a2: forward sweep
-  for (int m = 0; m < M; ++m) {
-    const GateRec gr = load_gate(d.gates + m);
-    const int64_t p0 = __ldg(d.pair_off + m), p1 = __ldg(d.pair_off + m + 1);
-    const double2 c_s = cs[m];
-    const int s0 = gr.sign0 < 0;
-    for (int64_t p = p0 + tid; p < p1; p += bs) {
-      const uint32_t k = __ldg(d.pairs + p);
-      const uint32_t k2 = k ^ gr.flip;
-      const double ss = sflip(c_s.y, parity32(k & gr.par) ^ s0);
-      T a = psi[k], b = psi[k2];
-      A::rot(a, b, c_s.x, ss);
-      psi[k] = a;
-      psi[k2] = b;
+  if (tid < sw) {
+    for (int m = 0; m < M; ++m) {
+      const GateRec gr = gates[m];
+      const int p0 = poff[m], cnt = poff[m + 1] - p0;
+      const double2 c_s = cs[m];
+      const int s0 = gr.sign0 < 0;
+      for (int q = spos; q < cnt; q += sw) {
+        const uint32_t k = pairs[p0 + q];
+        const uint32_t k2 = k ^ gr.flip;
+        const double ss = sflip(c_s.y, parity32(k & gr.par) ^ s0);
+        T a = psi[k], b = psi[k2];
+        A::rot(a, b, c_s.x, ss);
+        psi[k] = a;
+        psi[k2] = b;
+      }
+      sweep_barrier(sw);
     }
-    __syncthreads();
   }
+  // stage the H psi tables into the union region
+  const GroupRec* tg = d.groups;
+  const uint32_t* te = d.emask;
+  const C* tv;
+  if constexpr (REAL) tv = d.vals; else tv = d.cvals;
+  if (stage) {
+    GroupRec* sg = reinterpret_cast<GroupRec*>(smem + L.uni);
+    uint32_t* se = reinterpret_cast<uint32_t*>(smem + L.uni + uint32_t(G) * 32u);
+    C* sv = reinterpret_cast<C*>(smem + L.uni + uint32_t(G) * 32u + align_up(uint32_t(d.E) * 4u, 16u));
+    const int4* gsrc = reinterpret_cast<const int4*>(d.groups);
+    int4* gdst = reinterpret_cast<int4*>(sg);
+    for (int i = tid; i < 2 * G; i += bs) gdst[i] = __ldg(gsrc + i);
+    for (int i = tid; i < d.E; i += bs) se[i] = __ldg(d.emask + i);
+    for (int i = tid; i < d.S; i += bs) sv[i] = A::coef(d, i);
+    tg = sg;
+    te = se;
+    tv = sv;
+  }
+  __syncthreads();
 
   // a3: lambda = H psi on the sector, E = <psi|lambda>
   double e_part = 0.0;
-  for (int64_t r = tid; r < D; r += bs) {
+  for (int r = tid; r < D; r += bs) {
     const uint32_t k = __ldg(d.sector + r);
     T acc = A::zero();
-    for (int j = 0; j < d.W; ++j) {
-      const uint32_t gi = __ldg(d.ell + int64_t(j) * D + r);
-      if (gi == kEllPad) break;
-      const GroupRec g = load_group(d.groups + gi);
+    uint32_t gi = W > 0 ? __ldg(d.ell + r) : kEllPad;
+    for (int j = 0; j < W && gi != kEllPad; ++j) {
+      const uint32_t gnext = (j + 1 < W) ? __ldg(d.ell + int64_t(j + 1) * D + r) : kEllPad;
+      const GroupRec g = load_group_any(tg + gi);
       const uint32_t src = k ^ g.x;
-      A::mac(acc, group_coef<REAL>(d, g, src), psi[src]);
+      A::mac(acc, group_coef_tab<REAL>(g, te, tv, src), psi[src]);
+      gi = gnext;
     }
     lam[k] = acc;
     e_part += A::redot(psi[k], acc);
@@ -229,32 +318,35 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
   if (!with_grad) return;
 
   // a4: reverse sweep
-  for (int m = M - 1; m >= 0; --m) {
-    const GateRec gr = load_gate(d.gates + m);
-    const int64_t p0 = __ldg(d.pair_off + m), p1 = __ldg(d.pair_off + m + 1);
-    const double2 c_s = cs[m];
-    const int s0 = gr.sign0 < 0;
-    for (int64_t p = p0 + tid; p < p1; p += bs) {
-      const uint32_t k = __ldg(d.pairs + p);
-      const uint32_t k2 = k ^ gr.flip;
-      const int sb = parity32(k & gr.par) ^ s0;
-      const double ss = sflip(c_s.y, sb);
-      T pa = psi[k], pb = psi[k2], la = lam[k], lb = lam[k2];
-      gbuf[p] = sflip(A::redot(lb, pa) - A::redot(la, pb), sb);
-      A::rot(pa, pb, c_s.x, -ss);
-      A::rot(la, lb, c_s.x, -ss);
-      psi[k] = pa;
-      psi[k2] = pb;
-      lam[k] = la;
-      lam[k2] = lb;
+  if (tid < sw) {
+    for (int m = M - 1; m >= 0; --m) {
+      const GateRec gr = gates[m];
+      const int p0 = poff[m], cnt = poff[m + 1] - p0;
+      const double2 c_s = cs[m];
+      const int s0 = gr.sign0 < 0;
+      for (int q = spos; q < cnt; q += sw) {
+        const uint32_t k = pairs[p0 + q];
+        const uint32_t k2 = k ^ gr.flip;
+        const int sb = parity32(k & gr.par) ^ s0;
+        const double ss = sflip(c_s.y, sb);
+        T pa = psi[k], pb = psi[k2], la = lam[k], lb = lam[k2];
+        gbuf[p0 + q] = sflip(A::redot(lb, pa) - A::redot(la, pb), sb);
+        A::rot(pa, pb, c_s.x, -ss);
+        A::rot(la, lb, c_s.x, -ss);
+        psi[k] = pa;
+        psi[k2] = pb;
+        lam[k] = la;
+        lam[k2] = lb;
+      }
+      sweep_barrier(sw);
     }
-    __syncthreads();
   }
+  __syncthreads();
   double* g_out = grad + row * ld_grad;
   for (int m = tid; m < M; m += bs) {
-    const int64_t p0 = __ldg(d.pair_off + m), p1 = __ldg(d.pair_off + m + 1);
+    const int p0 = poff[m], p1 = poff[m + 1];
     double s = 0.0;
-    for (int64_t p = p0; p < p1; ++p) s += gbuf[p];
+    for (int p = p0; p < p1; ++p) s += gbuf[p];
     g_out[m] = 2.0 * s;
   }
 }
