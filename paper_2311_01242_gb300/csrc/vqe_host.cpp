@@ -196,6 +196,14 @@ struct vqe_batch_s {
 
 namespace {
 
+// FP64 additions the kernels spend on one group's coefficient for a source index.
+double fp64_adds(vqe_hamiltonian_t h, int g, uint32_t src) {
+  const GroupRec& r = h->groups[g];
+  if (r.kind == 0) return double(r.eend - r.ebeg - 1);
+  const int k = pc32(src & h->emask[r.ebeg + 1]);
+  return r.kind == 1 ? double(k) : double(k + k * (k - 1) / 2);
+}
+
 const vqe_hamiltonian_s::Ell* get_ell(vqe_hamiltonian_t h, vqe_ansatz_t a, int* err) {
   *err = VQE_OK;
   std::lock_guard<std::mutex> lock(h->mu);
@@ -249,7 +257,7 @@ const vqe_hamiltonian_s::Ell* get_ell(vqe_hamiltonian_t h, vqe_ansatz_t a, int* 
             const int g = order[oi];
             if (inside(k ^ h->groups[g].x)) {
               ell[size_t(j) * size_t(D) + size_t(r)] = uint32_t(g);
-              ex += h->groups[g].eend - h->groups[g].ebeg - 1;
+              ex += fp64_adds(h, g, k ^ h->groups[g].x);
               ++j;
             }
           }
@@ -278,7 +286,7 @@ const vqe_hamiltonian_s::Ell* get_ell(vqe_hamiltonian_t h, vqe_ansatz_t a, int* 
       for (int g = 0; g < G; ++g)
         if (inside(k ^ h->groups[g].x)) {
           nnz += 1;
-          ex += h->groups[g].eend - h->groups[g].ebeg - 1;
+          ex += fp64_adds(h, g, k ^ h->groups[g].x);
         }
       ++sampled;
     }
@@ -594,11 +602,68 @@ int vqe_create_hamiltonian(int n_qubits, int64_t n_terms, const uint64_t* xs, co
         tab[u] += (pc32(bits & z) & 1) ? -cp : cp;
       }
     }
+    // Evaluation form (see GroupRec::kind): the entry form, or the occupation
+    // form when every entry's Z mask differs from a base mask z0 by at most one
+    // bit (linear in the occupations) or, for a single pattern, by at most two
+    // bits (quadratic), using (-1)^{n_r} = 1 - 2 n_r.
+    int best_w = 99;
+    uint32_t z0 = 0;
+    for (const auto& cand : entries) {
+      int w = 0;
+      for (const auto& other : entries) w = std::max(w, pc32(other.first ^ cand.first));
+      if (w < best_w) {
+        best_w = w;
+        z0 = cand.first;
+      }
+    }
+    int kind = 0;
+    if (entries.size() > 2 && best_w <= 1)
+      kind = 1;
+    else if (entries.size() > 3 && ub == 0 && best_w <= 2)
+      kind = 2;
+    g.kind = kind;
+    g.nq = n_qubits;
     g.ebeg = int32_t(H->emask.size());
     g.vbeg = int32_t(H->cvals.size());
-    for (const auto& kv : entries) {
-      H->emask.push_back(kv.first);
-      for (int u = 0; u < nu; ++u) H->cvals.push_back(kv.second[u]);
+    if (kind == 0) {
+      for (const auto& kv : entries) {
+        H->emask.push_back(kv.first);
+        for (int u = 0; u < nu; ++u) H->cvals.push_back(kv.second[u]);
+      }
+    } else {
+      uint32_t R = 0;
+      for (const auto& kv : entries) R |= kv.first ^ z0;
+      H->emask.push_back(z0);
+      H->emask.push_back(R);
+      const int nq = n_qubits;
+      if (kind == 1) {
+        std::vector<cplx> B(size_t(1 + nq) * nu, cplx(0, 0));
+        for (const auto& kv : entries) {
+          const uint32_t dm = kv.first ^ z0;
+          for (int u = 0; u < nu; ++u) {
+            B[u] += kv.second[u];
+            if (dm) B[size_t(1 + __builtin_ctz(dm)) * nu + u] += -2.0 * kv.second[u];
+          }
+        }
+        H->cvals.insert(H->cvals.end(), B.begin(), B.end());
+      } else {
+        std::vector<cplx> Q(size_t(1 + nq + nq * nq), cplx(0, 0));
+        for (const auto& kv : entries) {
+          const uint32_t dm = kv.first ^ z0;
+          const cplx a = kv.second[0];
+          Q[0] += a;
+          if (pc32(dm) >= 1) {
+            const int pb = __builtin_ctz(dm);
+            Q[1 + pb] += -2.0 * a;
+            if (pc32(dm) == 2) {
+              const int qb = 31 - __builtin_clz(dm);
+              Q[1 + qb] += -2.0 * a;
+              Q[size_t(1 + nq) + size_t(pb) * nq + qb] += 4.0 * a;
+            }
+          }
+        }
+        H->cvals.insert(H->cvals.end(), Q.begin(), Q.end());
+      }
     }
     g.eend = int32_t(H->emask.size());
     H->groups.push_back(g);

@@ -18,11 +18,15 @@ constexpr int kResidentThreads = 512;
 constexpr int kStreamThreads = 256;
 constexpr int kMaxPartials = 1024;          // per-gate reduction partials (streaming)
 
-// One X-mask group of the Hamiltonian. For a source index `src` whose bits on
-// the group's pattern qubits form the pattern u (bit j of u = bit upos_j of
-// src), the group's coefficient is
-//   f(src) = sum_{e=ebeg}^{eend-1} (-1)^{|src & emask[e]|} vals[vbeg + (e-ebeg)*2^ubits + u]
-// and the group adds f(src) * psi[src] to lambda[src ^ x].
+// One X-mask group of the Hamiltonian. The group adds f(src) * psi[src] to
+// lambda[src ^ x]; u is the pattern of src on the group's pattern qubits
+// (bit j of u = bit upos_j of src). Three forms of f:
+//  kind 0 (entry form):
+//    f(src) = sum_{e=ebeg}^{eend-1} (-1)^{|src & emask[e]|} vals[vbeg + (e-ebeg)*2^ubits + u]
+//  kind 1 (linear occupation form), emask[ebeg] = z0, emask[ebeg+1] = R:
+//    f(src) = (-1)^{|src & z0|} (B[u] + sum_{r in src & R} B[(1+r)*2^ubits + u]),  B = vals + vbeg
+//  kind 2 (quadratic occupation form, ubits = 0), same z0 and R, Q = vals + vbeg:
+//    f(src) = (-1)^{|src & z0|} (Q[0] + sum_{p in src&R} Q[1+p] + sum_{p<q in src&R} Q[1+nq+p*nq+q])
 struct GroupRec {
   uint32_t x;       // X mask of every term in the group
   uint32_t upos;    // up to 4 pattern-bit positions, 8 bits each
@@ -30,7 +34,8 @@ struct GroupRec {
   int32_t eend;
   int32_t vbeg;     // first value slot (in values, real or complex)
   int32_t ubits;    // number of pattern bits (0..4)
-  int32_t pad0, pad1;
+  int32_t kind;     // 0, 1 or 2 (above)
+  int32_t nq;       // qubit count (row stride of the quadratic table)
 };
 
 // One excitation rotation. Its amplitude pairs are (k, k ^ flip) for k in the

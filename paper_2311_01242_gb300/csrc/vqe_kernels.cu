@@ -40,21 +40,6 @@ __device__ __forceinline__ uint32_t pattern_of(uint32_t src, uint32_t upos, int 
   return u;
 }
 
-__device__ __forceinline__ GroupRec load_group(const GroupRec* p) {
-  const int4* q = reinterpret_cast<const int4*>(p);
-  const int4 a = __ldg(q);
-  const int4 b = __ldg(q + 1);
-  GroupRec g;
-  g.x = uint32_t(a.x);
-  g.upos = uint32_t(a.y);
-  g.ebeg = a.z;
-  g.eend = a.w;
-  g.vbeg = b.x;
-  g.ubits = b.y;
-  g.pad0 = g.pad1 = 0;
-  return g;
-}
-
 __device__ __forceinline__ GateRec load_gate(const GateRec* p) {
   const int4 a = __ldg(reinterpret_cast<const int4*>(p));
   GateRec r;
@@ -110,25 +95,77 @@ template <> struct Amp<false> {
   static __device__ __forceinline__ T from_c(double2 a) { return a; }
 };
 
-// Folded coefficient f_g(src) of a group (see GroupRec).
+__device__ __forceinline__ GroupRec load_group(const GroupRec* p) {
+  const int4* q = reinterpret_cast<const int4*>(p);
+  const int4 a = q[0];
+  const int4 b = q[1];
+  GroupRec g;
+  g.x = uint32_t(a.x);
+  g.upos = uint32_t(a.y);
+  g.ebeg = a.z;
+  g.eend = a.w;
+  g.vbeg = b.x;
+  g.ubits = b.y;
+  g.kind = b.z;
+  g.nq = b.w;
+  return g;
+}
+
+template <typename C>
+__device__ __forceinline__ void cadd(C& f, const C& v) {
+  if constexpr (sizeof(C) == sizeof(double)) {
+    f += v;
+  } else {
+    f.x += v.x;
+    f.y += v.y;
+  }
+}
+
+// Folded coefficient f_g(src) of a group (all three forms of GroupRec), from
+// tables in shared or global memory. Signs are applied in the integer pipe.
 template <bool REAL>
-__device__ __forceinline__ typename Amp<REAL>::C group_coef(const InstDesc& d, const GroupRec& g,
+__device__ __forceinline__ typename Amp<REAL>::C group_coef(const GroupRec& g, const uint32_t* emask,
+                                                            const typename Amp<REAL>::C* vals,
                                                             uint32_t src) {
-  typedef Amp<REAL> A;
-  const uint32_t u = pattern_of(src, g.upos, g.ubits);
-  const int64_t base = int64_t(g.vbeg) + u;
-  typename A::C f = sflip(A::coef(d, base), parity32(src & __ldg(d.emask + g.ebeg)));
-  for (int e = g.ebeg + 1, j = 1; e < g.eend; ++e, ++j) {
-    const typename A::C v = sflip(A::coef(d, base + (int64_t(j) << g.ubits)),
-                                  parity32(src & __ldg(d.emask + e)));
-    if constexpr (REAL) {
-      f += v;
-    } else {
-      f.x += v.x;
-      f.y += v.y;
+  typedef typename Amp<REAL>::C C;
+  if (g.kind == 0) {
+    const uint32_t u = pattern_of(src, g.upos, g.ubits);
+    const C* vp = vals + g.vbeg + u;
+    C f = sflip(vp[0], parity32(src & emask[g.ebeg]));
+    for (int e = g.ebeg + 1, j = 1; e < g.eend; ++e, ++j)
+      cadd(f, sflip(vp[j << g.ubits], parity32(src & emask[e])));
+    return f;
+  }
+  const uint32_t z0 = emask[g.ebeg];
+  uint32_t m = src & emask[g.ebeg + 1];
+  C f;
+  if (g.kind == 1) {
+    const uint32_t u = pattern_of(src, g.upos, g.ubits);
+    const C* vp = vals + g.vbeg + u;
+    f = vp[0];
+    while (m) {
+      const int r = __ffs(m) - 1;
+      m &= m - 1;
+      cadd(f, vp[(1 + r) << g.ubits]);
+    }
+  } else {
+    const C* q = vals + g.vbeg;
+    const int nq = g.nq;
+    f = q[0];
+    while (m) {
+      const int pb = __ffs(m) - 1;
+      m &= m - 1;
+      cadd(f, q[1 + pb]);
+      const C* row = q + 1 + nq + pb * nq;
+      uint32_t m2 = m;
+      while (m2) {
+        const int qb = __ffs(m2) - 1;
+        m2 &= m2 - 1;
+        cadd(f, row[qb]);
+      }
     }
   }
-  return f;
+  return sflip(f, parity32(src & z0));
 }
 
 __device__ __forceinline__ bool in_sector(uint32_t k, int n_elec, int n_alpha) {
@@ -151,42 +188,6 @@ __device__ double block_sum(double v, double* red) {
 }
 
 // ---------------------------------------------------------------- resident kernel
-// Folded group coefficient from explicit tables (shared or global memory).
-template <bool REAL>
-__device__ __forceinline__ typename Amp<REAL>::C group_coef_tab(const GroupRec& g, const uint32_t* emask,
-                                                                const typename Amp<REAL>::C* vals,
-                                                                uint32_t src) {
-  typedef typename Amp<REAL>::C C;
-  const uint32_t u = pattern_of(src, g.upos, g.ubits);
-  const C* vp = vals + g.vbeg + u;
-  C f = sflip(vp[0], parity32(src & emask[g.ebeg]));
-  for (int e = g.ebeg + 1, j = 1; e < g.eend; ++e, ++j) {
-    const C v = sflip(vp[j << g.ubits], parity32(src & emask[e]));
-    if constexpr (REAL) {
-      f += v;
-    } else {
-      f.x += v.x;
-      f.y += v.y;
-    }
-  }
-  return f;
-}
-
-__device__ __forceinline__ GroupRec load_group_any(const GroupRec* p) {
-  const int4* q = reinterpret_cast<const int4*>(p);
-  const int4 a = q[0];
-  const int4 b = q[1];
-  GroupRec g;
-  g.x = uint32_t(a.x);
-  g.upos = uint32_t(a.y);
-  g.ebeg = a.z;
-  g.eend = a.w;
-  g.vbeg = b.x;
-  g.ubits = b.y;
-  g.pad0 = g.pad1 = 0;
-  return g;
-}
-
 __device__ __forceinline__ void sweep_barrier(int nthreads) {
   asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
 }
@@ -256,15 +257,28 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
   const int swarps = sw >> 5;
   const int spos = (tid & 31) * swarps + (tid >> 5);
 
-  // a2: forward sweep
-  if (tid < sw) {
+  // a2: forward sweep. The next gate's record, cos/sin and first pair index
+  // are loaded before the current gate runs, off the barrier-to-barrier path.
+  if (tid < sw && M > 0) {
+    GateRec gr = gates[0];
+    int p0 = poff[0], cnt = poff[1] - p0;
+    double2 c_s = cs[0];
+    uint32_t kf = (spos < cnt) ? pairs[p0 + spos] : 0u;
     for (int m = 0; m < M; ++m) {
-      const GateRec gr = gates[m];
-      const int p0 = poff[m], cnt = poff[m + 1] - p0;
-      const double2 c_s = cs[m];
+      GateRec grn = gr;
+      int p0n = 0, cntn = 0;
+      double2 c_sn = c_s;
+      uint32_t kfn = 0u;
+      if (m + 1 < M) {
+        grn = gates[m + 1];
+        p0n = poff[m + 1];
+        cntn = poff[m + 2] - p0n;
+        c_sn = cs[m + 1];
+        if (spos < cntn) kfn = pairs[p0n + spos];
+      }
       const int s0 = gr.sign0 < 0;
       for (int q = spos; q < cnt; q += sw) {
-        const uint32_t k = pairs[p0 + q];
+        const uint32_t k = (q == spos) ? kf : pairs[p0 + q];
         const uint32_t k2 = k ^ gr.flip;
         const double ss = sflip(c_s.y, parity32(k & gr.par) ^ s0);
         T a = psi[k], b = psi[k2];
@@ -273,6 +287,11 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
         psi[k2] = b;
       }
       sweep_barrier(sw);
+      gr = grn;
+      p0 = p0n;
+      cnt = cntn;
+      c_s = c_sn;
+      kf = kfn;
     }
   }
   // stage the H psi tables into the union region
@@ -303,9 +322,9 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
     uint32_t gi = W > 0 ? __ldg(d.ell + r) : kEllPad;
     for (int j = 0; j < W && gi != kEllPad; ++j) {
       const uint32_t gnext = (j + 1 < W) ? __ldg(d.ell + int64_t(j + 1) * D + r) : kEllPad;
-      const GroupRec g = load_group_any(tg + gi);
+      const GroupRec g = load_group(tg + gi);
       const uint32_t src = k ^ g.x;
-      A::mac(acc, group_coef_tab<REAL>(g, te, tv, src), psi[src]);
+      A::mac(acc, group_coef<REAL>(g, te, tv, src), psi[src]);
       gi = gnext;
     }
     lam[k] = acc;
@@ -317,15 +336,28 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
 
   if (!with_grad) return;
 
-  // a4: reverse sweep
-  if (tid < sw) {
-    for (int m = M - 1; m >= 0; --m) {
-      const GateRec gr = gates[m];
-      const int p0 = poff[m], cnt = poff[m + 1] - p0;
-      const double2 c_s = cs[m];
+  // a4: reverse sweep (same prefetch of the next gate as the forward sweep)
+  if (tid < sw && M > 0) {
+    int m = M - 1;
+    GateRec gr = gates[m];
+    int p0 = poff[m], cnt = poff[m + 1] - p0;
+    double2 c_s = cs[m];
+    uint32_t kf = (spos < cnt) ? pairs[p0 + spos] : 0u;
+    for (; m >= 0; --m) {
+      GateRec grn = gr;
+      int p0n = 0, cntn = 0;
+      double2 c_sn = c_s;
+      uint32_t kfn = 0u;
+      if (m > 0) {
+        grn = gates[m - 1];
+        p0n = poff[m - 1];
+        cntn = poff[m] - p0n;
+        c_sn = cs[m - 1];
+        if (spos < cntn) kfn = pairs[p0n + spos];
+      }
       const int s0 = gr.sign0 < 0;
       for (int q = spos; q < cnt; q += sw) {
-        const uint32_t k = pairs[p0 + q];
+        const uint32_t k = (q == spos) ? kf : pairs[p0 + q];
         const uint32_t k2 = k ^ gr.flip;
         const int sb = parity32(k & gr.par) ^ s0;
         const double ss = sflip(c_s.y, sb);
@@ -339,15 +371,30 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
         lam[k2] = lb;
       }
       sweep_barrier(sw);
+      gr = grn;
+      p0 = p0n;
+      cnt = cntn;
+      c_s = c_sn;
+      kf = kfn;
     }
   }
   __syncthreads();
+  // per-gate sums of the pair contributions: four consecutive lanes split a
+  // gate's pairs into four contiguous quarters, combined by a fixed shuffle tree
   double* g_out = grad + row * ld_grad;
-  for (int m = tid; m < M; m += bs) {
-    const int p0 = poff[m], p1 = poff[m + 1];
+  for (int base = 0; base < 4 * M; base += bs) {
+    const int t = base + tid;
+    const int m = t >> 2, qtr = t & 3;
     double s = 0.0;
-    for (int p = p0; p < p1; ++p) s += gbuf[p];
-    g_out[m] = 2.0 * s;
+    if (m < M) {
+      const int p0 = poff[m], p1 = poff[m + 1];
+      const int len = p1 - p0, chunk = (len + 3) >> 2;
+      const int a = p0 + qtr * chunk, b = min(p1, a + chunk);
+      for (int p = a; p < b; ++p) s += gbuf[p];
+    }
+    s += __shfl_down_sync(0xffffffffu, s, 2, 4);
+    s += __shfl_down_sync(0xffffffffu, s, 1, 4);
+    if (m < M && qtr == 0) g_out[m] = 2.0 * s;
   }
 }
 
@@ -394,12 +441,15 @@ __global__ void k_gate_fwd(const uint32_t* __restrict__ pairs, int64_t P, const 
 
 // lambda = H psi on the sector; per-block energy partials.
 template <bool REAL, bool ELL>
-__global__ void __launch_bounds__(kStreamThreads)
+__global__ void __launch_bounds__(kStreamThreads, 1)
 k_hpsi(const InstDesc d, int n_elec, int n_alpha, const typename Amp<REAL>::T* __restrict__ psi,
        typename Amp<REAL>::T* __restrict__ lam, double* __restrict__ epart) {
   typedef Amp<REAL> A;
   typedef typename A::T T;
+  typedef typename A::C C;
   __shared__ double red[32];
+  const C* tv;
+  if constexpr (REAL) tv = d.vals; else tv = d.cvals;
   double e_part = 0.0;
   for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < d.D;
        r += int64_t(gridDim.x) * blockDim.x) {
@@ -411,14 +461,14 @@ k_hpsi(const InstDesc d, int n_elec, int n_alpha, const typename Amp<REAL>::T* _
         if (gi == kEllPad) break;
         const GroupRec g = load_group(d.groups + gi);
         const uint32_t src = k ^ g.x;
-        A::mac(acc, group_coef<REAL>(d, g, src), psi[src]);
+        A::mac(acc, group_coef<REAL>(g, d.emask, tv, src), psi[src]);
       }
     } else {
       for (int gi = 0; gi < d.G; ++gi) {
         const GroupRec g = load_group(d.groups + gi);
         const uint32_t src = k ^ g.x;
         if (!in_sector(src, n_elec, n_alpha)) continue;
-        A::mac(acc, group_coef<REAL>(d, g, src), psi[src]);
+        A::mac(acc, group_coef<REAL>(g, d.emask, tv, src), psi[src]);
       }
     }
     lam[k] = acc;
@@ -429,7 +479,7 @@ k_hpsi(const InstDesc d, int n_elec, int n_alpha, const typename Amp<REAL>::T* _
 }
 
 template <bool REAL>
-__global__ void __launch_bounds__(kStreamThreads)
+__global__ void __launch_bounds__(kStreamThreads, 1)
 k_gate_adj(const uint32_t* __restrict__ pairs, int64_t P, const GateRec* __restrict__ gate,
            const double2* __restrict__ cs, typename Amp<REAL>::T* __restrict__ phi,
            typename Amp<REAL>::T* __restrict__ lam, double* __restrict__ gpart) {
