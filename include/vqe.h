@@ -216,6 +216,43 @@ int vqe_batch_energy_grad_host(vqe_batch_t b, const double* theta_host, int64_t 
 void vqe_destroy_batch(vqe_batch_t b);
 
 /*
+ * Learned warm start: a small network that predicts the UCCSD angles at a new
+ * geometry from angles the VQE itself converged to along a bond-stretch scan
+ * (the paper scans bond lengths, Sec. 3.1, and starts each VQE from the
+ * Hartree-Fock state; the network is not from the paper). Architecture:
+ * n_in -> n_hidden -> n_hidden -> n_out, SiLU after the first two layers, BF16
+ * weights and BF16 GEMM operands on the tensor cores with FP32 accumulation,
+ * FP32 biases, Adam on FP32 master weights.
+ * Parameters are one FP32 array (length vqe_mlp_param_count) laid out as
+ *   W1 [n_hidden x Ip], b1 [n_hidden], W2 [n_hidden x n_hidden], b2 [n_hidden],
+ *   W3 [Op x n_hidden], b3 [Op],
+ * Ip = n_in rounded up to 16, Op = n_out rounded up to 16, padding zero; the
+ * BF16 copy (uint16 bit patterns) has the same layout. x: [batch x n_in] FP32
+ * row-major; target and y: [batch x n_out] FP32 row-major. n_hidden must be a
+ * multiple of 16. All device pointers; asynchronous on `stream`.
+ * BF16 rounding points: x, both hidden activations, the output gradient and
+ * both pre-activation gradients; loss = mean over batch and outputs of
+ * (y - target)^2.
+ */
+int64_t vqe_mlp_param_count(int n_in, int n_hidden, int n_out);
+size_t vqe_mlp_workspace_bytes(int batch, int n_in, int n_hidden, int n_out);
+/* dst[i] = bf16(src[i]) (round to nearest even) for i < n. */
+int vqe_mlp_to_bf16(int64_t n, const float* src, uint16_t* dst, vqe_stream_t stream);
+/* y = network(x). */
+int vqe_mlp_forward(int batch, int n_in, int n_hidden, int n_out, const float* x, const float* params,
+                    const uint16_t* params_bf16, float* y, void* workspace, size_t workspace_bytes,
+                    vqe_stream_t stream);
+/* loss[0] and the full parameter gradient (same layout as params). */
+int vqe_mlp_loss_grad(int batch, int n_in, int n_hidden, int n_out, const float* x, const float* target,
+                      const float* params, const uint16_t* params_bf16, float* grads, float* loss,
+                      void* workspace, size_t workspace_bytes, vqe_stream_t stream);
+/* One bias-corrected Adam step on params, refreshing params_bf16. step_dev is a
+ * device int holding this update's 1-based step number; it is incremented on
+ * the device afterwards, so a captured training step can be replayed. */
+int vqe_mlp_adam(int64_t n, float* params, const float* grads, float* m, float* v, int* step_dev, float lr,
+                 float beta1, float beta2, float eps, uint16_t* params_bf16, vqe_stream_t stream);
+
+/*
  * Energy (and gradient when grad_dev != NULL) with no device allocation at all.
  * The paper has no counterpart; this exists for callers that may not call
  * cudaMalloc: code that runs inside another framework whose allocator owns the

@@ -121,6 +121,68 @@ void add_ladder_product(std::unordered_map<uint64_t, cplx>& acc, double coef, co
 
 }  // namespace
 
+// ------------------------------------------------------------------ shared connectivity tables
+// Hamiltonians with the same X-mask structure (a bond-stretch scan) have the
+// same connectivity table for a sector; one device copy serves them all.
+namespace {
+struct SharedEll {
+  uint32_t* d = nullptr;
+  std::vector<uint32_t> host;
+  int refs = 0;
+};
+std::mutex g_ell_mu;
+std::multimap<uint64_t, SharedEll*> g_ell_reg;
+
+uint64_t fnv1a(const std::vector<uint32_t>& v) {
+  uint64_t h = 1469598103934665603ull;
+  const unsigned char* p = reinterpret_cast<const unsigned char*>(v.data());
+  for (size_t i = 0; i < v.size() * 4; ++i) {
+    h ^= p[i];
+    h *= 1099511628211ull;
+  }
+  return h ^ v.size();
+}
+
+int ell_acquire(const std::vector<uint32_t>& v, uint32_t** out) {
+  std::lock_guard<std::mutex> lock(g_ell_mu);
+  const uint64_t h = fnv1a(v);
+  auto range = g_ell_reg.equal_range(h);
+  for (auto it = range.first; it != range.second; ++it) {
+    if (it->second->host == v) {
+      ++it->second->refs;
+      *out = it->second->d;
+      return VQE_OK;
+    }
+  }
+  SharedEll* e = new SharedEll;
+  const int rc = upload(v, &e->d);
+  if (rc) {
+    delete e;
+    return rc;
+  }
+  e->host = v;
+  e->refs = 1;
+  g_ell_reg.emplace(h, e);
+  *out = e->d;
+  return VQE_OK;
+}
+
+void ell_release(uint32_t* d) {
+  if (!d) return;
+  std::lock_guard<std::mutex> lock(g_ell_mu);
+  for (auto it = g_ell_reg.begin(); it != g_ell_reg.end(); ++it) {
+    if (it->second->d == d) {
+      if (--it->second->refs == 0) {
+        dfree(it->second->d);
+        delete it->second;
+        g_ell_reg.erase(it);
+      }
+      return;
+    }
+  }
+}
+}  // namespace
+
 // ------------------------------------------------------------------ handles
 struct vqe_hamiltonian_s {
   int n = 0;
@@ -148,7 +210,7 @@ struct vqe_hamiltonian_s {
     dfree(d_emask);
     dfree(d_vals);
     dfree(d_cvals);
-    for (auto& kv : ells) dfree(kv.second.d_ell);
+    for (auto& kv : ells) ell_release(kv.second.d_ell);
   }
 };
 
@@ -267,7 +329,7 @@ const vqe_hamiltonian_s::Ell* get_ell(vqe_hamiltonian_t h, vqe_ansatz_t a, int* 
       for (int64_t r = 0; r < D; ++r) e.extra_adds += extra[r];
       e.W = W;
       e.use_ell = true;
-      int rc = upload(ell, &e.d_ell);
+      int rc = W > 0 ? ell_acquire(ell, &e.d_ell) : VQE_OK;
       if (rc != VQE_OK) {
         *err = rc;
         return nullptr;

@@ -188,6 +188,10 @@ __device__ double block_sum(double v, double* red) {
 }
 
 // ---------------------------------------------------------------- resident kernel
+__device__ __forceinline__ void prefetch_l2(const void* p) {
+  asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
+}
+
 __device__ __forceinline__ void sweep_barrier(int nthreads) {
   asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
 }
@@ -247,6 +251,17 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
   for (uint32_t k = tid; k < dim; k += bs) {
     psi[k] = A::zero();
     lam[k] = A::zero();
+  }
+  // pull the tables H psi reads later into L2 while the forward sweep runs
+  {
+    const char* ell_b = reinterpret_cast<const char*>(d.ell);
+    const int64_t ell_bytes = int64_t(W) * D * 4;
+    for (int64_t o = int64_t(tid) * 128; o < ell_bytes; o += int64_t(bs) * 128) prefetch_l2(ell_b + o);
+    const char* val_b = REAL ? reinterpret_cast<const char*>(d.vals) : reinterpret_cast<const char*>(d.cvals);
+    const int64_t val_bytes = int64_t(d.S) * (REAL ? 8 : 16);
+    for (int64_t o = int64_t(tid) * 128; o < val_bytes; o += int64_t(bs) * 128) prefetch_l2(val_b + o);
+    const char* sec_b = reinterpret_cast<const char*>(d.sector);
+    for (int64_t o = int64_t(tid) * 128; o < int64_t(D) * 4; o += int64_t(bs) * 128) prefetch_l2(sec_b + o);
   }
   __syncthreads();
   if (tid == 0) psi[d.hf] = A::unit();

@@ -98,3 +98,11 @@ def test_create_rejects_invalid_arguments_before_device_work(lib):
     exc = np.array([[0, 7, -1, -1]], dtype=np.int32)
     assert lib.vqe_create_ansatz(4, 3, 1, api._ptr(exc), ctypes.byref(a)) == 1
     assert lib.vqe_create_ansatz(4, 1 << 6, 0, None, ctypes.byref(a)) == 1
+
+
+def test_mlp_param_count_matches_oracle_layout(lib):
+    from oracle import mlp as omlp
+    for dims in [(9, 256, 360), (3, 16, 5), (17, 32, 16)]:
+        assert lib.vqe_mlp_param_count(*dims) == omlp.layout(*dims)[1]
+    assert lib.vqe_mlp_param_count(9, 20, 5) == 0  # hidden width must be a multiple of 16
+    assert lib.vqe_mlp_workspace_bytes(128, 9, 256, 360) > 0
