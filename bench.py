@@ -220,6 +220,22 @@ def run_reference(args, rank):
 
 
 # ------------------------------------------------------------------ ours
+def reduce_max(value, world, device=None):
+    """Max of a per-rank float over all ranks (identity for one rank)."""
+    if world <= 1:
+        return float(value)
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([float(value)], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def throughput(units_per_rank, world, steps, max_seconds):
+    """Whole-job units per second: every rank did units_per_rank per step."""
+    return units_per_rank * world * steps / max_seconds
+
+
 def kernel_source_hash():
     with open(KERNEL_SRC, "rb") as f:
         return hashlib.sha256(f.read()).hexdigest()[:16]
@@ -267,7 +283,7 @@ def run_warmstart(args):
     rest = [i for i in range(len(rs)) if i % 4 != 0]
     held = rest[::max(1, len(rest) // args.held_out)][:args.held_out]
     t0 = time.perf_counter()
-    geoms = [ws.Geometry(scan.at(rs[i]), rs[i], A) for i in train]
+    geoms = [ws.Geometry(scan.at(rs[i]), rs[i], A, graph=True) for i in train]
     t_create = time.perf_counter() - t0
     t0 = time.perf_counter()
     thetas, energies, evals = ws.training_set(geoms, gtol=1e-6)
@@ -280,7 +296,7 @@ def run_warmstart(args):
     arms = {"hf": [], "continuation": [], "mlp": []}
     fallbacks, reached_exact = 0, 0
     for i in held:
-        g = ws.Geometry(scan.at(rs[i]), rs[i], A)
+        g = ws.Geometry(scan.at(rs[i]), rs[i], A, graph=True)
         e0 = ws.lanczos_ground(g.H, A, n, ne)
         prev = max(j for j, ti in enumerate(train) if ti < i)
         tp = time.perf_counter()
@@ -390,13 +406,9 @@ def main():
     t_wall = time.perf_counter() - t_wall0
     clocks = sampler.stop()
     per = [s.elapsed_time(e) for s, e in zip(starts, ends)]
-    dev_ms = sum(per)
-    if world > 1:
-        t = torch.tensor([dev_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        dev_ms = float(t.item())
+    dev_ms = reduce_max(sum(per), world, "cuda")
     ms_per_step = dev_ms / K
-    value = n_inst * world * K / (dev_ms / 1000.0)
+    value = throughput(n_inst, world, K, dev_ms / 1000.0)
 
     # e2e through the host-buffer C entry point (copies + sync inside the timed region)
     K2 = args.e2e_steps or min(K, 500)
@@ -412,12 +424,8 @@ def main():
     t0 = time.perf_counter()
     for _ in range(K2):
         B.energy_grad_host(th_np, e_np, g_np, wsh, stream)
-    t_e2e = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([t_e2e], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        t_e2e = float(t.item())
-    e2e_value = n_inst * world * K2 / t_e2e
+    t_e2e = reduce_max(time.perf_counter() - t0, world, "cuda")
+    e2e_value = throughput(n_inst, world, K2, t_e2e)
     assert np.allclose(e_np, energies.cpu().numpy(), rtol=0, atol=0), "host and device entries disagree"
 
     achieved = flops_per_launch / (ms_per_step / 1000.0) / 1e12

@@ -213,6 +213,15 @@ int vqe_batch_energy_grad_host(vqe_batch_t b, const double* theta_host, int64_t 
                                double* energies_host, double* grads_host, int64_t ld_grad,
                                void* workspace, size_t workspace_bytes, vqe_stream_t stream);
 
+/*
+ * Launch shape of a batch (used by the autotuner): threads per block of the
+ * gate-major streaming kernels (multiple of 32 in [64, 512]) and threads that
+ * run the gate sweeps of shared-memory-resident instances (multiple of 32 in
+ * [32, 512]); 0 keeps the current value. Synchronous. Results do not depend on
+ * either value.
+ */
+int vqe_batch_set_tuning(vqe_batch_t b, int stream_threads, int sweep_threads);
+
 void vqe_destroy_batch(vqe_batch_t b);
 
 /*

@@ -110,6 +110,7 @@ PROTOTYPES = {
     "vqe_batch_energy_grad": (ctypes.c_int, [c_vp, c_vp, c_i64, c_vp, c_vp, c_i64, c_vp, c_sz, c_vp]),
     "vqe_batch_host_workspace_bytes": (c_sz, [c_vp, ctypes.c_int]),
     "vqe_batch_energy_grad_host": (ctypes.c_int, [c_vp, c_vp, c_i64, c_vp, c_vp, c_i64, c_vp, c_sz, c_vp]),
+    "vqe_batch_set_tuning": (ctypes.c_int, [c_vp, ctypes.c_int, ctypes.c_int]),
     "vqe_destroy_batch": (None, [c_vp]),
     "vqe_work_estimate": (ctypes.c_int, [c_vp, c_vp, ctypes.c_int, P(c_dbl), P(c_dbl)]),
     "vqe_energy_grad_noalloc": (ctypes.c_int, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),

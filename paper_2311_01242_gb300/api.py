@@ -164,12 +164,16 @@ def energy(h, a, theta, workspace=None, stream=None, device="cuda"):
     return e[0]
 
 
-def energy_grad(h, a, theta, workspace=None, stream=None, device="cuda"):
+def energy_grad(h, a, theta, workspace=None, stream=None, device="cuda", out=None):
+    """(E, dE/dtheta); out=(e[1], g[>=n_params]) reuses caller buffers."""
     theta = _as_theta(theta, device)
     if workspace is None:
         workspace = alloc_workspace(workspace_bytes(h, a, VQE_WS_GRAD), theta.device)
-    e = torch.empty(1, dtype=torch.float64, device=theta.device)
-    g = torch.empty(max(a.n_params, 1), dtype=torch.float64, device=theta.device)
+    if out is None:
+        e = torch.empty(1, dtype=torch.float64, device=theta.device)
+        g = torch.empty(max(a.n_params, 1), dtype=torch.float64, device=theta.device)
+    else:
+        e, g = out
     _check(_lib().vqe_energy_grad(h.handle, a.handle, _ptr(theta), _ptr(e), _ptr(g), _ptr(workspace),
                                   workspace.numel(), _stream(stream)))
     return e[0], g[:a.n_params]
@@ -256,3 +260,36 @@ class Batch:
         if b is not None and b.value:
             self._lib.vqe_destroy_batch(b)
             self.handle = None
+
+
+class GraphEnergyGrad:
+    """vqe_energy_grad of one (Hamiltonian, ansatz) pair captured once in a CUDA
+    graph and replayed with new angles copied into the captured buffer (the
+    streaming path issues two launches per gate; replay removes their host cost)."""
+
+    def __init__(self, h, a, device="cuda"):
+        self.h, self.a = h, a
+        m = max(a.n_params, 1)
+        self.theta = torch.zeros(m, dtype=torch.float64, device=device)
+        self.e = torch.zeros(1, dtype=torch.float64, device=device)
+        self.g = torch.zeros(m, dtype=torch.float64, device=device)
+        self.ws = alloc_workspace(workspace_bytes(h, a, VQE_WS_GRAD), device)
+        self._run()
+        torch.cuda.synchronize()
+        side = torch.cuda.Stream(device=device)
+        side.wait_stream(torch.cuda.current_stream())
+        self.graph = torch.cuda.CUDAGraph()
+        with torch.cuda.stream(side):
+            with torch.cuda.graph(self.graph, stream=side):
+                self._run()
+        torch.cuda.current_stream().wait_stream(side)
+
+    def _run(self):
+        energy_grad(self.h, self.a, self.theta[:self.a.n_params] if self.a.n_params else self.theta,
+                    workspace=self.ws, out=(self.e, self.g))
+
+    def __call__(self, theta):
+        if self.a.n_params:
+            self.theta[:self.a.n_params].copy_(torch.as_tensor(theta, dtype=torch.float64))
+        self.graph.replay()
+        return self.e, self.g[:self.a.n_params]

@@ -143,8 +143,24 @@ uint64_t fnv1a(const std::vector<uint32_t>& v) {
   return h ^ v.size();
 }
 
+// Tables above this size are not shared (no host copy is kept for them).
+constexpr size_t kShareEllBytes = size_t(16) << 20;
+uint64_t g_ell_unique = 0;
+
 int ell_acquire(const std::vector<uint32_t>& v, uint32_t** out) {
   std::lock_guard<std::mutex> lock(g_ell_mu);
+  if (v.size() * 4 > kShareEllBytes) {
+    SharedEll* e = new SharedEll;
+    const int rc = upload(v, &e->d);
+    if (rc) {
+      delete e;
+      return rc;
+    }
+    e->refs = 1;
+    g_ell_reg.emplace(~uint64_t(0) - (g_ell_unique++), e);  // never matched by a hash lookup
+    *out = e->d;
+    return VQE_OK;
+  }
   const uint64_t h = fnv1a(v);
   auto range = g_ell_reg.equal_range(h);
   for (auto it = range.first; it != range.second; ++it) {
@@ -181,6 +197,31 @@ void ell_release(uint32_t* d) {
     }
   }
 }
+// Device-built 16-bit tables, shared by Hamiltonians with the same group
+// X masks (in connectivity order) and the same sector.
+struct SharedEll16 {
+  uint16_t* d = nullptr;
+  int W = 0;
+  std::vector<uint32_t> key;
+  int refs = 0;
+};
+std::mutex g_ell16_mu;
+std::vector<SharedEll16*> g_ell16_reg;
+
+void ell16_release(uint16_t* d) {
+  if (!d) return;
+  std::lock_guard<std::mutex> lock(g_ell16_mu);
+  for (size_t i = 0; i < g_ell16_reg.size(); ++i) {
+    if (g_ell16_reg[i]->d == d) {
+      if (--g_ell16_reg[i]->refs == 0) {
+        dfree(g_ell16_reg[i]->d);
+        delete g_ell16_reg[i];
+        g_ell16_reg.erase(g_ell16_reg.begin() + long(i));
+      }
+      return;
+    }
+  }
+}
 }  // namespace
 
 // ------------------------------------------------------------------ handles
@@ -200,6 +241,7 @@ struct vqe_hamiltonian_s {
     int W = 0;
     bool use_ell = false;
     uint32_t* d_ell = nullptr;
+    uint16_t* d_ell16 = nullptr;      // device-built 16-bit table (large sectors)
     int64_t nnz = 0;                  // connected (output, group) pairs
     double extra_adds = 0;            // sum over nnz of (entries - 1)
   };
@@ -210,7 +252,10 @@ struct vqe_hamiltonian_s {
     dfree(d_emask);
     dfree(d_vals);
     dfree(d_cvals);
-    for (auto& kv : ells) ell_release(kv.second.d_ell);
+    for (auto& kv : ells) {
+      ell_release(kv.second.d_ell);
+      ell16_release(kv.second.d_ell16);
+    }
   }
 };
 
@@ -239,9 +284,41 @@ struct vqe_ansatz_s {
   }
 };
 
+// Gate-major streaming of the batch's instances that do not fit shared memory
+// (real-amplitude path): device-side plan built once at batch creation.
+struct StreamBatch {
+  std::vector<int> slots;                 // batch index of each streamed slot
+  std::vector<InstDesc> descs;
+  std::vector<int64_t> psi_off, lam_off, ebase, gbase;
+  int Mmax = 0;
+  std::vector<vqe::BatchSegs> gate_segs;  // per gate index, device pointers inside
+  vqe::BatchSegs out_segs{};
+  int64_t n_gm = 0;
+  size_t cs_off = 0, ebuf_off = 0, gbuf_off = 0, total_energy = 0, total_grad = 0;
+  int threads = 256;
+  InstDesc* d_desc = nullptr;
+  int64_t *d_psi_off = nullptr, *d_lam_off = nullptr, *d_ebase = nullptr, *d_gbase = nullptr;
+  int32_t *d_seg_inst = nullptr, *d_out_inst = nullptr, *d_gm_inst = nullptr, *d_gm_gate = nullptr;
+  int64_t *d_seg_pref = nullptr, *d_out_pref = nullptr;
+  ~StreamBatch() {
+    dfree(d_desc);
+    dfree(d_psi_off);
+    dfree(d_lam_off);
+    dfree(d_ebase);
+    dfree(d_gbase);
+    dfree(d_seg_inst);
+    dfree(d_out_inst);
+    dfree(d_gm_inst);
+    dfree(d_gm_gate);
+    dfree(d_seg_pref);
+    dfree(d_out_pref);
+  }
+};
+
 struct vqe_batch_s {
   int n_inst = 0;
   int32_t max_params = 0;
+  StreamBatch sb;
   std::vector<vqe_hamiltonian_t> hams;
   std::vector<vqe_ansatz_t> ans;
   std::vector<InstDesc> descs;          // host copies, device pointers inside
@@ -257,6 +334,74 @@ struct vqe_batch_s {
 };
 
 namespace {
+
+// Builds (or shares) a 16-bit connectivity table on the device when it fits in
+// 40% of the free device memory (at most 96 GB); leaves e unchanged otherwise.
+int build_ell_device(vqe_hamiltonian_t h, vqe_ansatz_t a, const std::vector<int>& order,
+                     vqe_hamiltonian_s::Ell* e) {
+  const int G = int(h->groups.size());
+  const int64_t D = int64_t(a->sector.size());
+  std::vector<uint32_t> key;
+  key.reserve(size_t(G) + 4);
+  key.push_back(uint32_t(a->n));
+  key.push_back(uint32_t(a->n_elec));
+  key.push_back(uint32_t(a->n_alpha));
+  key.push_back(uint32_t(D));
+  for (int g : order) key.push_back(h->groups[g].x);
+  {
+    std::lock_guard<std::mutex> lock(g_ell16_mu);
+    for (auto* s : g_ell16_reg)
+      if (s->key == key) {
+        ++s->refs;
+        e->W = s->W;
+        e->d_ell16 = s->d;
+        e->use_ell = true;
+        return VQE_OK;
+      }
+  }
+  std::vector<int32_t> ord(order.begin(), order.end());
+  int32_t *d_order = nullptr, *d_len = nullptr, *d_wmax = nullptr;
+  int rc = upload(ord, &d_order);
+  if (rc) return rc;
+  cudaError_t ce = cudaMalloc(reinterpret_cast<void**>(&d_len), size_t(D) * 4);
+  if (ce == cudaSuccess) ce = cudaMalloc(reinterpret_cast<void**>(&d_wmax), 4);
+  if (ce == cudaSuccess)
+    ce = vqe::ell_device_count(a->d_sector, D, h->d_groups, G, d_order, a->n_elec, a->n_alpha, d_len, d_wmax, 0);
+  int32_t W = 0;
+  if (ce == cudaSuccess) ce = cudaMemcpy(&W, d_wmax, 4, cudaMemcpyDeviceToHost);
+  size_t free_b = 0, total_b = 0;
+  if (ce == cudaSuccess) ce = cudaMemGetInfo(&free_b, &total_b);
+  uint16_t* d_ell = nullptr;
+  const double bytes = double(W) * double(D) * 2.0;
+  if (ce == cudaSuccess && W > 0 && bytes <= std::min(0.4 * double(free_b), 96.0e9)) {
+    ce = cudaMalloc(reinterpret_cast<void**>(&d_ell), size_t(W) * size_t(D) * 2);
+    if (ce == cudaSuccess)
+      ce = vqe::ell_device_fill(a->d_sector, D, h->d_groups, G, d_order, a->n_elec, a->n_alpha, W, d_ell, 0);
+    if (ce == cudaSuccess) ce = cudaDeviceSynchronize();
+  }
+  dfree(d_order);
+  dfree(d_len);
+  dfree(d_wmax);
+  if (ce != cudaSuccess) {
+    dfree(d_ell);
+    return cuda_fail(ce, "device connectivity table");
+  }
+  if (d_ell) {
+    SharedEll16* s = new SharedEll16;
+    s->d = d_ell;
+    s->W = W;
+    s->key = std::move(key);
+    s->refs = 1;
+    {
+      std::lock_guard<std::mutex> lock(g_ell16_mu);
+      g_ell16_reg.push_back(s);
+    }
+    e->W = W;
+    e->d_ell16 = d_ell;
+    e->use_ell = true;
+  }
+  return VQE_OK;
+}
 
 // FP64 additions the kernels spend on one group's coefficient for a source index.
 double fp64_adds(vqe_hamiltonian_t h, int g, uint32_t src) {
@@ -290,7 +435,13 @@ const vqe_hamiltonian_s::Ell* get_ell(vqe_hamiltonian_t h, vqe_ansatz_t a, int* 
   // row lengths
   std::vector<int32_t> len(D, 0);
   const double cost = double(D) * double(G);
-  if (cost <= 4.0e9 && G > 0) {
+  if (cost > 2.0e7 && G > 0 && G < 65535) {
+    const int rc = build_ell_device(h, a, order, &e);
+    if (rc != VQE_OK) {
+      *err = rc;
+      return nullptr;
+    }
+  } else if (cost <= 4.0e9 && G > 0) {
     parallel_for(D, [&](int64_t lo, int64_t hi) {
       for (int64_t r = lo; r < hi; ++r) {
         const uint32_t k = a->sector[r];
@@ -307,7 +458,7 @@ const vqe_hamiltonian_s::Ell* get_ell(vqe_hamiltonian_t h, vqe_ansatz_t a, int* 
     }
     e.nnz = nnz;
     const double bytes = double(W) * double(D) * 4.0;
-    if (bytes <= 2.0e9) {
+    if (bytes <= 512.0e6) {
       std::vector<uint32_t> ell(size_t(W) * size_t(D), vqe::kEllPad);
       std::vector<double> extra(D, 0.0);
       parallel_for(D, [&](int64_t lo, int64_t hi) {
@@ -336,8 +487,8 @@ const vqe_hamiltonian_s::Ell* get_ell(vqe_hamiltonian_t h, vqe_ansatz_t a, int* 
       }
     }
   }
-  if (!e.use_ell) {
-    // scan mode: count work on a sample only when the exact count is too costly
+  if (!e.use_ell || e.d_ell16) {
+    // device-built table or scan mode: estimate the work from a sample of outputs
     e.nnz = 0;
     e.extra_adds = 0;
     const int64_t step = std::max<int64_t>(1, D / 4096);
@@ -379,11 +530,14 @@ InstDesc make_desc(vqe_hamiltonian_t h, vqe_ansatz_t a, const vqe_hamiltonian_s:
   d.vals = h->d_vals;
   d.cvals = h->d_cvals;
   d.ell = e->d_ell;
+  d.ell16 = e->d_ell16;
   d.inst = inst;
   d.E = int32_t(h->emask.size());
   d.S = int32_t(h->cvals.size());
   d.stage_tables = 0;
   d.sweep_threads = 128;
+  d.n_elec = a->n_elec;
+  d.n_alpha = a->n_alpha;
   return d;
 }
 
@@ -393,7 +547,7 @@ bool use_real() { return (g_flags & VQE_FLAG_FORCE_COMPLEX) == 0; }
 // so, sets the shared-memory bytes and the descriptor's staging/sweep fields.
 bool resident_fit(vqe_ansatz_t a, const vqe_hamiltonian_s::Ell* e, bool real, InstDesc* d, size_t* smem) {
   if (g_flags & VQE_FLAG_FORCE_STREAMING) return false;
-  if (!e->use_ell || a->n > 16) return false;
+  if (!e->use_ell || !e->d_ell || a->n > 16) return false;
   if (a->pairs.size() > (size_t(1) << 24) || d->S > (1 << 24) || d->G > (1 << 20)) return false;
   int dev = 0, optin = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return false;
@@ -975,6 +1129,102 @@ int vqe_apply_hamiltonian(vqe_hamiltonian_t h, vqe_ansatz_t a, const double* psi
   return VQE_OK;
 }
 
+static int build_stream_batch(vqe_batch_s* B) {
+  StreamBatch& sb = B->sb;
+  for (int i : B->streaming[0]) {
+    sb.slots.push_back(i);
+    sb.descs.push_back(B->descs[i]);
+  }
+  const int n = int(sb.slots.size());
+  if (n == 0) return VQE_OK;
+  size_t off = 0;
+  int64_t eb = 0, gb = 0;
+  for (int s = 0; s < n; ++s) {
+    vqe_ansatz_t a = B->ans[sb.slots[s]];
+    const size_t vec = align256((size_t(1) << a->n) * 8);
+    sb.psi_off.push_back(int64_t(off));
+    sb.lam_off.push_back(int64_t(off + vec));
+    off += 2 * vec;
+    sb.ebase.push_back(eb);
+    eb += int64_t(a->sector.size());
+    sb.gbase.push_back(gb);
+    gb += int64_t(a->pairs.size());
+    sb.Mmax = std::max(sb.Mmax, a->M);
+  }
+  sb.cs_off = off;
+  off += align256(size_t(n) * size_t(std::max(sb.Mmax, 1)) * 16);
+  sb.ebuf_off = off;
+  off += align256(size_t(std::max<int64_t>(eb, 1)) * 8);
+  sb.total_energy = off;
+  sb.gbuf_off = off;
+  sb.total_grad = off + align256(size_t(std::max<int64_t>(gb, 1)) * 8);
+  // per-gate segments: slots that have pairs for gate m, in slot order
+  std::vector<int32_t> seg_inst;
+  std::vector<int64_t> seg_pref;
+  std::vector<std::pair<size_t, size_t>> where(sb.Mmax);
+  std::vector<int64_t> totals(sb.Mmax, 0);
+  std::vector<int32_t> nsegs(sb.Mmax, 0);
+  for (int m = 0; m < sb.Mmax; ++m) {
+    const size_t i0 = seg_inst.size(), p0 = seg_pref.size();
+    int64_t acc = 0;
+    seg_pref.push_back(0);
+    for (int s = 0; s < n; ++s) {
+      vqe_ansatz_t a = B->ans[sb.slots[s]];
+      if (m >= a->M) continue;
+      const int64_t cnt = a->pair_off[m + 1] - a->pair_off[m];
+      if (cnt == 0) continue;
+      seg_inst.push_back(s);
+      acc += cnt;
+      seg_pref.push_back(acc);
+    }
+    where[m] = std::make_pair(i0, p0);
+    totals[m] = acc;
+    nsegs[m] = int32_t(seg_inst.size() - i0);
+  }
+  std::vector<int32_t> out_inst(n);
+  std::vector<int64_t> out_pref(n + 1, 0);
+  for (int s = 0; s < n; ++s) {
+    out_inst[s] = s;
+    out_pref[s + 1] = out_pref[s] + int64_t(B->ans[sb.slots[s]]->sector.size());
+  }
+  std::vector<int32_t> gm_inst, gm_gate;
+  for (int s = 0; s < n; ++s)
+    for (int m = 0; m < B->ans[sb.slots[s]]->M; ++m) {
+      gm_inst.push_back(s);
+      gm_gate.push_back(m);
+    }
+  sb.n_gm = int64_t(gm_inst.size());
+  int rc;
+  if ((rc = upload(sb.descs, &sb.d_desc))) return rc;
+  if ((rc = upload(sb.psi_off, &sb.d_psi_off))) return rc;
+  if ((rc = upload(sb.lam_off, &sb.d_lam_off))) return rc;
+  if ((rc = upload(sb.ebase, &sb.d_ebase))) return rc;
+  if ((rc = upload(sb.gbase, &sb.d_gbase))) return rc;
+  if (seg_inst.empty()) seg_inst.push_back(0);
+  if ((rc = upload(seg_inst, &sb.d_seg_inst))) return rc;
+  if ((rc = upload(seg_pref, &sb.d_seg_pref))) return rc;
+  if ((rc = upload(out_inst, &sb.d_out_inst))) return rc;
+  if ((rc = upload(out_pref, &sb.d_out_pref))) return rc;
+  if (!gm_inst.empty()) {
+    if ((rc = upload(gm_inst, &sb.d_gm_inst))) return rc;
+    if ((rc = upload(gm_gate, &sb.d_gm_gate))) return rc;
+  }
+  sb.gate_segs.resize(sb.Mmax);
+  for (int m = 0; m < sb.Mmax; ++m) {
+    vqe::BatchSegs g;
+    g.inst = sb.d_seg_inst + where[m].first;
+    g.pref = sb.d_seg_pref + where[m].second;
+    g.nseg = nsegs[m];
+    g.total = totals[m];
+    sb.gate_segs[m] = g;
+  }
+  sb.out_segs.inst = sb.d_out_inst;
+  sb.out_segs.pref = sb.d_out_pref;
+  sb.out_segs.nseg = n;
+  sb.out_segs.total = out_pref[n];
+  return VQE_OK;
+}
+
 int vqe_create_batch(int n_inst, const vqe_hamiltonian_t* hams, const vqe_ansatz_t* ans, vqe_batch_t* out) {
   if (!out) return fail(VQE_ERR_INVALID_ARG, "NULL out");
   *out = nullptr;
@@ -1007,6 +1257,8 @@ int vqe_create_batch(int n_inst, const vqe_hamiltonian_t* hams, const vqe_ansatz
     int rc = upload(B->res_descs[mode], &B->d_res[mode]);
     if (rc) return rc;
   }
+  int rc = build_stream_batch(B.get());
+  if (rc) return rc;
   *out = B.release();
   return VQE_OK;
 }
@@ -1016,6 +1268,7 @@ int32_t vqe_batch_max_params(vqe_batch_t b) { return b ? b->max_params : 0; }
 size_t vqe_batch_workspace_bytes(vqe_batch_t b, int with_grad) {
   if (!b) return 0;
   const int mode = use_real() ? 0 : 1;
+  if (mode == 0) return b->sb.slots.empty() ? 0 : (with_grad ? b->sb.total_grad : b->sb.total_energy);
   size_t need = 0;
   for (int i : b->streaming[mode]) need = std::max(need, ws_layout(b->ans[i], mode == 1, with_grad != 0).total);
   return need;
@@ -1038,7 +1291,27 @@ static int batch_run(vqe_batch_t b, const double* theta, int64_t ld_theta, doubl
                                           grads, ld_grad, stream);
     if (ce != cudaSuccess) return cuda_fail(ce, "batched resident launch");
   }
-  if (!b->streaming[mode].empty()) {
+  if (real && !b->sb.slots.empty()) {
+    const StreamBatch& sb = b->sb;
+    const size_t need = with_grad ? sb.total_grad : sb.total_energy;
+    if ((rc = check_ws(ws, ws_bytes, need))) return rc;
+    vqe::BatchDev bd;
+    bd.desc = sb.d_desc;
+    bd.psi_off = sb.d_psi_off;
+    bd.lam_off = sb.d_lam_off;
+    bd.ebase = sb.d_ebase;
+    bd.gbase = sb.d_gbase;
+    bd.ws = static_cast<char*>(ws);
+    bd.cs = reinterpret_cast<double2*>(static_cast<char*>(ws) + sb.cs_off);
+    bd.ebuf = reinterpret_cast<double*>(static_cast<char*>(ws) + sb.ebuf_off);
+    bd.gbuf = reinterpret_cast<double*>(static_cast<char*>(ws) + sb.gbuf_off);
+    bd.n = int(sb.slots.size());
+    bd.Mmax = sb.Mmax;
+    cudaError_t ce = vqe::batch_stream_run(bd, sb.gate_segs.data(), sb.out_segs, sb.d_gm_inst, sb.d_gm_gate, sb.n_gm,
+                                           theta, ld_theta, energies, with_grad ? grads : nullptr, ld_grad,
+                                           sb.threads, stream);
+    if (ce != cudaSuccess) return cuda_fail(ce, "batched streaming launch");
+  } else if (!b->streaming[mode].empty()) {
     const size_t need = vqe_batch_workspace_bytes(b, with_grad);
     if ((rc = check_ws(ws, ws_bytes, need))) return rc;
     for (int i : b->streaming[mode]) {
@@ -1108,6 +1381,26 @@ int vqe_batch_energy_grad_host(vqe_batch_t b, const double* theta_host, int64_t 
   }
   ce = cudaStreamSynchronize(stream);
   if (ce != cudaSuccess) return cuda_fail(ce, "stream synchronize");
+  return VQE_OK;
+}
+
+int vqe_batch_set_tuning(vqe_batch_t b, int stream_threads, int sweep_threads) {
+  if (!b) return fail(VQE_ERR_INVALID_ARG, "NULL batch");
+  if (stream_threads != 0 && (stream_threads < 64 || stream_threads > 512 || stream_threads % 32))
+    return fail(VQE_ERR_INVALID_ARG, "stream_threads: a multiple of 32 in [64, 512], or 0 to keep");
+  if (sweep_threads != 0 && (sweep_threads < 32 || sweep_threads > vqe::kResidentThreads || sweep_threads % 32))
+    return fail(VQE_ERR_INVALID_ARG, "sweep_threads: a multiple of 32 in [32, 512], or 0 to keep");
+  if (stream_threads) b->sb.threads = stream_threads;
+  if (sweep_threads) {
+    for (int mode = 0; mode < 2; ++mode) {
+      for (auto& d : b->res_descs[mode]) d.sweep_threads = sweep_threads;
+      if (!b->res_descs[mode].empty()) {
+        cudaError_t e = cudaMemcpy(b->d_res[mode], b->res_descs[mode].data(),
+                                   b->res_descs[mode].size() * sizeof(InstDesc), cudaMemcpyHostToDevice);
+        if (e != cudaSuccess) return cuda_fail(e, "cudaMemcpy");
+      }
+    }
+  }
   return VQE_OK;
 }
 

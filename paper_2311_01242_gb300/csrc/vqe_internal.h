@@ -63,13 +63,44 @@ struct InstDesc {
   const uint32_t* emask;     // [entries]
   const double* vals;        // real tables (one double per slot)
   const double2* cvals;      // complex tables (one double2 per slot)
-  const uint32_t* ell;       // [W][D] column-major: groups connected to each output
+  const uint32_t* ell;       // [W][D] column-major: groups connected to each output (host-built)
+  const uint16_t* ell16;     // same, 16-bit entries built on the device (pad 0xFFFF); used when set
   // row of this instance in the caller's theta / energy / gradient arrays
   int64_t inst;
   int32_t E, S;              // folded entries and value slots of the Hamiltonian
   int32_t stage_tables;      // resident kernel: copy the group tables to shared memory
   int32_t sweep_threads;     // resident kernel: threads that run the gate sweeps
+  int32_t n_elec, n_alpha;   // sector (n_alpha < 0: electron number only)
 };
+
+// Gate-major batched streaming plan: one launch per gate index over every
+// instance that has that gate, one H psi launch over all instances. Work items
+// of a launch are the concatenation of per-instance segments; a thread finds
+// its segment by binary search over the segment prefix sums.
+struct BatchSegs {
+  const int32_t* inst;   // [nseg] instance slot of each segment
+  const int64_t* pref;   // [nseg + 1] exclusive prefix sums of segment sizes
+  int32_t nseg;
+  int64_t total;
+};
+
+struct BatchDev {
+  const InstDesc* desc;    // [n] descriptors of the streamed instances
+  const int64_t* psi_off;  // [n] byte offsets of psi in the workspace
+  const int64_t* lam_off;  // [n] byte offsets of lambda
+  const int64_t* ebase;    // [n] first slot in the per-output energy buffer
+  const int64_t* gbase;    // [n] first slot in the per-pair gradient buffer
+  char* ws;                // workspace base
+  double2* cs;             // [n * Mmax] cos/sin
+  double* ebuf;            // [sum D] per-output psi*lambda
+  double* gbuf;            // [sum P] per-pair gradient contributions
+  int32_t n, Mmax;
+};
+
+cudaError_t batch_stream_run(const BatchDev& b, const BatchSegs* gate_segs, const BatchSegs& out_segs,
+                             const int32_t* d_gm_inst, const int32_t* d_gm_gate, int64_t n_gm,
+                             const double* theta, int64_t ld_theta, double* energy, double* grad,
+                             int64_t ld_grad, int threads, cudaStream_t stream);
 
 // Shared-memory layout of the resident kernel (byte offsets), computed the same
 // way on the host (to size the launch) and on the device (to carve it).
@@ -100,7 +131,9 @@ __host__ __device__ inline ResidentLayout resident_layout(int n, int M, int P, i
   L.pairs = align_up(o, 16u);
   o = L.pairs + uint32_t(P) * 4u;
   L.uni = align_up(o, 16u);
-  const uint32_t gb = uint32_t(P) * 8u;  // per-pair gradient contributions (reverse sweep)
+  // gradient contributions of the reverse sweep: two per pair with real amplitudes
+  // (one per lane of the pair), one per pair with complex amplitudes
+  const uint32_t gb = uint32_t(P) * (real ? 16u : 8u);
   const uint32_t tb = stage ? staged_table_bytes(G, E, S, real) : 0u;  // tables (H psi)
   o = L.uni + (gb > tb ? gb : tb);
   L.red = align_up(o, 16u);
@@ -147,6 +180,15 @@ cudaError_t stream_state(const InstDesc& d, const StreamPlan& sp, const StreamBu
 cudaError_t stream_apply_h(const InstDesc& d, const StreamPlan& sp, const StreamBuffers& b,
                            const double* psi_in, double* lam_out, double* energy,
                            cudaStream_t stream);
+
+// Device-built connectivity table (16-bit group indices) for large sectors:
+// len[r] = groups connected to output r; then rows filled in `order`.
+cudaError_t ell_device_count(const uint32_t* sector, int64_t D, const GroupRec* groups, int G,
+                             const int32_t* order, int n_elec, int n_alpha, int32_t* len, int32_t* wmax,
+                             cudaStream_t stream);
+cudaError_t ell_device_fill(const uint32_t* sector, int64_t D, const GroupRec* groups, int G,
+                            const int32_t* order, int n_elec, int n_alpha, int W, uint16_t* ell,
+                            cudaStream_t stream);
 
 // Host helpers for the allocation-free entry point (vqe_static.cu).
 int prepare_noalloc(vqe_hamiltonian_s* h, vqe_ansatz_s* a, bool with_grad, InstDesc* d, StreamPlan* sp,

@@ -63,11 +63,16 @@ template <> struct Amp<true> {
   static __device__ __forceinline__ void mac(T& acc, C f, T p) { acc = fma(f, p, acc); }
   // Re(conj(a) * b)
   static __device__ __forceinline__ double redot(T a, T b) { return a * b; }
-  // (c a - ss b, ss a + c b)
-  static __device__ __forceinline__ void rot(T& a, T& b, double c, double ss) {
+  // (c a - ss b, ss a + c b); nss = -ss comes in precomputed (sign bit flipped
+  // in the integer pipe) so that no FP64 negation is issued
+  static __device__ __forceinline__ void rot(T& a, T& b, double c, double ss, double nss) {
     const T a0 = a;
-    a = fma(-ss, b, c * a0);
+    a = fma(nss, b, c * a0);
     b = fma(ss, a0, c * b);
+  }
+  // lb pa - la pb
+  static __device__ __forceinline__ double cross(T lb, T pa, T la, T pb) {
+    return fma(lb, pa, -(la * pb));
   }
   static __device__ __forceinline__ double2 to_c(T a) { return make_double2(a, 0.0); }
   static __device__ __forceinline__ T from_c(double2 a) { return a.x; }
@@ -84,12 +89,15 @@ template <> struct Amp<false> {
     acc.y = fma(f.x, p.y, fma(f.y, p.x, acc.y));
   }
   static __device__ __forceinline__ double redot(T a, T b) { return fma(a.x, b.x, a.y * b.y); }
-  static __device__ __forceinline__ void rot(T& a, T& b, double c, double ss) {
+  static __device__ __forceinline__ void rot(T& a, T& b, double c, double ss, double nss) {
     const T a0 = a;
-    a.x = fma(-ss, b.x, c * a0.x);
-    a.y = fma(-ss, b.y, c * a0.y);
+    a.x = fma(nss, b.x, c * a0.x);
+    a.y = fma(nss, b.y, c * a0.y);
     b.x = fma(ss, a0.x, c * b.x);
     b.y = fma(ss, a0.y, c * b.y);
+  }
+  static __device__ __forceinline__ double cross(T lb, T pa, T la, T pb) {
+    return fma(lb.x, pa.x, fma(lb.y, pa.y, -fma(la.x, pb.x, la.y * pb.y)));
   }
   static __device__ __forceinline__ double2 to_c(T a) { return a; }
   static __device__ __forceinline__ T from_c(double2 a) { return a; }
@@ -171,6 +179,15 @@ __device__ __forceinline__ typename Amp<REAL>::C group_coef(const GroupRec& g, c
 __device__ __forceinline__ bool in_sector(uint32_t k, int n_elec, int n_alpha) {
   if (__popc(k) != n_elec) return false;
   return n_alpha < 0 || __popc(k & 0x55555555u) == n_alpha;
+}
+
+// Entry j of output r's connectivity row (kEllPad past the row's end).
+__device__ __forceinline__ uint32_t ell_at(const uint32_t* ell, const uint16_t* ell16, int64_t idx) {
+  if (ell16) {
+    const uint32_t v = __ldg(ell16 + idx);
+    return v == 0xFFFFu ? kEllPad : v;
+  }
+  return __ldg(ell + idx);
 }
 
 // Deterministic block sum; the result is valid in thread 0.
@@ -270,7 +287,11 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
   // lane-interleaved position of this thread in the sweep: consecutive pairs go
   // to consecutive warps so every sub-partition gets FP64 work on small gates
   const int swarps = sw >> 5;
-  const int spos = (tid & 31) * swarps + (tid >> 5);
+  // complex: one lane per pair, consecutive pairs on consecutive warps;
+  // real: two adjacent lanes per pair (role 0 and 1), pairs dealt the same way
+  const int role = REAL ? (tid & 1) : 0;
+  const int pstride = REAL ? (sw >> 1) : sw;
+  const int spos = REAL ? (((tid & 31) >> 1) * swarps + (tid >> 5)) : ((tid & 31) * swarps + (tid >> 5));
 
   // a2: forward sweep. The next gate's record, cos/sin and first pair index
   // are loaded before the current gate runs, off the barrier-to-barrier path.
@@ -292,14 +313,36 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
         if (spos < cntn) kfn = pairs[p0n + spos];
       }
       const int s0 = gr.sign0 < 0;
-      for (int q = spos; q < cnt; q += sw) {
-        const uint32_t k = (q == spos) ? kf : pairs[p0 + q];
-        const uint32_t k2 = k ^ gr.flip;
-        const double ss = sflip(c_s.y, parity32(k & gr.par) ^ s0);
-        T a = psi[k], b = psi[k2];
-        A::rot(a, b, c_s.x, ss);
-        psi[k] = a;
-        psi[k2] = b;
+      if constexpr (REAL) {
+        // two lanes per pair: role 0 writes c a - s b to k, role 1 writes c b + s a
+        // to k2; both lanes read before either writes (warp-uniform trip count)
+        for (int q0 = 0; q0 < cnt; q0 += pstride) {
+          const int q = q0 + spos;
+          const bool act = q < cnt;
+          uint32_t kd = 0;
+          double self = 0.0, other = 0.0, coef = 0.0;
+          if (act) {
+            const uint32_t k = (q0 == 0) ? kf : pairs[p0 + q];
+            const uint32_t k2 = k ^ gr.flip;
+            kd = role ? k2 : k;
+            self = psi[kd];
+            other = psi[role ? k : k2];
+            coef = sflip(c_s.y, parity32(k & gr.par) ^ s0 ^ role ^ 1);
+          }
+          __syncwarp();
+          if (act) psi[kd] = fma(coef, other, c_s.x * self);
+        }
+      } else {
+        for (int q = spos; q < cnt; q += sw) {
+          const uint32_t k = (q == spos) ? kf : pairs[p0 + q];
+          const uint32_t k2 = k ^ gr.flip;
+          const int sb = parity32(k & gr.par) ^ s0;
+          const double ss = sflip(c_s.y, sb), nss = sflip(c_s.y, sb ^ 1);
+          T a = psi[k], b = psi[k2];
+          A::rot(a, b, c_s.x, ss, nss);
+          psi[k] = a;
+          psi[k2] = b;
+        }
       }
       sweep_barrier(sw);
       gr = grn;
@@ -371,19 +414,49 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
         if (spos < cntn) kfn = pairs[p0n + spos];
       }
       const int s0 = gr.sign0 < 0;
-      for (int q = spos; q < cnt; q += sw) {
-        const uint32_t k = (q == spos) ? kf : pairs[p0 + q];
-        const uint32_t k2 = k ^ gr.flip;
-        const int sb = parity32(k & gr.par) ^ s0;
-        const double ss = sflip(c_s.y, sb);
-        T pa = psi[k], pb = psi[k2], la = lam[k], lb = lam[k2];
-        gbuf[p0 + q] = sflip(A::redot(lb, pa) - A::redot(la, pb), sb);
-        A::rot(pa, pb, c_s.x, -ss);
-        A::rot(la, lb, c_s.x, -ss);
-        psi[k] = pa;
-        psi[k2] = pb;
-        lam[k] = la;
-        lam[k2] = lb;
+      if constexpr (REAL) {
+        // two lanes per pair: role 0 keeps s lb pa and un-applies at k, role 1
+        // keeps -s la pb and un-applies at k2 (phi and lambda alike)
+        for (int q0 = 0; q0 < cnt; q0 += pstride) {
+          const int q = q0 + spos;
+          const bool act = q < cnt;
+          uint32_t ks = 0;
+          int sr_bit = 0;
+          double ps = 0.0, po = 0.0, ls = 0.0, lo = 0.0;
+          if (act) {
+            const uint32_t k = (q0 == 0) ? kf : pairs[p0 + q];
+            const uint32_t k2 = k ^ gr.flip;
+            sr_bit = parity32(k & gr.par) ^ s0 ^ role;
+            ks = role ? k2 : k;
+            const uint32_t ko = role ? k : k2;
+            ps = psi[ks];
+            po = psi[ko];
+            ls = lam[ks];
+            lo = lam[ko];
+          }
+          __syncwarp();
+          if (act) {
+            gbuf[2 * (p0 + q) + role] = sflip(lo * ps, sr_bit);
+            const double sr = sflip(c_s.y, sr_bit);
+            psi[ks] = fma(sr, po, c_s.x * ps);
+            lam[ks] = fma(sr, lo, c_s.x * ls);
+          }
+        }
+      } else {
+        for (int q = spos; q < cnt; q += sw) {
+          const uint32_t k = (q == spos) ? kf : pairs[p0 + q];
+          const uint32_t k2 = k ^ gr.flip;
+          const int sb = parity32(k & gr.par) ^ s0;
+          const double ss = sflip(c_s.y, sb), nss = sflip(c_s.y, sb ^ 1);
+          T pa = psi[k], pb = psi[k2], la = lam[k], lb = lam[k2];
+          gbuf[p0 + q] = sflip(A::cross(lb, pa, la, pb), sb);
+          A::rot(pa, pb, c_s.x, nss, ss);
+          A::rot(la, lb, c_s.x, nss, ss);
+          psi[k] = pa;
+          psi[k2] = pb;
+          lam[k] = la;
+          lam[k2] = lb;
+        }
       }
       sweep_barrier(sw);
       gr = grn;
@@ -402,7 +475,8 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
     const int m = t >> 2, qtr = t & 3;
     double s = 0.0;
     if (m < M) {
-      const int p0 = poff[m], p1 = poff[m + 1];
+      const int per = REAL ? 2 : 1;  // contributions per pair
+      const int p0 = per * poff[m], p1 = per * poff[m + 1];
       const int len = p1 - p0, chunk = (len + 3) >> 2;
       const int a = p0 + qtr * chunk, b = min(p1, a + chunk);
       for (int p = a; p < b; ++p) s += gbuf[p];
@@ -446,9 +520,10 @@ __global__ void k_gate_fwd(const uint32_t* __restrict__ pairs, int64_t P, const 
        p += int64_t(gridDim.x) * blockDim.x) {
     const uint32_t k = __ldg(pairs + p);
     const uint32_t k2 = k ^ gr.flip;
-    const double ss = sflip(c_s.y, parity32(k & gr.par) ^ s0);
+    const int sb = parity32(k & gr.par) ^ s0;
+    const double ss = sflip(c_s.y, sb), nss = sflip(c_s.y, sb ^ 1);
     T a = psi[k], b = psi[k2];
-    A::rot(a, b, c_s.x, ss);
+    A::rot(a, b, c_s.x, ss, nss);
     psi[k] = a;
     psi[k2] = b;
   }
@@ -472,7 +547,7 @@ k_hpsi(const InstDesc d, int n_elec, int n_alpha, const typename Amp<REAL>::T* _
     T acc = A::zero();
     if (ELL) {
       for (int j = 0; j < d.W; ++j) {
-        const uint32_t gi = __ldg(d.ell + int64_t(j) * d.D + r);
+        const uint32_t gi = ell_at(d.ell, d.ell16, int64_t(j) * d.D + r);
         if (gi == kEllPad) break;
         const GroupRec g = load_group(d.groups + gi);
         const uint32_t src = k ^ g.x;
@@ -510,11 +585,11 @@ k_gate_adj(const uint32_t* __restrict__ pairs, int64_t P, const GateRec* __restr
     const uint32_t k = __ldg(pairs + p);
     const uint32_t k2 = k ^ gr.flip;
     const int sb = parity32(k & gr.par) ^ s0;
-    const double ss = sflip(c_s.y, sb);
+    const double ss = sflip(c_s.y, sb), nss = sflip(c_s.y, sb ^ 1);
     T pa = phi[k], pb = phi[k2], la = lam[k], lb = lam[k2];
-    acc += sflip(A::redot(lb, pa) - A::redot(la, pb), sb);
-    A::rot(pa, pb, c_s.x, -ss);
-    A::rot(la, lb, c_s.x, -ss);
+    acc += sflip(A::cross(lb, pa, la, pb), sb);
+    A::rot(pa, pb, c_s.x, nss, ss);
+    A::rot(la, lb, c_s.x, nss, ss);
     phi[k] = pa;
     phi[k2] = pb;
     lam[k] = la;
@@ -559,6 +634,192 @@ __global__ void k_gather_in(const uint32_t* __restrict__ sector, int64_t D, cons
 }
 
 }  // namespace
+
+// ---------------------------------------------------------------- batched streaming (gate-major)
+__device__ __forceinline__ int find_seg(const int64_t* __restrict__ pref, int nseg, int64_t item) {
+  int lo = 0, hi = nseg;  // pref[lo] <= item < pref[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(pref + mid) <= item)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
+}
+
+// cos/sin of every (instance, gate)
+__global__ void kb_trig(BatchDev b, const double* __restrict__ theta, int64_t ld) {
+  const int64_t n_items = int64_t(b.n) * b.Mmax;
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < n_items; t += int64_t(gridDim.x) * blockDim.x) {
+    const int i = int(t / b.Mmax), m = int(t % b.Mmax);
+    const InstDesc* d = b.desc + i;
+    if (m < d->M) {
+      double sn, c;
+      sincos(theta[d->inst * ld + m], &sn, &c);
+      b.cs[t] = make_double2(c, sn);
+    }
+  }
+}
+
+__global__ void kb_init(BatchDev b, BatchSegs sg) {
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < sg.total; t += int64_t(gridDim.x) * blockDim.x) {
+    const int s = find_seg(sg.pref, sg.nseg, t);
+    const int i = __ldg(sg.inst + s);
+    const int64_t r = t - __ldg(sg.pref + s);
+    const InstDesc* d = b.desc + i;
+    double* psi = reinterpret_cast<double*>(b.ws + b.psi_off[i]);
+    const uint32_t k = __ldg(d->sector + r);
+    psi[k] = (k == d->hf) ? 1.0 : 0.0;
+  }
+}
+
+__global__ void __launch_bounds__(512) kb_gate_fwd(int m, BatchDev b, BatchSegs sg) {
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < sg.total; t += int64_t(gridDim.x) * blockDim.x) {
+    const int s = find_seg(sg.pref, sg.nseg, t);
+    const int i = __ldg(sg.inst + s);
+    const int64_t q = t - __ldg(sg.pref + s);
+    const InstDesc* d = b.desc + i;
+    double* psi = reinterpret_cast<double*>(b.ws + b.psi_off[i]);
+    const GateRec gr = load_gate(d->gates + m);
+    const double2 c_s = b.cs[int64_t(i) * b.Mmax + m];
+    const uint32_t k = __ldg(d->pairs + __ldg(d->pair_off + m) + q);
+    const uint32_t k2 = k ^ gr.flip;
+    const int sb = parity32(k & gr.par) ^ (gr.sign0 < 0);
+    const double ss = sflip(c_s.y, sb), nss = sflip(c_s.y, sb ^ 1);
+    double a = psi[k], bb = psi[k2];
+    Amp<true>::rot(a, bb, c_s.x, ss, nss);
+    psi[k] = a;
+    psi[k2] = bb;
+  }
+}
+
+__global__ void __launch_bounds__(512, 1) kb_hpsi(BatchDev b, BatchSegs sg) {
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < sg.total; t += int64_t(gridDim.x) * blockDim.x) {
+    const int s = find_seg(sg.pref, sg.nseg, t);
+    const int i = __ldg(sg.inst + s);
+    const int64_t r = t - __ldg(sg.pref + s);
+    const InstDesc* d = b.desc + i;
+    const double* psi = reinterpret_cast<const double*>(b.ws + b.psi_off[i]);
+    double* lam = reinterpret_cast<double*>(b.ws + b.lam_off[i]);
+    const uint32_t k = __ldg(d->sector + r);
+    const GroupRec* groups = d->groups;
+    const uint32_t* emask = d->emask;
+    const double* vals = d->vals;
+    const int W = d->W, G = d->G;
+    const int64_t D = d->D;
+    double acc = 0.0;
+    if (W > 0) {
+      const uint32_t* ell = d->ell;
+      const uint16_t* ell16 = d->ell16;
+      for (int j = 0; j < W; ++j) {
+        const uint32_t gi = ell_at(ell, ell16, int64_t(j) * D + r);
+        if (gi == kEllPad) break;
+        const GroupRec g = load_group(groups + gi);
+        const uint32_t src = k ^ g.x;
+        acc = fma(group_coef<true>(g, emask, vals, src), psi[src], acc);
+      }
+    } else {
+      const int ne = d->n_elec, na = d->n_alpha;
+      for (int gi = 0; gi < G; ++gi) {
+        const GroupRec g = load_group(groups + gi);
+        const uint32_t src = k ^ g.x;
+        if (!in_sector(src, ne, na)) continue;
+        acc = fma(group_coef<true>(g, emask, vals, src), psi[src], acc);
+      }
+    }
+    lam[k] = acc;
+    b.ebuf[b.ebase[i] + r] = psi[k] * acc;
+  }
+}
+
+// E of instance slot blockIdx.x: fixed-order sum of its per-output terms
+__global__ void kb_energy(BatchDev b, double* __restrict__ energy) {
+  __shared__ double red[32];
+  const int i = blockIdx.x;
+  const InstDesc* d = b.desc + i;
+  const double* e = b.ebuf + b.ebase[i];
+  double acc = 0.0;
+  for (int64_t r = threadIdx.x; r < d->D; r += blockDim.x) acc += e[r];
+  const double tot = block_sum(acc, red);
+  if (threadIdx.x == 0) energy[d->inst] = tot;
+}
+
+__global__ void __launch_bounds__(512) kb_gate_adj(int m, BatchDev b, BatchSegs sg) {
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < sg.total; t += int64_t(gridDim.x) * blockDim.x) {
+    const int s = find_seg(sg.pref, sg.nseg, t);
+    const int i = __ldg(sg.inst + s);
+    const int64_t q = t - __ldg(sg.pref + s);
+    const InstDesc* d = b.desc + i;
+    double* phi = reinterpret_cast<double*>(b.ws + b.psi_off[i]);
+    double* lam = reinterpret_cast<double*>(b.ws + b.lam_off[i]);
+    const GateRec gr = load_gate(d->gates + m);
+    const double2 c_s = b.cs[int64_t(i) * b.Mmax + m];
+    const int64_t p = __ldg(d->pair_off + m) + q;
+    const uint32_t k = __ldg(d->pairs + p);
+    const uint32_t k2 = k ^ gr.flip;
+    const int sb = parity32(k & gr.par) ^ (gr.sign0 < 0);
+    const double ss = sflip(c_s.y, sb), nss = sflip(c_s.y, sb ^ 1);
+    double pa = phi[k], pb = phi[k2], la = lam[k], lb = lam[k2];
+    b.gbuf[b.gbase[i] + p] = sflip(Amp<true>::cross(lb, pa, la, pb), sb);
+    Amp<true>::rot(pa, pb, c_s.x, nss, ss);
+    Amp<true>::rot(la, lb, c_s.x, nss, ss);
+    phi[k] = pa;
+    phi[k2] = pb;
+    lam[k] = la;
+    lam[k2] = lb;
+  }
+}
+
+// g of (instance, gate) pair blockIdx.x: fixed-order sum of its pair contributions
+__global__ void kb_grad(BatchDev b, const int32_t* __restrict__ gm_inst, const int32_t* __restrict__ gm_gate,
+                        double* __restrict__ grad, int64_t ld_grad) {
+  __shared__ double red[32];
+  const int i = gm_inst[blockIdx.x], m = gm_gate[blockIdx.x];
+  const InstDesc* d = b.desc + i;
+  const int64_t p0 = d->pair_off[m], p1 = d->pair_off[m + 1];
+  const double* gb = b.gbuf + b.gbase[i];
+  double acc = 0.0;
+  for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) acc += gb[p];
+  const double tot = block_sum(acc, red);
+  if (threadIdx.x == 0) grad[d->inst * ld_grad + m] = 2.0 * tot;
+}
+
+inline int batch_grid(int64_t total, int threads) {
+  int64_t g = (total + threads - 1) / threads;
+  if (g < 1) g = 1;
+  if (g > 152 * 16) g = 152 * 16;
+  return int(g);
+}
+
+// ---------------------------------------------------------------- device-built connectivity
+__global__ void k_ell_count(const uint32_t* __restrict__ sector, int64_t D, const GroupRec* __restrict__ groups, int G,
+                            int n_elec, int n_alpha, int32_t* __restrict__ len, int32_t* __restrict__ wmax) {
+  for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < D; r += int64_t(gridDim.x) * blockDim.x) {
+    const uint32_t k = __ldg(sector + r);
+    int c = 0;
+    for (int g = 0; g < G; ++g) c += in_sector(k ^ __ldg(&groups[g].x), n_elec, n_alpha);
+    len[r] = c;
+    atomicMax(wmax, c);
+  }
+}
+
+__global__ void k_ell_fill(const uint32_t* __restrict__ sector, int64_t D, const GroupRec* __restrict__ groups, int G,
+                           const int32_t* __restrict__ order, int n_elec, int n_alpha, int W,
+                           uint16_t* __restrict__ ell) {
+  for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < D; r += int64_t(gridDim.x) * blockDim.x) {
+    const uint32_t k = __ldg(sector + r);
+    int j = 0;
+    for (int oi = 0; oi < G && j < W; ++oi) {
+      const int g = __ldg(order + oi);
+      if (in_sector(k ^ __ldg(&groups[g].x), n_elec, n_alpha)) {
+        ell[int64_t(j) * D + r] = uint16_t(g);
+        ++j;
+      }
+    }
+    for (; j < W; ++j) ell[int64_t(j) * D + r] = 0xFFFFu;
+  }
+}
 
 // ---------------------------------------------------------------- launchers
 cudaError_t set_resident_smem_limit(size_t smem, bool real) {
@@ -669,6 +930,43 @@ cudaError_t stream_apply_h(const InstDesc& d, const StreamPlan& sp, const Stream
   if (e != cudaSuccess) return e;
   k_scatter_out<false><<<stream_grid(d.D), kStreamThreads, 0, stream>>>(
       d.sector, d.D, static_cast<const double2*>(b.lam), reinterpret_cast<double2*>(lam_out));
+  return cudaGetLastError();
+}
+
+cudaError_t batch_stream_run(const BatchDev& b, const BatchSegs* gate_segs, const BatchSegs& out_segs,
+                             const int32_t* d_gm_inst, const int32_t* d_gm_gate, int64_t n_gm,
+                             const double* theta, int64_t ld_theta, double* energy, double* grad,
+                             int64_t ld_grad, int threads, cudaStream_t stream) {
+  if (b.n == 0) return cudaSuccess;
+  const int nt = threads;
+  if (b.Mmax > 0) kb_trig<<<batch_grid(int64_t(b.n) * b.Mmax, nt), nt, 0, stream>>>(b, theta, ld_theta);
+  kb_init<<<batch_grid(out_segs.total, nt), nt, 0, stream>>>(b, out_segs);
+  for (int m = 0; m < b.Mmax; ++m)
+    if (gate_segs[m].total > 0)
+      kb_gate_fwd<<<batch_grid(gate_segs[m].total, nt), nt, 0, stream>>>(m, b, gate_segs[m]);
+  kb_hpsi<<<batch_grid(out_segs.total, nt), nt, 0, stream>>>(b, out_segs);
+  kb_energy<<<b.n, 256, 0, stream>>>(b, energy);
+  if (grad) {
+    for (int m = b.Mmax - 1; m >= 0; --m)
+      if (gate_segs[m].total > 0)
+        kb_gate_adj<<<batch_grid(gate_segs[m].total, nt), nt, 0, stream>>>(m, b, gate_segs[m]);
+    if (n_gm > 0) kb_grad<<<int(n_gm), 128, 0, stream>>>(b, d_gm_inst, d_gm_gate, grad, ld_grad);
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t ell_device_count(const uint32_t* sector, int64_t D, const GroupRec* groups, int G, const int32_t* order,
+                             int n_elec, int n_alpha, int32_t* len, int32_t* wmax, cudaStream_t stream) {
+  (void)order;
+  cudaError_t e = cudaMemsetAsync(wmax, 0, sizeof(int32_t), stream);
+  if (e != cudaSuccess) return e;
+  k_ell_count<<<stream_grid(D) * 4, kStreamThreads, 0, stream>>>(sector, D, groups, G, n_elec, n_alpha, len, wmax);
+  return cudaGetLastError();
+}
+
+cudaError_t ell_device_fill(const uint32_t* sector, int64_t D, const GroupRec* groups, int G, const int32_t* order,
+                            int n_elec, int n_alpha, int W, uint16_t* ell, cudaStream_t stream) {
+  k_ell_fill<<<stream_grid(D) * 4, kStreamThreads, 0, stream>>>(sector, D, groups, G, order, n_elec, n_alpha, W, ell);
   return cudaGetLastError();
 }
 

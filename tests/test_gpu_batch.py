@@ -1,0 +1,85 @@
+"""Batched evaluation of uneven instances: gate-major streaming, CUDA-graph
+replay and autotuned launch shapes, checked against single-instance calls and
+the oracle."""
+import numpy as np
+import pytest
+import torch
+
+import oracle
+import synth
+import paper_2311_01242_gb300 as vq
+from paper_2311_01242_gb300 import batch as vb
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def mixed():
+    """Two 12-qubit scan geometries (shared-memory resident) and config-2
+    instances of 14 and 16 qubits (streamed), in one batch."""
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    vq.load()
+    ns, _ = synth.configs.config2_sizes()
+    picks = [int(np.nonzero(ns == n)[0][k]) for n in (14, 16) for k in range(3)]
+    insts = [synth.config2_instance(j) for j in picks]
+    w1 = synth.config1(2)
+    insts += [(w1.problems[i], w1.excitations[i], w1.thetas[i]) for i in range(2)]
+    hams = [vq.Hamiltonian.from_problem(p) for p, _, _ in insts]
+    ans = [vq.Ansatz(p.n_qubits, synth.hf_bitstring(p.n_elec), e) for p, e, _ in insts]
+    B = vq.Batch(hams, ans)
+    theta = torch.zeros(len(insts), B.max_params, dtype=torch.float64)
+    for i, (_, _, th) in enumerate(insts):
+        theta[i, :len(th)] = torch.as_tensor(th)
+    return insts, hams, ans, B, theta.cuda()
+
+
+def test_batch_matches_single_instance_calls(mixed):
+    insts, hams, ans, B, theta = mixed
+    e, g = B.energy_grad(theta)
+    e, g = e.cpu().numpy(), g.cpu().numpy()
+    for i, (p, exc, th) in enumerate(insts):
+        e1, g1 = vq.energy_grad(hams[i], ans[i], theta[i, :len(th)])
+        assert abs(float(e1) - e[i]) <= 1e-12
+        assert np.abs(g1.cpu().numpy() - g[i, :len(th)]).max() <= 1e-12
+
+
+def test_batch_matches_oracle_on_streamed_instances(mixed):
+    insts, hams, ans, B, theta = mixed
+    e, g = B.energy_grad(theta)
+    e, g = e.cpu().numpy(), g.cpu().numpy()
+    for i in (0, 3):
+        p, exc, th = insts[i]
+        idx = [0, len(exc) - 1]
+        model = oracle.EnergyModel.from_problem(p, full=False)
+        e_o, g_o = oracle.gradient_direct(model, synth.hf_bitstring(p.n_elec), exc, th, idx)
+        assert abs(e[i] - e_o) <= 1e-10
+        assert np.abs(g[i, idx] - g_o).max() <= 1e-9
+
+
+def _same(e, g, e_ref, g_ref, ms):
+    """Bitwise equal energies and gradients (each row up to its instance's M)."""
+    if not torch.equal(e, e_ref):
+        return False
+    return all(torch.equal(g[i, :m], g_ref[i, :m]) for i, m in enumerate(ms))
+
+
+def test_graph_replay_and_tuning_do_not_change_results(mixed, tmp_path):
+    insts, hams, ans, B, theta = mixed
+    ms = [a.n_params for a in ans]
+    e_ref, g_ref = [t.clone() for t in B.energy_grad(theta)]
+    gb = vb.GraphBatch(B)
+    e, g = gb(theta)
+    assert _same(e, g, e_ref, g_ref, ms)
+    theta2 = theta + 0.01
+    e2, g2 = gb(theta2)
+    e2_ref, g2_ref = B.energy_grad(theta2.contiguous())
+    assert _same(e2, g2, e2_ref, g2_ref, ms)
+    cache = str(tmp_path / "tune.json")
+    choice, timings = vb.autotune(B, theta, stream_threads=(128, 512), sweep_threads=(64, 128), reps=2,
+                                  cache_path=cache)
+    assert len(timings) == 4 and choice in [(128, 64), (128, 128), (512, 64), (512, 128)]
+    e3, g3 = B.energy_grad(theta)
+    assert _same(e3, g3, e_ref, g_ref, ms)
+    choice2, _ = vb.autotune(B, theta, cache_path=cache)  # served from the cache
+    assert choice2 == choice

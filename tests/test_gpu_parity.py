@@ -333,5 +333,5 @@ def test_autograd_function():
     e = vq.vqe_energy(t, H, A)
     (3.0 * e).backward()
     e_o, g_o = oracle_eg(p, exc, th)
-    assert abs(float(e) - e_o) <= E_TOL
+    assert abs(float(e.detach()) - e_o) <= E_TOL
     assert np.abs(t.grad.cpu().numpy() - 3.0 * g_o).max() <= 3 * G_TOL
