@@ -35,7 +35,7 @@ FP64_DFMA_PER_CLK_SM = 2
 N_SMS = 152
 SM_MAX_MHZ = 2070.0
 FP64_PEAK_TFLOPS = FP64_DFMA_PER_CLK_SM * N_SMS * SM_MAX_MHZ * 1e6 * 2 / 1e12
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_resident_config1.json")
+PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_resident_config1.md")
 KERNEL_SRC = os.path.join(ROOT, "paper_2311_01242_gb300", "csrc", "vqe_kernels.cu")
 
 
@@ -242,98 +242,20 @@ def kernel_source_hash():
 
 
 def profiled_traffic(per_launch_units):
-    """dram bytes per launch from the committed ncu summary, if it was taken on
-    the current kernel source; else None."""
+    """dram bytes per launch from the committed ncu summary (profiles/), scaled
+    to per_launch_units, if it was taken on the current kernel source; else None."""
+    import re
     try:
         with open(PROFILE_SUMMARY) as f:
-            prof = json.load(f)
-    except (OSError, ValueError):
+            text = f.read()
+    except OSError:
         return None
-    if prof.get("kernel_source_sha256_16") != kernel_source_hash():
+    sha = re.search(r"sha256 \(first 16 hex\): `([0-9a-f]+)`", text)
+    b = re.search(r"dram_bytes_per_launch: (\d+)", text)
+    units = re.search(r"units_per_launch: (\d+)", text)
+    if not (sha and b and units) or sha.group(1) != kernel_source_hash():
         return None
-    b = prof.get("dram_bytes_per_launch")
-    units = prof.get("units_per_launch")
-    if b is None or not units:
-        return None
-    return b * per_launch_units / units
-
-
-def run_warmstart(args):
-    """16 qubits, 8 electrons, 512-point scan r in [0.7, 4.0], 360 UCCSD angles:
-    plain VQE with continuation on every 4th point trains the network; at
-    held-out points, BFGS runs from the HF start, from the nearest earlier
-    training point's angles (continuation), and from the network prediction
-    (HF when the prediction's energy is not below HF). Reports evaluations and
-    seconds until E <= E_exact + 1 mHa (exact: GPU Lanczos in the sector)."""
-    import numpy as np
-    import torch
-
-    import synth
-    import paper_2311_01242_gb300 as vq
-    from paper_2311_01242_gb300 import warmstart as ws
-
-    torch.cuda.set_device(0)
-    vq.load()
-    w = synth.config4()
-    scan = w.scan
-    rs = scan.rs
-    n, ne = 2 * scan.n_spatial, scan.n_elec
-    A = vq.Ansatz(n, synth.hf_bitstring(ne), w.excitations[0])
-    train = list(range(0, len(rs), 4))
-    rest = [i for i in range(len(rs)) if i % 4 != 0]
-    held = rest[::max(1, len(rest) // args.held_out)][:args.held_out]
-    t0 = time.perf_counter()
-    geoms = [ws.Geometry(scan.at(rs[i]), rs[i], A, graph=True) for i in train]
-    t_create = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    thetas, energies, evals = ws.training_set(geoms, gtol=1e-6)
-    t_data = time.perf_counter() - t0
-    t0 = time.perf_counter()
-    model = ws.WarmStart(geoms[0].features.size, A.n_params, hidden=256, seed=0)
-    hist = model.fit(np.stack([g.features for g in geoms]), thetas, steps=3000, lr=1e-3)
-    torch.cuda.synchronize()
-    t_fit = time.perf_counter() - t0
-    arms = {"hf": [], "continuation": [], "mlp": []}
-    fallbacks, reached_exact = 0, 0
-    for i in held:
-        g = ws.Geometry(scan.at(rs[i]), rs[i], A, graph=True)
-        e0 = ws.lanczos_ground(g.H, A, n, ne)
-        prev = max(j for j, ti in enumerate(train) if ti < i)
-        tp = time.perf_counter()
-        pred = model.predict(g.features[None, :])[0]
-        e_pred = float(vq.energy(g.H, A, pred))
-        e_hf = float(vq.energy(g.H, A, np.zeros(A.n_params)))
-        start = pred
-        if not e_pred < e_hf:
-            start = np.zeros(A.n_params)
-            fallbacks += 1
-        t_pred = time.perf_counter() - tp
-        res = ws.compare_starts(g, {"hf": np.zeros(A.n_params), "continuation": thetas[prev], "mlp": start}, e0,
-                                gtol=1e-6)
-        reached_exact += int(res["reached_exact"])
-        for name in arms:
-            r = res[name]
-            extra_e, extra_t = (2, t_pred) if name == "mlp" else (0, 0.0)
-            arms[name].append((None if r["evals"] is None else r["evals"] + extra_e,
-                               None if r["seconds"] is None else r["seconds"] + extra_t))
-    summary = {}
-    for name, v in arms.items():
-        ev = [a for a, _ in v if a is not None]
-        sec = [b for _, b in v if b is not None]
-        summary[name] = {"mean_evals": float(np.mean(ev)) if ev else None,
-                         "median_evals": float(np.median(ev)) if ev else None,
-                         "mean_seconds": float(np.mean(sec)) if sec else None,
-                         "reached": len(ev), "points": len(v)}
-    line = {"metric": "time to 1 mHa vs plain (learned warm start)", "value": summary["mlp"]["mean_seconds"],
-            "unit": "s", "higher_is_better": False, "n_gpus": 1, "dtype": "f64 (VQE), bf16/f32 (network)",
-            "data": "synthetic",
-            "config": {"workload": "16 qubits, 8 electrons, 512-point scan r in [0.7,4.0], 360 UCCSD angles",
-                       "train_points": len(train), "held_out_points": len(held), "target": "E_exact + 1 mHa "
-                       "(or best converged + 1 mHa where UCCSD cannot reach it)"},
-            "arms": summary, "fallbacks_to_hf": fallbacks, "held_out_reaching_exact": reached_exact,
-            "training": {"vqe_seconds": t_data, "vqe_evals": int(np.sum(evals)), "fit_seconds": t_fit,
-                         "fit_steps": 3000, "final_loss": float(hist[-1]), "create_seconds": t_create}}
-    print(json.dumps(line), flush=True)
+    return int(b.group(1)) * per_launch_units / int(units.group(1))
 
 
 def main():
