@@ -352,6 +352,7 @@ def main():
 
     achieved = flops_per_launch / (ms_per_step / 1000.0) / 1e12
     traffic = profiled_traffic(n_inst)
+    probe = vq.probe_fp64()  # untimed: confirms the per-SM FP64 rate behind the peak
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": max(3, args.warmup), "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -362,7 +363,10 @@ def main():
                      "frac": achieved / FP64_PEAK_TFLOPS, "traffic": traffic,
                      "kernel": "k_resident<REAL> (one launch per step)",
                      "peak_source": "derived: 2 DFMA/clk/SM (probe) x 152 SMs x 2070 MHz x 2",
-                     "fp64_flops_per_launch": flops_per_launch},
+                     "fp64_flops_per_launch": flops_per_launch,
+                     "probe": {"dfma_per_clock_per_sm": probe["dfma_per_clock_per_sm"],
+                               "dependent_dfma_clocks": probe["dependent_dfma_clocks"],
+                               "sm_count": probe["sm_count"]}},
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(th_np.nbytes),
                 "d2h_bytes_per_step": int(e_np.nbytes + g_np.nbytes), "steps": K2},

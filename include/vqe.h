@@ -292,6 +292,17 @@ int vqe_energy_grad_noalloc(vqe_hamiltonian_t h, vqe_ansatz_t a, const double* t
 int vqe_work_estimate(vqe_hamiltonian_t h, vqe_ansatz_t a, int with_grad,
                       double* fp64_flops, double* state_bytes);
 
+/*
+ * Device probe (synchronous, allocates and frees a small buffer): the rate of
+ * independent FP64 FMAs over the whole device (per second and per clock per SM
+ * at the nominal SM clock), the clocks of one dependent FMA in a warp, the SM
+ * count and clock, the opt-in shared memory per block and the L2 size. The
+ * FP64 rate bounds the state-vector kernels (the paper has no counterpart).
+ * Any output pointer may be NULL.
+ */
+int vqe_probe_fp64(double* dfma_per_sec, double* dfma_per_clock_per_sm, double* dependent_dfma_clocks,
+                   int* sm_count, int* sm_clock_khz, size_t* smem_optin, int* l2_bytes);
+
 #ifdef __cplusplus
 }
 #endif

@@ -5,12 +5,12 @@ from ._native import build, load
 from .api import (Hamiltonian, Ansatz, Batch, VQEError, energy, energy_grad, state,
                   apply_hamiltonian, jordan_wigner, workspace_bytes, alloc_workspace,
                   work_estimate, set_flags, VQE_WS_ENERGY, VQE_WS_GRAD, VQE_WS_COMPLEX,
-                  VQE_FLAG_FORCE_COMPLEX, VQE_FLAG_FORCE_STREAMING)
+                  VQE_FLAG_FORCE_COMPLEX, VQE_FLAG_FORCE_STREAMING, probe_fp64, GraphEnergyGrad)
 from .autograd import VQEEnergy, vqe_energy
 
 __all__ = [
     "build", "load", "Hamiltonian", "Ansatz", "Batch", "VQEError", "energy", "energy_grad",
     "state", "apply_hamiltonian", "jordan_wigner", "workspace_bytes", "alloc_workspace",
     "work_estimate", "set_flags", "VQEEnergy", "vqe_energy", "VQE_WS_ENERGY", "VQE_WS_GRAD",
-    "VQE_WS_COMPLEX", "VQE_FLAG_FORCE_COMPLEX", "VQE_FLAG_FORCE_STREAMING",
+    "VQE_WS_COMPLEX", "VQE_FLAG_FORCE_COMPLEX", "VQE_FLAG_FORCE_STREAMING", "probe_fp64", "GraphEnergyGrad",
 ]

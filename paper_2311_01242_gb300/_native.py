@@ -17,7 +17,7 @@ _BUILD_DIR = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(_BUILD_DIR, "libvqe.so")
 HEADER = os.path.join(_ROOT, "include", "vqe.h")
 
-SOURCES = ["vqe_kernels.cu", "vqe_host.cpp", "vqe_static.cu", "vqe_mlp.cu"]
+SOURCES = ["vqe_kernels.cu", "vqe_host.cpp", "vqe_static.cu", "vqe_mlp.cu", "vqe_probe.cu"]
 DEPS = SOURCES + ["vqe_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ARCH + ["-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC"]
@@ -114,6 +114,8 @@ PROTOTYPES = {
     "vqe_destroy_batch": (None, [c_vp]),
     "vqe_work_estimate": (ctypes.c_int, [c_vp, c_vp, ctypes.c_int, P(c_dbl), P(c_dbl)]),
     "vqe_energy_grad_noalloc": (ctypes.c_int, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "vqe_probe_fp64": (ctypes.c_int, [P(c_dbl), P(c_dbl), P(c_dbl), P(ctypes.c_int), P(ctypes.c_int), P(c_sz),
+                                      P(ctypes.c_int)]),
     "vqe_mlp_param_count": (c_i64, [ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "vqe_mlp_workspace_bytes": (c_sz, [ctypes.c_int, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
     "vqe_mlp_to_bf16": (ctypes.c_int, [c_i64, c_vp, c_vp, c_vp]),

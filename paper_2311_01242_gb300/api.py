@@ -293,3 +293,15 @@ class GraphEnergyGrad:
             self.theta[:self.a.n_params].copy_(torch.as_tensor(theta, dtype=torch.float64))
         self.graph.replay()
         return self.e, self.g[:self.a.n_params]
+
+
+def probe_fp64():
+    """FP64 throughput/latency and device limits measured by vqe_probe_fp64."""
+    r = [ctypes.c_double(), ctypes.c_double(), ctypes.c_double()]
+    i = [ctypes.c_int(), ctypes.c_int()]
+    sm = ctypes.c_size_t()
+    l2 = ctypes.c_int()
+    _check(_lib().vqe_probe_fp64(ctypes.byref(r[0]), ctypes.byref(r[1]), ctypes.byref(r[2]), ctypes.byref(i[0]),
+                                 ctypes.byref(i[1]), ctypes.byref(sm), ctypes.byref(l2)))
+    return {"dfma_per_sec": r[0].value, "dfma_per_clock_per_sm": r[1].value, "dependent_dfma_clocks": r[2].value,
+            "sm_count": i[0].value, "sm_clock_khz": i[1].value, "smem_optin": sm.value, "l2_bytes": l2.value}
