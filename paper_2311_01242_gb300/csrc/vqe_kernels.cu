@@ -265,9 +265,16 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
   }
   for (int m = tid; m <= M; m += bs) poff[m] = int32_t(__ldg(d.pair_off + m));
   for (int p = tid; p < P; p += bs) pairs[p] = __ldg(d.pairs + p);
-  for (uint32_t k = tid; k < dim; k += bs) {
-    psi[k] = A::zero();
-    lam[k] = A::zero();
+  // real amplitudes: psi and lambda interleaved, pl[k] = {psi_k, lambda_k}, so
+  // the reverse sweep moves both with one 16-byte access
+  double2* pl = reinterpret_cast<double2*>(smem + L.psi);
+  if constexpr (REAL) {
+    for (uint32_t k = tid; k < dim; k += bs) pl[k] = make_double2(0.0, 0.0);
+  } else {
+    for (uint32_t k = tid; k < dim; k += bs) {
+      psi[k] = A::zero();
+      lam[k] = A::zero();
+    }
   }
   // pull the tables H psi reads later into L2 while the forward sweep runs
   {
@@ -281,7 +288,12 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
     for (int64_t o = int64_t(tid) * 128; o < int64_t(D) * 4; o += int64_t(bs) * 128) prefetch_l2(sec_b + o);
   }
   __syncthreads();
-  if (tid == 0) psi[d.hf] = A::unit();
+  if (tid == 0) {
+    if constexpr (REAL)
+      pl[d.hf].x = 1.0;
+    else
+      psi[d.hf] = A::unit();
+  }
   __syncthreads();
 
   // lane-interleaved position of this thread in the sweep: consecutive pairs go
@@ -315,22 +327,20 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
       const int s0 = gr.sign0 < 0;
       if constexpr (REAL) {
         // two lanes per pair: role 0 writes c a - s b to k, role 1 writes c b + s a
-        // to k2; both lanes read before either writes (warp-uniform trip count)
+        // to k2; both lanes read before either writes (warp-uniform trip count,
+        // lanes past the gate's end read index 0 and store nothing)
         for (int q0 = 0; q0 < cnt; q0 += pstride) {
           const int q = q0 + spos;
           const bool act = q < cnt;
-          uint32_t kd = 0;
-          double self = 0.0, other = 0.0, coef = 0.0;
-          if (act) {
-            const uint32_t k = (q0 == 0) ? kf : pairs[p0 + q];
-            const uint32_t k2 = k ^ gr.flip;
-            kd = role ? k2 : k;
-            self = psi[kd];
-            other = psi[role ? k : k2];
-            coef = sflip(c_s.y, parity32(k & gr.par) ^ s0 ^ role ^ 1);
-          }
+          const uint32_t kraw = (q0 == 0) ? kf : pairs[p0 + min(q, cnt - 1)];
+          const uint32_t k = act ? kraw : 0u;
+          const uint32_t k2 = k ^ (act ? gr.flip : 0u);
+          const uint32_t kd = role ? k2 : k;
+          const double self = pl[kd].x, other = pl[role ? k : k2].x;
+          const double coef = sflip(c_s.y, parity32(k & gr.par) ^ s0 ^ role ^ 1);
           __syncwarp();
-          if (act) psi[kd] = fma(coef, other, c_s.x * self);
+          const double out = fma(coef, other, c_s.x * self);
+          if (act) pl[kd].x = out;
         }
       } else {
         for (int q = spos; q < cnt; q += sw) {
@@ -382,11 +392,19 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
       const uint32_t gnext = (j + 1 < W) ? __ldg(d.ell + int64_t(j + 1) * D + r) : kEllPad;
       const GroupRec g = load_group(tg + gi);
       const uint32_t src = k ^ g.x;
-      A::mac(acc, group_coef<REAL>(g, te, tv, src), psi[src]);
+      if constexpr (REAL)
+        A::mac(acc, group_coef<REAL>(g, te, tv, src), pl[src].x);
+      else
+        A::mac(acc, group_coef<REAL>(g, te, tv, src), psi[src]);
       gi = gnext;
     }
-    lam[k] = acc;
-    e_part += A::redot(psi[k], acc);
+    if constexpr (REAL) {
+      pl[k].y = acc;
+      e_part += pl[k].x * acc;
+    } else {
+      lam[k] = acc;
+      e_part += A::redot(psi[k], acc);
+    }
   }
   const double e_tot = block_sum(e_part, red);
   if (tid == 0) energy[row] = e_tot;
@@ -420,26 +438,19 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
         for (int q0 = 0; q0 < cnt; q0 += pstride) {
           const int q = q0 + spos;
           const bool act = q < cnt;
-          uint32_t ks = 0;
-          int sr_bit = 0;
-          double ps = 0.0, po = 0.0, ls = 0.0, lo = 0.0;
-          if (act) {
-            const uint32_t k = (q0 == 0) ? kf : pairs[p0 + q];
-            const uint32_t k2 = k ^ gr.flip;
-            sr_bit = parity32(k & gr.par) ^ s0 ^ role;
-            ks = role ? k2 : k;
-            const uint32_t ko = role ? k : k2;
-            ps = psi[ks];
-            po = psi[ko];
-            ls = lam[ks];
-            lo = lam[ko];
-          }
+          const uint32_t kraw = (q0 == 0) ? kf : pairs[p0 + min(q, cnt - 1)];
+          const uint32_t k = act ? kraw : 0u;
+          const uint32_t k2 = k ^ (act ? gr.flip : 0u);
+          const int sr_bit = parity32(k & gr.par) ^ s0 ^ role;
+          const uint32_t ks = role ? k2 : k, ko = role ? k : k2;
+          const double2 sv = pl[ks], ov = pl[ko];
           __syncwarp();
+          const double sr = sflip(c_s.y, sr_bit);
+          const double g_term = sflip(ov.y * sv.x, sr_bit);
+          const double2 nv = make_double2(fma(sr, ov.x, c_s.x * sv.x), fma(sr, ov.y, c_s.x * sv.y));
           if (act) {
-            gbuf[2 * (p0 + q) + role] = sflip(lo * ps, sr_bit);
-            const double sr = sflip(c_s.y, sr_bit);
-            psi[ks] = fma(sr, po, c_s.x * ps);
-            lam[ks] = fma(sr, lo, c_s.x * ls);
+            gbuf[2 * (p0 + q) + role] = g_term;
+            pl[ks] = nv;
           }
         }
       } else {
