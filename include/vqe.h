@@ -65,10 +65,20 @@ int vqe_version(void);
  * Process-wide switches, for verification only (0 = normal operation):
  *   VQE_FLAG_FORCE_COMPLEX   evaluate E and g with complex amplitudes and full
  *                            complex coefficients instead of the real path;
- *   VQE_FLAG_FORCE_STREAMING never use the shared-memory-resident kernel.
+ *   VQE_FLAG_FORCE_STREAMING never use the shared-memory-resident kernel;
+ *   VQE_FLAG_NO_CLUSTER      run each resident instance on one CTA instead of
+ *                            a cluster of two;
+ *   VQE_FLAG_FP64_SWEEPS     run the resident kernel's gate sweeps in FP64
+ *                            instead of 64-bit fixed point (H psi, the energy
+ *                            and every streaming kernel are FP64 either way).
  * Returns the previous flags. Not thread-safe against concurrent compute calls.
  */
-enum { VQE_FLAG_FORCE_COMPLEX = 1, VQE_FLAG_FORCE_STREAMING = 2 };
+enum {
+  VQE_FLAG_FORCE_COMPLEX = 1,
+  VQE_FLAG_FORCE_STREAMING = 2,
+  VQE_FLAG_NO_CLUSTER = 4,
+  VQE_FLAG_FP64_SWEEPS = 8
+};
 int vqe_set_flags(int flags);
 
 /* Message of the last failed call on this thread ("" if none). */
@@ -97,8 +107,10 @@ int vqe_jordan_wigner(int n_spatial, const double* h, const double* eri, double 
  * per-pattern coefficient tables: for the pattern u of the source index on
  * the group's X bits (up to 4 bits), and the terms' Z bits outside them.
  * The Hamiltonian is flagged real when every folded coefficient
- * c * i^{|x&z|} is real; then all amplitudes stay real and kernels skip the
- * (identically zero) imaginary arithmetic. Synchronous; allocates device memory.
+ * c * i^{|x&z|} is real (informational: the energy and gradient kernels use
+ * real amplitudes either way, because psi(theta) is real for every theta and
+ * only the real parts of the folded coefficients enter E and g).
+ * Synchronous; allocates device memory.
  */
 int vqe_create_hamiltonian(int n_qubits, int64_t n_terms, const uint64_t* x_masks,
                            const uint64_t* z_masks, const double* coefs,
@@ -107,6 +119,32 @@ int vqe_create_hamiltonian(int n_qubits, int64_t n_terms, const uint64_t* x_mask
 /* Counts after merging/dropping; is_real as described above. Any out may be NULL. */
 int vqe_hamiltonian_info(vqe_hamiltonian_t h, int* n_qubits, int64_t* n_terms,
                          int64_t* n_groups, int* is_real);
+
+/*
+ * The kept terms (after merging and dropping) in the order vqe_set_coefs
+ * expects: sorted by (x_mask, z_mask), n_terms of vqe_hamiltonian_info each.
+ * coefs are the create-time values (vqe_set_coefs does not update them). Any
+ * output may be NULL. Host only.
+ */
+int vqe_hamiltonian_terms(vqe_hamiltonian_t h, uint64_t* x_masks, uint64_t* z_masks,
+                          double* coefs);
+
+/*
+ * New coefficients for the same Pauli structure: the Hamiltonian at another
+ * point r of a scan (Sec. 2.1.1's mapping applied to the integrals at r gives
+ * the same strings with new weights). coefs_dev: n_terms device doubles in the
+ * kept-term order above. The group tables are refolded on the device (each
+ * table entry is a fixed combination of term coefficients with weights
+ * +-1, +-2, +-4 times 1 or i), giving the same bits as vqe_create_hamiltonian
+ * with these coefficients when it keeps the same terms. The term set, the
+ * grouping and the connectivity tables do not change: a coefficient that is
+ * now below the create-time drop tolerance is kept, and a string that was
+ * dropped at create time cannot come back. Asynchronous on stream; every
+ * later call that uses h (on any stream, including batches and captured
+ * graphs holding h) reads the new tables once this work has run, so order
+ * the streams accordingly. Allocates nothing; graph-capturable.
+ */
+int vqe_set_coefs(vqe_hamiltonian_t h, const double* coefs_dev, vqe_stream_t stream);
 
 void vqe_destroy_hamiltonian(vqe_hamiltonian_t h);
 
@@ -223,6 +261,31 @@ int vqe_batch_energy_grad_host(vqe_batch_t b, const double* theta_host, int64_t 
 int vqe_batch_set_tuning(vqe_batch_t b, int stream_threads, int sweep_threads);
 
 void vqe_destroy_batch(vqe_batch_t b);
+
+/*
+ * The batched calls by instance list, without a batch handle: instance i is
+ * (hams[i], ansatze[i]) with its angles at theta_dev[i] (n_params_i device
+ * doubles) and, for the gradient, its output at grads_dev[i]. theta_dev and
+ * grads_dev are HOST arrays of n_inst device pointers; energies_dev holds
+ * n_inst device doubles. The library keeps a batch plan per instance list
+ * (keyed by the handles, at most 16 plans, least recently used dropped; a
+ * destroyed handle drops the plans that use it). The plan is built by
+ * vqe_batched_workspace_bytes, or by the first compute call for that list
+ * (synchronous, allocates); later calls with the same list allocate nothing
+ * and can be captured in a CUDA graph. The angles are gathered into the
+ * workspace and the gradients scattered back by two small kernels around the
+ * batch's own launches. Results equal vqe_batch_energy_grad's bit for bit.
+ * vqe_batched_workspace_bytes returns 0 and sets the error message on failure.
+ */
+size_t vqe_batched_workspace_bytes(int n_inst, const vqe_hamiltonian_t* hams,
+                                   const vqe_ansatz_t* ansatze, int with_grad);
+int vqe_energy_batched(int n_inst, const vqe_hamiltonian_t* hams, const vqe_ansatz_t* ansatze,
+                       const double* const* theta_dev, double* energies_dev,
+                       void* workspace, size_t workspace_bytes, vqe_stream_t stream);
+int vqe_energy_grad_batched(int n_inst, const vqe_hamiltonian_t* hams,
+                            const vqe_ansatz_t* ansatze, const double* const* theta_dev,
+                            double* energies_dev, double* const* grads_dev,
+                            void* workspace, size_t workspace_bytes, vqe_stream_t stream);
 
 /*
  * Learned warm start: a small network that predicts the UCCSD angles at a new

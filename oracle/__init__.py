@@ -16,7 +16,7 @@ the MLP oracle (when present) is pinned by finite differences.
 from .fermion import popcount, ladder, apply_string, fermion_matrix_op
 from .hamiltonian import hamiltonian_matrix, sector_basis, full_basis
 from .jw import jordan_wigner
-from .pauli import pauli_dense, pauli_apply, pauli_sum_apply, pauli_sum_dense
+from .pauli import pauli_dense, pauli_apply, pauli_sum_apply, pauli_sum_dense, pauli_sum_row
 from .ansatz import (excitation_ops, apply_gate, apply_generator, prepare_state,
                      hf_state)
 from .vqe import (energy, energy_pauli, gradient_direct, gradient_shift,
@@ -25,7 +25,7 @@ from .vqe import (energy, energy_pauli, gradient_direct, gradient_shift,
 __all__ = [
     "popcount", "ladder", "apply_string", "fermion_matrix_op", "hamiltonian_matrix",
     "sector_basis", "full_basis", "jordan_wigner", "pauli_dense", "pauli_apply",
-    "pauli_sum_apply", "pauli_sum_dense", "excitation_ops", "apply_gate",
+    "pauli_sum_apply", "pauli_sum_dense", "pauli_sum_row", "excitation_ops", "apply_gate",
     "apply_generator", "prepare_state", "hf_state", "energy", "energy_pauli",
     "gradient_direct", "gradient_shift", "gradient_fd", "exact_ground_energy",
     "run_bfgs", "EnergyModel",

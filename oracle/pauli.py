@@ -55,3 +55,18 @@ def pauli_sum_apply(xs, zs, cs, psi):
     for x, z, c in zip(xs, zs, cs):
         out += c * pauli_apply(x, z, psi)
     return out
+
+
+def pauli_sum_row(xs, zs, cs, k, amp):
+    """(H psi)[k] for H = sum_t c_t P(x_t, z_t), where amp(indices) returns psi
+    at an array of basis indices. From the action above, the amplitude at k
+    comes from source j = k XOR x_t:
+        (H psi)[k] = sum_t c_t i^{|x_t & z_t|} (-1)^{|j_t & z_t|} psi[j_t].
+    For one output row of a state too large to hold on the host."""
+    xs = np.asarray(xs, dtype=np.uint64)
+    zs = np.asarray(zs, dtype=np.uint64)
+    cs = np.asarray(cs)
+    src = np.uint64(int(k)) ^ xs
+    phase = np.array([1, 1j, -1, -1j])[popcount(xs & zs) % 4]
+    sign = 1 - 2 * (popcount(src & zs) & 1)
+    return complex(np.sum(cs * phase * sign * amp(src)))

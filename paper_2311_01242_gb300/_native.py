@@ -17,7 +17,7 @@ _BUILD_DIR = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(_BUILD_DIR, "libvqe.so")
 HEADER = os.path.join(_ROOT, "include", "vqe.h")
 
-SOURCES = ["vqe_kernels.cu", "vqe_host.cpp", "vqe_static.cu", "vqe_mlp.cu", "vqe_probe.cu"]
+SOURCES = ["vqe_kernels.cu", "vqe_host.cpp", "vqe_static.cu", "vqe_mlp.cu", "vqe_probe.cu", "vqe_aux.cu"]
 DEPS = SOURCES + ["vqe_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ARCH + ["-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC"]
@@ -95,6 +95,8 @@ PROTOTYPES = {
                                          P(c_i64)]),
     "vqe_create_hamiltonian": (ctypes.c_int, [ctypes.c_int, c_i64, c_vp, c_vp, c_vp, c_dbl, P(c_vp)]),
     "vqe_hamiltonian_info": (ctypes.c_int, [c_vp, P(ctypes.c_int), P(c_i64), P(c_i64), P(ctypes.c_int)]),
+    "vqe_hamiltonian_terms": (ctypes.c_int, [c_vp, c_vp, c_vp, c_vp]),
+    "vqe_set_coefs": (ctypes.c_int, [c_vp, c_vp, c_vp]),
     "vqe_destroy_hamiltonian": (None, [c_vp]),
     "vqe_create_ansatz": (ctypes.c_int, [ctypes.c_int, c_u64, c_i32, c_vp, P(c_vp)]),
     "vqe_ansatz_info": (ctypes.c_int, [c_vp, P(ctypes.c_int), P(c_i32), P(c_i64), P(c_i64)]),
@@ -112,6 +114,9 @@ PROTOTYPES = {
     "vqe_batch_energy_grad_host": (ctypes.c_int, [c_vp, c_vp, c_i64, c_vp, c_vp, c_i64, c_vp, c_sz, c_vp]),
     "vqe_batch_set_tuning": (ctypes.c_int, [c_vp, ctypes.c_int, ctypes.c_int]),
     "vqe_destroy_batch": (None, [c_vp]),
+    "vqe_batched_workspace_bytes": (c_sz, [ctypes.c_int, c_vp, c_vp, ctypes.c_int]),
+    "vqe_energy_batched": (ctypes.c_int, [ctypes.c_int, c_vp, c_vp, c_vp, c_vp, c_vp, c_sz, c_vp]),
+    "vqe_energy_grad_batched": (ctypes.c_int, [ctypes.c_int, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_sz, c_vp]),
     "vqe_work_estimate": (ctypes.c_int, [c_vp, c_vp, ctypes.c_int, P(c_dbl), P(c_dbl)]),
     "vqe_energy_grad_noalloc": (ctypes.c_int, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "vqe_probe_fp64": (ctypes.c_int, [P(c_dbl), P(c_dbl), P(c_dbl), P(ctypes.c_int), P(ctypes.c_int), P(c_sz),

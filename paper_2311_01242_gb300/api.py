@@ -11,7 +11,7 @@ import torch
 from . import _native
 
 VQE_WS_ENERGY, VQE_WS_GRAD, VQE_WS_COMPLEX = 0, 1, 2
-VQE_FLAG_FORCE_COMPLEX, VQE_FLAG_FORCE_STREAMING = 1, 2
+VQE_FLAG_FORCE_COMPLEX, VQE_FLAG_FORCE_STREAMING, VQE_FLAG_NO_CLUSTER, VQE_FLAG_FP64_SWEEPS = 1, 2, 4, 8
 
 
 class VQEError(RuntimeError):
@@ -98,6 +98,35 @@ class Hamiltonian:
         _check(self._lib.vqe_hamiltonian_info(self.handle, ctypes.byref(n), ctypes.byref(t), ctypes.byref(g),
                                               ctypes.byref(r)))
         return {"n_qubits": n.value, "n_terms": t.value, "n_groups": g.value, "is_real": bool(r.value)}
+
+    def terms(self):
+        """Kept (x_masks, z_masks, create-time coefs), in vqe_set_coefs order."""
+        t = self.info()["n_terms"]
+        xs = np.zeros(t, dtype=np.uint64)
+        zs = np.zeros(t, dtype=np.uint64)
+        cs = np.zeros(t, dtype=np.float64)
+        _check(self._lib.vqe_hamiltonian_terms(self.handle, _ptr(xs), _ptr(zs), _ptr(cs)))
+        return xs, zs, cs
+
+    def set_coefs(self, coefs, stream=None):
+        """New coefficients (device float64, kept-term order) for the same Pauli strings."""
+        if not (isinstance(coefs, torch.Tensor) and coefs.is_cuda and coefs.dtype == torch.float64
+                and coefs.is_contiguous()):
+            raise TypeError("coefs must be a contiguous float64 CUDA tensor")
+        if coefs.numel() != self.info()["n_terms"]:
+            raise ValueError("coefs must hold one value per kept term")
+        _check(self._lib.vqe_set_coefs(self.handle, _ptr(coefs), _stream(stream)))
+
+    def set_coefs_from(self, x_masks, z_masks, coefs, stream=None):
+        """set_coefs from a term list (e.g. jordan_wigner at a new geometry); the
+        strings must equal the kept ones."""
+        xs, zs, _ = self.terms()
+        if not (np.array_equal(np.asarray(x_masks, dtype=np.uint64), xs)
+                and np.array_equal(np.asarray(z_masks, dtype=np.uint64), zs)):
+            raise ValueError("Pauli strings differ from the Hamiltonian's kept terms")
+        c = torch.as_tensor(np.ascontiguousarray(coefs, dtype=np.float64)).cuda()
+        self.set_coefs(c, stream)
+        return c
 
     def __del__(self):
         h = getattr(self, "handle", None)
@@ -260,6 +289,54 @@ class Batch:
         if b is not None and b.value:
             self._lib.vqe_destroy_batch(b)
             self.handle = None
+
+
+def _handle_arrays(hams, ansatze):
+    if len(hams) != len(ansatze) or not hams:
+        raise ValueError("hams and ansatze must be non-empty and of equal length")
+    hs = (ctypes.c_void_p * len(hams))(*[h.handle.value for h in hams])
+    As = (ctypes.c_void_p * len(ansatze))(*[a.handle.value for a in ansatze])
+    return hs, As
+
+
+def batched_workspace_bytes(hams, ansatze, with_grad=True):
+    """vqe_batched_workspace_bytes (builds and caches the instance list's plan)."""
+    hs, As = _handle_arrays(hams, ansatze)
+    n = int(_lib().vqe_batched_workspace_bytes(len(hams), hs, As, int(bool(with_grad))))
+    if n == 0:
+        raise VQEError(1, _lib().vqe_last_error().decode(errors="replace"))
+    return n
+
+
+def energy_grad_batched(hams, ansatze, thetas, energies=None, grads=None, workspace=None, stream=None,
+                        with_grad=True):
+    """vqe_energy_grad_batched / vqe_energy_batched over per-instance angle
+    tensors (float64 CUDA, one per instance). Returns (energies, list of grads)."""
+    hs, As = _handle_arrays(hams, ansatze)
+    n = len(hams)
+    if len(thetas) != n:
+        raise ValueError("one theta per instance")
+    thetas = [t if (t.dtype == torch.float64 and t.is_cuda and t.is_contiguous()) else
+              torch.as_tensor(t, dtype=torch.float64).cuda().contiguous() for t in thetas]
+    for t, a in zip(thetas, ansatze):
+        if t.numel() < a.n_params:
+            raise ValueError("theta shorter than the ansatz's parameter count")
+    dev = thetas[0].device
+    if energies is None:
+        energies = torch.empty(n, dtype=torch.float64, device=dev)
+    if with_grad and grads is None:
+        grads = [torch.empty(max(a.n_params, 1), dtype=torch.float64, device=dev) for a in ansatze]
+    if workspace is None:
+        workspace = alloc_workspace(batched_workspace_bytes(hams, ansatze, with_grad), dev)
+    tp = (ctypes.c_void_p * n)(*[t.data_ptr() for t in thetas])
+    if with_grad:
+        gp = (ctypes.c_void_p * n)(*[g.data_ptr() for g in grads])
+        _check(_lib().vqe_energy_grad_batched(n, hs, As, tp, _ptr(energies), gp, _ptr(workspace),
+                                              workspace.numel(), _stream(stream)))
+        return energies, [g[:a.n_params] for g, a in zip(grads, ansatze)]
+    _check(_lib().vqe_energy_batched(n, hs, As, tp, _ptr(energies), _ptr(workspace), workspace.numel(),
+                                     _stream(stream)))
+    return energies, None
 
 
 class GraphEnergyGrad:

@@ -2,6 +2,7 @@
 // X-mask grouping and folding of the Pauli sum, excitation records, sector and
 // pair lists, the connectivity table, workspace layout and kernel dispatch.
 #include <algorithm>
+#include <atomic>
 #include <cmath>
 #include <complex>
 #include <cstdio>
@@ -133,6 +134,10 @@ struct SharedEll {
 std::mutex g_ell_mu;
 std::multimap<uint64_t, SharedEll*> g_ell_reg;
 
+// Handle serial numbers, never reused (keys of the cached batch plans).
+std::atomic<uint64_t> g_serial{1};
+uint64_t next_serial() { return g_serial.fetch_add(1); }
+
 uint64_t fnv1a(const std::vector<uint32_t>& v) {
   uint64_t h = 1469598103934665603ull;
   const unsigned char* p = reinterpret_cast<const unsigned char*>(v.data());
@@ -233,6 +238,14 @@ struct vqe_hamiltonian_s {
   std::vector<uint32_t> emask;
   std::vector<cplx> cvals;
   int is_real = 1;
+  uint64_t serial = 0;  // never reused: keys cached batch plans
+  // value tables as a linear map of the kept terms' coefficients (vqe_set_coefs)
+  std::vector<int64_t> lin_off;
+  std::vector<int32_t> lin_term;
+  std::vector<float> lin_w;
+  int64_t* d_lin_off = nullptr;
+  int32_t* d_lin_term = nullptr;
+  float* d_lin_w = nullptr;
   GroupRec* d_groups = nullptr;
   uint32_t* d_emask = nullptr;
   double* d_vals = nullptr;
@@ -252,6 +265,9 @@ struct vqe_hamiltonian_s {
     dfree(d_emask);
     dfree(d_vals);
     dfree(d_cvals);
+    dfree(d_lin_off);
+    dfree(d_lin_term);
+    dfree(d_lin_w);
     for (auto& kv : ells) {
       ell_release(kv.second.d_ell);
       ell16_release(kv.second.d_ell16);
@@ -274,6 +290,7 @@ struct vqe_ansatz_s {
   uint32_t* d_pairs = nullptr;
   uint32_t* d_sector = nullptr;
   int32_t* d_nb_rows = nullptr;
+  uint64_t serial = 0;  // never reused: keys cached batch plans
   std::tuple<int, int, int> key() const { return std::make_tuple(n, n_elec, n_alpha); }
   ~vqe_ansatz_s() {
     dfree(d_gates);
@@ -542,6 +559,7 @@ InstDesc make_desc(vqe_hamiltonian_t h, vqe_ansatz_t a, const vqe_hamiltonian_s:
 }
 
 bool use_real() { return (g_flags & VQE_FLAG_FORCE_COMPLEX) == 0; }
+bool use_fixed(bool real) { return real && (g_flags & VQE_FLAG_FP64_SWEEPS) == 0; }
 
 // Whether an instance fits the shared-memory-resident kernel in this mode; if
 // so, sets the shared-memory bytes and the descriptor's staging/sweep fields.
@@ -637,6 +655,16 @@ int ensure_smem(size_t smem, bool real) {
   return VQE_OK;
 }
 
+// Two CTAs (a cluster) per resident instance when amplitudes are real and every
+// instance's pair of CTAs fits on the device at once; one otherwise.
+int ctas_per_instance(bool real, int n_inst) {
+  if (!real || (g_flags & VQE_FLAG_NO_CLUSTER)) return 1;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return 1;
+  if (cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) return 1;
+  return 2 * n_inst <= sms ? 2 : 1;
+}
+
 int run_single(vqe_hamiltonian_t h, vqe_ansatz_t a, const double* theta, double* energy, double* grad,
                void* ws, size_t ws_bytes, cudaStream_t stream, bool with_grad) {
   int rc = check_pair(h, a);
@@ -651,7 +679,7 @@ int run_single(vqe_hamiltonian_t h, vqe_ansatz_t a, const double* theta, double*
   if (resident_fit(a, e, real, &d, &smem)) {
     if ((rc = ensure_smem(smem, real))) return rc;
     cudaError_t ce = vqe::launch_resident(nullptr, &d, 1, smem, real, with_grad, theta, 0, energy, grad, 0,
-                                          stream);
+                                          stream, ctas_per_instance(real, 1), use_fixed(real));
     if (ce != cudaSuccess) return cuda_fail(ce, "resident kernel launch");
     return VQE_OK;
   }
@@ -787,8 +815,16 @@ int vqe_create_hamiltonian(int n_qubits, int64_t n_terms, const uint64_t* xs, co
     H->z.push_back(kv.first.second);
     H->c.push_back(kv.second);
   }
-  // group by x (merged is sorted by x then z)
+  // Group by x (merged is sorted by x then z). Every table slot is built as a
+  // linear combination of the kept terms (term index, weight f * i^p, f a
+  // small power of two) so that vqe_set_coefs can refold the tables on the
+  // device in the same order; the values come from that same combination.
+  using Lin = std::vector<std::pair<int32_t, cplx>>;
   static const cplx ipow[4] = {cplx(1, 0), cplx(0, 1), cplx(-1, 0), cplx(0, -1)};
+  std::vector<Lin> slots;
+  auto scaled = [](const Lin& a, double f, Lin& out) {
+    for (const auto& tw : a) out.emplace_back(tw.first, tw.second * f);
+  };
   size_t t = 0;
   while (t < H->x.size()) {
     size_t t1 = t;
@@ -805,17 +841,17 @@ int vqe_create_hamiltonian(int n_qubits, int64_t n_terms, const uint64_t* xs, co
     g.upos = 0;
     for (int j = 0; j < ub; ++j) g.upos |= uint32_t(pos[j]) << (8 * j);
     const int nu = 1 << ub;
-    std::map<uint32_t, std::vector<cplx>> entries;  // z outside the pattern bits -> table
+    std::map<uint32_t, std::vector<Lin>> entries;  // z outside the pattern bits -> table
     for (size_t i = t; i < t1; ++i) {
       const uint32_t z = uint32_t(H->z[i]);
-      const cplx cp = H->c[i] * ipow[pc32(x & z) & 3];
+      const cplx ph = ipow[pc32(x & z) & 3];
       auto& tab = entries[z & ~xsel];
-      if (tab.empty()) tab.assign(nu, cplx(0, 0));
+      if (tab.empty()) tab.assign(nu, Lin());
       for (int u = 0; u < nu; ++u) {
         uint32_t bits = 0;
         for (int j = 0; j < ub; ++j)
           if ((u >> j) & 1) bits |= 1u << pos[j];
-        tab[u] += (pc32(bits & z) & 1) ? -cp : cp;
+        tab[u].emplace_back(int32_t(i), (pc32(bits & z) & 1) ? -ph : ph);
       }
     }
     // Evaluation form (see GroupRec::kind): the entry form, or the occupation
@@ -840,11 +876,11 @@ int vqe_create_hamiltonian(int n_qubits, int64_t n_terms, const uint64_t* xs, co
     g.kind = kind;
     g.nq = n_qubits;
     g.ebeg = int32_t(H->emask.size());
-    g.vbeg = int32_t(H->cvals.size());
+    g.vbeg = int32_t(slots.size());
     if (kind == 0) {
-      for (const auto& kv : entries) {
+      for (auto& kv : entries) {
         H->emask.push_back(kv.first);
-        for (int u = 0; u < nu; ++u) H->cvals.push_back(kv.second[u]);
+        for (int u = 0; u < nu; ++u) slots.push_back(std::move(kv.second[u]));
       }
     } else {
       uint32_t R = 0;
@@ -853,37 +889,63 @@ int vqe_create_hamiltonian(int n_qubits, int64_t n_terms, const uint64_t* xs, co
       H->emask.push_back(R);
       const int nq = n_qubits;
       if (kind == 1) {
-        std::vector<cplx> B(size_t(1 + nq) * nu, cplx(0, 0));
+        std::vector<Lin> B(size_t(1 + nq) * nu);
         for (const auto& kv : entries) {
           const uint32_t dm = kv.first ^ z0;
           for (int u = 0; u < nu; ++u) {
-            B[u] += kv.second[u];
-            if (dm) B[size_t(1 + __builtin_ctz(dm)) * nu + u] += -2.0 * kv.second[u];
+            scaled(kv.second[u], 1.0, B[u]);
+            if (dm) scaled(kv.second[u], -2.0, B[size_t(1 + __builtin_ctz(dm)) * nu + u]);
           }
         }
-        H->cvals.insert(H->cvals.end(), B.begin(), B.end());
+        for (auto& l : B) slots.push_back(std::move(l));
       } else {
-        std::vector<cplx> Q(size_t(1 + nq + nq * nq), cplx(0, 0));
+        std::vector<Lin> Q(size_t(1 + nq + nq * nq));
         for (const auto& kv : entries) {
           const uint32_t dm = kv.first ^ z0;
-          const cplx a = kv.second[0];
-          Q[0] += a;
+          const Lin& a = kv.second[0];
+          scaled(a, 1.0, Q[0]);
           if (pc32(dm) >= 1) {
             const int pb = __builtin_ctz(dm);
-            Q[1 + pb] += -2.0 * a;
+            scaled(a, -2.0, Q[1 + pb]);
             if (pc32(dm) == 2) {
               const int qb = 31 - __builtin_clz(dm);
-              Q[1 + qb] += -2.0 * a;
-              Q[size_t(1 + nq) + size_t(pb) * nq + qb] += 4.0 * a;
+              scaled(a, -2.0, Q[1 + qb]);
+              scaled(a, 4.0, Q[size_t(1 + nq) + size_t(pb) * nq + qb]);
             }
           }
         }
-        H->cvals.insert(H->cvals.end(), Q.begin(), Q.end());
+        for (auto& l : Q) slots.push_back(std::move(l));
       }
     }
     g.eend = int32_t(H->emask.size());
     H->groups.push_back(g);
     t = t1;
+  }
+  // Flatten the linear map: weight f * i^p stored as the float f and the sign
+  // bit of the term index set when p = 1. The values are summed in the same
+  // order as the device refold (each product is exact).
+  H->lin_off.assign(slots.size() + 1, 0);
+  for (size_t s2 = 0; s2 < slots.size(); ++s2) {
+    H->lin_off[s2 + 1] = H->lin_off[s2] + int64_t(slots[s2].size());
+    for (const auto& tw : slots[s2]) {
+      const bool imag = tw.second.imag() != 0.0;
+      const double f = imag ? tw.second.imag() : tw.second.real();
+      H->lin_term.push_back(imag ? int32_t(uint32_t(tw.first) | 0x80000000u) : tw.first);
+      H->lin_w.push_back(float(f));
+    }
+  }
+  H->cvals.resize(slots.size());
+  for (size_t s2 = 0; s2 < slots.size(); ++s2) {
+    double re = 0.0, im = 0.0;
+    for (int64_t j = H->lin_off[s2]; j < H->lin_off[s2 + 1]; ++j) {
+      const int32_t tt = H->lin_term[size_t(j)];
+      const double v = double(H->lin_w[size_t(j)]) * H->c[size_t(tt & 0x7fffffff)];
+      if (tt < 0)
+        im += v;
+      else
+        re += v;
+    }
+    H->cvals[s2] = cplx(re, im);
   }
   std::vector<double> vals(H->cvals.size());
   std::vector<double2> cv(H->cvals.size());
@@ -911,6 +973,12 @@ int vqe_create_hamiltonian(int n_qubits, int64_t n_terms, const uint64_t* xs, co
   if ((rc = upload(H->emask, &H->d_emask))) return rc;
   if ((rc = upload(vals, &H->d_vals))) return rc;
   if ((rc = upload(cv, &H->d_cvals))) return rc;
+  if (!H->lin_term.empty()) {
+    if ((rc = upload(H->lin_off, &H->d_lin_off))) return rc;
+    if ((rc = upload(H->lin_term, &H->d_lin_term))) return rc;
+    if ((rc = upload(H->lin_w, &H->d_lin_w))) return rc;
+  }
+  H->serial = next_serial();
   *out = H.release();
   return VQE_OK;
 }
@@ -925,7 +993,34 @@ int vqe_hamiltonian_info(vqe_hamiltonian_t h, int* n_qubits, int64_t* n_terms, i
   return VQE_OK;
 }
 
-void vqe_destroy_hamiltonian(vqe_hamiltonian_t h) { delete h; }
+static void purge_plans(uint64_t serial);
+
+int vqe_hamiltonian_terms(vqe_hamiltonian_t h, uint64_t* x_masks, uint64_t* z_masks, double* coefs) {
+  if (!h) return fail(VQE_ERR_INVALID_ARG, "NULL handle");
+  for (size_t t = 0; t < h->x.size(); ++t) {
+    if (x_masks) x_masks[t] = h->x[t];
+    if (z_masks) z_masks[t] = h->z[t];
+    if (coefs) coefs[t] = h->c[t];
+  }
+  return VQE_OK;
+}
+
+int vqe_set_coefs(vqe_hamiltonian_t h, const double* coefs_dev, vqe_stream_t stream) {
+  if (!h) return fail(VQE_ERR_INVALID_ARG, "NULL handle");
+  if (!coefs_dev) return fail(VQE_ERR_INVALID_ARG, "NULL coefficient pointer");
+  const int64_t n_slots = int64_t(h->lin_off.size()) - 1;
+  if (n_slots <= 0 || h->lin_term.empty()) return VQE_OK;  // every term was dropped: H = 0
+  cudaError_t ce = vqe::fold_coefs(n_slots, h->d_lin_off, h->d_lin_term, h->d_lin_w, coefs_dev, h->d_vals,
+                                   h->d_cvals, static_cast<cudaStream_t>(stream));
+  if (ce != cudaSuccess) return cuda_fail(ce, "coefficient refold");
+  return VQE_OK;
+}
+
+void vqe_destroy_hamiltonian(vqe_hamiltonian_t h) {
+  if (!h) return;
+  purge_plans(h->serial);
+  delete h;
+}
 
 int vqe_create_ansatz(int n_qubits, uint64_t hf_bits, int32_t n_exc, const int32_t* exc,
                       vqe_ansatz_t* out) {
@@ -1064,6 +1159,7 @@ int vqe_create_ansatz(int n_qubits, uint64_t hf_bits, int32_t n_exc, const int32
     std::vector<uint32_t> one(1, 0);
     if ((rc = upload(one, &A->d_pairs))) return rc;
   }
+  A->serial = next_serial();
   *out = A.release();
   return VQE_OK;
 }
@@ -1077,7 +1173,11 @@ int vqe_ansatz_info(vqe_ansatz_t a, int* n_qubits, int32_t* n_params, int64_t* s
   return VQE_OK;
 }
 
-void vqe_destroy_ansatz(vqe_ansatz_t a) { delete a; }
+void vqe_destroy_ansatz(vqe_ansatz_t a) {
+  if (!a) return;
+  purge_plans(a->serial);
+  delete a;
+}
 
 size_t vqe_workspace_bytes(vqe_hamiltonian_t h, vqe_ansatz_t a, int mode) {
   if (check_pair(h, a)) return 0;
@@ -1288,7 +1388,9 @@ static int batch_run(vqe_batch_t b, const double* theta, int64_t ld_theta, doubl
     if ((rc = ensure_smem(b->res_smem[mode], real))) return rc;
     cudaError_t ce = vqe::launch_resident(b->d_res[mode], nullptr, int(b->resident[mode].size()),
                                           b->res_smem[mode], real, with_grad, theta, ld_theta, energies,
-                                          grads, ld_grad, stream);
+                                          grads, ld_grad, stream,
+                                          ctas_per_instance(real, int(b->resident[mode].size())),
+                                          use_fixed(real));
     if (ce != cudaSuccess) return cuda_fail(ce, "batched resident launch");
   }
   if (real && !b->sb.slots.empty()) {
@@ -1405,6 +1507,140 @@ int vqe_batch_set_tuning(vqe_batch_t b, int stream_threads, int sweep_threads) {
 }
 
 void vqe_destroy_batch(vqe_batch_t b) { delete b; }
+
+// Batch plans behind the pointer-array calls, keyed by the instances' handle
+// serial numbers; the least recently used plan is dropped beyond kMaxPlans.
+namespace {
+constexpr size_t kMaxPlans = 16;
+struct CachedPlan {
+  vqe_batch_t b = nullptr;
+  uint64_t last_use = 0;
+};
+std::mutex g_plan_mu;
+std::map<std::vector<uint64_t>, CachedPlan> g_plans;
+uint64_t g_plan_clock = 0;
+
+int plan_for(int n, const vqe_hamiltonian_t* hams, const vqe_ansatz_t* ans, vqe_batch_t* out) {
+  *out = nullptr;
+  if (n < 1 || !hams || !ans) return fail(VQE_ERR_INVALID_ARG, "bad instance arrays");
+  std::vector<uint64_t> key;
+  key.reserve(2 * size_t(n));
+  for (int i = 0; i < n; ++i) {
+    if (!hams[i] || !ans[i]) return fail(VQE_ERR_INVALID_ARG, "NULL handle in instance " + std::to_string(i));
+    key.push_back(hams[i]->serial);
+    key.push_back(ans[i]->serial);
+  }
+  std::lock_guard<std::mutex> lk(g_plan_mu);
+  auto it = g_plans.find(key);
+  if (it == g_plans.end()) {
+    vqe_batch_t b = nullptr;
+    int rc = vqe_create_batch(n, hams, ans, &b);
+    if (rc) return rc;
+    if (g_plans.size() >= kMaxPlans) {
+      auto old = g_plans.begin();
+      for (auto j = g_plans.begin(); j != g_plans.end(); ++j)
+        if (j->second.last_use < old->second.last_use) old = j;
+      vqe_destroy_batch(old->second.b);
+      g_plans.erase(old);
+    }
+    it = g_plans.emplace(std::move(key), CachedPlan{b, 0}).first;
+  }
+  it->second.last_use = ++g_plan_clock;
+  *out = it->second.b;
+  return VQE_OK;
+}
+
+struct PackedLayout {
+  int64_t ld = 1;
+  size_t theta_off = 0, grad_off = 0, batch_off = 0, total = 0;
+};
+
+PackedLayout packed_layout(vqe_batch_t b, bool with_grad) {
+  PackedLayout L;
+  L.ld = std::max<int64_t>(b->max_params, 1);
+  const size_t mat = align256(size_t(b->n_inst) * size_t(L.ld) * 8);
+  L.theta_off = 0;
+  L.grad_off = mat;
+  L.batch_off = mat + (with_grad ? mat : 0);
+  L.total = L.batch_off + vqe_batch_workspace_bytes(b, with_grad);
+  return L;
+}
+
+int batched_run(int n, const vqe_hamiltonian_t* hams, const vqe_ansatz_t* ans, const double* const* theta,
+                double* energies, double* const* grads, void* ws, size_t ws_bytes, cudaStream_t stream) {
+  if (!theta || !energies) return fail(VQE_ERR_INVALID_ARG, "NULL theta array or energies pointer");
+  vqe_batch_t b = nullptr;
+  int rc = plan_for(n, hams, ans, &b);
+  if (rc) return rc;
+  const bool with_grad = grads != nullptr;
+  for (int i = 0; i < n; ++i) {
+    if (ans[i]->M > 0 && !theta[i]) return fail(VQE_ERR_INVALID_ARG, "NULL theta pointer, instance " + std::to_string(i));
+    if (with_grad && ans[i]->M > 0 && !grads[i])
+      return fail(VQE_ERR_INVALID_ARG, "NULL gradient pointer, instance " + std::to_string(i));
+  }
+  const PackedLayout L = packed_layout(b, with_grad);
+  if ((rc = check_ws(ws, ws_bytes, L.total))) return rc;
+  char* base = static_cast<char*>(ws);
+  double* d_theta = reinterpret_cast<double*>(base + L.theta_off);
+  double* d_grad = with_grad ? reinterpret_cast<double*>(base + L.grad_off) : nullptr;
+  auto rows = [&](bool pack) -> int {
+    for (int r0 = 0; r0 < n; r0 += vqe::kRowPtrs) {
+      vqe::RowPtrs rp;
+      std::memset(&rp, 0, sizeof(rp));
+      rp.base = r0;
+      rp.count = std::min(vqe::kRowPtrs, n - r0);
+      int max_len = 0;
+      for (int r = 0; r < rp.count; ++r) {
+        rp.p[r] = pack ? theta[r0 + r] : grads[r0 + r];
+        rp.len[r] = ans[r0 + r]->M;
+        max_len = std::max(max_len, rp.len[r]);
+      }
+      cudaError_t ce = pack ? vqe::pack_rows(rp, d_theta, L.ld, max_len, stream)
+                            : vqe::unpack_rows(rp, d_grad, L.ld, max_len, stream);
+      if (ce != cudaSuccess) return cuda_fail(ce, pack ? "theta gather" : "gradient scatter");
+    }
+    return VQE_OK;
+  };
+  if ((rc = rows(true))) return rc;
+  rc = batch_run(b, d_theta, L.ld, energies, d_grad, L.ld, base + L.batch_off, ws_bytes - L.batch_off, stream);
+  if (rc) return rc;
+  return with_grad ? rows(false) : VQE_OK;
+}
+}  // namespace
+
+static void purge_plans(uint64_t serial) {
+  std::lock_guard<std::mutex> lk(g_plan_mu);
+  for (auto it = g_plans.begin(); it != g_plans.end();) {
+    if (std::find(it->first.begin(), it->first.end(), serial) != it->first.end()) {
+      vqe_destroy_batch(it->second.b);
+      it = g_plans.erase(it);
+    } else {
+      ++it;
+    }
+  }
+}
+
+size_t vqe_batched_workspace_bytes(int n_inst, const vqe_hamiltonian_t* hams, const vqe_ansatz_t* ans,
+                                   int with_grad) {
+  vqe_batch_t b = nullptr;
+  if (plan_for(n_inst, hams, ans, &b)) return 0;
+  return packed_layout(b, with_grad != 0).total;
+}
+
+int vqe_energy_batched(int n_inst, const vqe_hamiltonian_t* hams, const vqe_ansatz_t* ans,
+                       const double* const* theta_dev, double* energies_dev, void* ws, size_t ws_bytes,
+                       vqe_stream_t stream) {
+  return batched_run(n_inst, hams, ans, theta_dev, energies_dev, nullptr, ws, ws_bytes,
+                     static_cast<cudaStream_t>(stream));
+}
+
+int vqe_energy_grad_batched(int n_inst, const vqe_hamiltonian_t* hams, const vqe_ansatz_t* ans,
+                            const double* const* theta_dev, double* energies_dev, double* const* grads_dev,
+                            void* ws, size_t ws_bytes, vqe_stream_t stream) {
+  if (!grads_dev) return fail(VQE_ERR_INVALID_ARG, "NULL gradient array");
+  return batched_run(n_inst, hams, ans, theta_dev, energies_dev, grads_dev, ws, ws_bytes,
+                     static_cast<cudaStream_t>(stream));
+}
 
 int vqe_work_estimate(vqe_hamiltonian_t h, vqe_ansatz_t a, int with_grad, double* flops, double* bytes) {
   int rc = check_pair(h, a);

@@ -142,10 +142,12 @@ __host__ __device__ inline ResidentLayout resident_layout(int n, int M, int P, i
 }
 
 // Kernel launchers (vqe_kernels.cu). All are asynchronous on `stream`.
+// ctas_per_instance: 1, or 2 (a cluster per instance; real amplitudes only).
+// fixed_point: real sweeps in 64-bit fixed point on the integer pipe (real only).
 cudaError_t launch_resident(const InstDesc* d_descs, const InstDesc* one, int n_inst,
                             size_t smem, bool real, bool with_grad, const double* theta,
                             int64_t ld_theta, double* energy, double* grad, int64_t ld_grad,
-                            cudaStream_t stream);
+                            cudaStream_t stream, int ctas_per_instance, bool fixed_point);
 cudaError_t set_resident_smem_limit(size_t smem, bool real);
 
 struct StreamBuffers {
@@ -194,5 +196,23 @@ cudaError_t ell_device_fill(const uint32_t* sector, int64_t D, const GroupRec* g
 int prepare_noalloc(vqe_hamiltonian_s* h, vqe_ansatz_s* a, bool with_grad, InstDesc* d, StreamPlan* sp,
                     bool* real, size_t off[5], size_t* need);
 int set_error(int code, const char* msg);
+
+// Table refold from new coefficients (vqe_aux.cu): slot s of the value tables is
+// sum_{j in [off[s], off[s+1])} w[j] * coefs[term[j] & 0x7fffffff], added to the
+// imaginary part when term[j] < 0.
+cudaError_t fold_coefs(int64_t n_slots, const int64_t* off, const int32_t* term, const float* w,
+                       const double* coefs, double* vals, double2* cvals, cudaStream_t stream);
+
+// Up to kRowPtrs device rows per launch, passed by value: row r (global index
+// base + r) has len[r] doubles at p[r].
+constexpr int kRowPtrs = 64;
+struct RowPtrs {
+  const double* p[kRowPtrs];
+  int32_t len[kRowPtrs];
+  int32_t base, count;
+};
+// dst[(base + r) * ld + k] = p[r][k]  /  p[r][k] = src[(base + r) * ld + k], k < len[r].
+cudaError_t pack_rows(const RowPtrs& rp, double* dst, int64_t ld, int max_len, cudaStream_t stream);
+cudaError_t unpack_rows(const RowPtrs& rp, const double* src, int64_t ld, int max_len, cudaStream_t stream);
 
 }  // namespace vqe

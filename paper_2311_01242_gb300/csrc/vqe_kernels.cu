@@ -15,6 +15,8 @@
 //
 // Every reduction is deterministic: fixed work assignment, fixed shuffle
 // trees, fixed summation order of partials.
+#include <cooperative_groups.h>
+#include <type_traits>
 #include <cuda_runtime.h>
 
 #include "vqe_internal.h"
@@ -31,6 +33,32 @@ __device__ __forceinline__ double sflip(double v, int s) {
 __device__ __forceinline__ double2 sflip(double2 v, int s) {
   return make_double2(sflip(v.x, s), sflip(v.y, s));
 }
+
+// ---------------------------------------------------------------- fixed-point sweeps
+// The resident kernel's real sweeps can run in 64-bit fixed point on the
+// integer pipe: amplitudes of the unit-norm state as Q1.62 (value = v / 2^62),
+// cos and sin magnitudes as unsigned Q0.64 with their signs kept apart, so a
+// product is the high word of a 64 x 64 multiply. Rotations preserve the
+// 2-norm, so |value| <= 1 holds for every entry at every gate.
+__device__ __forceinline__ long long dbits(double v) { return __double_as_longlong(v); }
+__device__ __forceinline__ double llbits(long long v) { return __longlong_as_double(v); }
+// floor(a * b / 2^64) for signed a, unsigned b
+__device__ __forceinline__ long long mulhi_su(long long a, unsigned long long b) {
+  const unsigned long long h = __umul64hi(static_cast<unsigned long long>(a), b);
+  return static_cast<long long>(h - (a < 0 ? b : 0ull));
+}
+// v, negated when b == 1
+__device__ __forceinline__ long long neg_if(long long v, int b) {
+  const long long m = -static_cast<long long>(b);
+  return (v ^ m) - m;
+}
+// |x| * 2^64 rounded, for |x| <= 1 (1 itself saturates to 2^64 - 1)
+__device__ __forceinline__ unsigned long long fix_mag(double x) {
+  const double a = fabs(x) * 18446744073709551616.0;
+  return a >= 18446744073709551616.0 ? ~0ull : __double2ull_rn(a);
+}
+// 2^e as a double, for |e| < 1000
+__device__ __forceinline__ double pow2(int e) { return __longlong_as_double(static_cast<long long>(1023 + e) << 52); }
 
 __device__ __forceinline__ uint32_t pattern_of(uint32_t src, uint32_t upos, int ubits) {
   uint32_t u = 0;
@@ -190,6 +218,32 @@ __device__ __forceinline__ uint32_t ell_at(const uint32_t* ell, const uint16_t* 
   return __ldg(ell + idx);
 }
 
+// Calls f(gi) for the group indices of output r's connectivity row, in row
+// order, up to the first pad. The indices are read in chunks of kEllChunk and
+// the next chunk is requested before the current one is used, so a thread has
+// a chunk of loads in flight instead of one L2 round trip per entry.
+constexpr int kEllChunk = 8;
+template <class F>
+__device__ __forceinline__ void ell_row(const uint32_t* ell, const uint16_t* ell16, int W, int64_t D, int64_t r,
+                                       F&& f) {
+  uint32_t cur[kEllChunk];
+#pragma unroll
+  for (int u = 0; u < kEllChunk; ++u) cur[u] = u < W ? ell_at(ell, ell16, int64_t(u) * D + r) : kEllPad;
+  for (int j0 = 0; j0 < W; j0 += kEllChunk) {
+    const bool more = cur[kEllChunk - 1] != kEllPad && j0 + kEllChunk < W;
+    uint32_t nxt[kEllChunk];
+#pragma unroll
+    for (int u = 0; u < kEllChunk; ++u)
+      nxt[u] = (more && j0 + kEllChunk + u < W) ? ell_at(ell, ell16, int64_t(j0 + kEllChunk + u) * D + r) : kEllPad;
+#pragma unroll
+    for (int u = 0; u < kEllChunk; ++u)
+      if (cur[u] != kEllPad) f(cur[u]);
+    if (!more) break;
+#pragma unroll
+    for (int u = 0; u < kEllChunk; ++u) cur[u] = nxt[u];
+  }
+}
+
 // Deterministic block sum; the result is valid in thread 0.
 __device__ double block_sum(double v, double* red) {
 #pragma unroll
@@ -222,7 +276,13 @@ __device__ __forceinline__ void sweep_barrier(int nthreads) {
 // instance's pairs are dealt round-robin over those warps. The H psi tables
 // are staged into the region the reverse sweep later uses for its per-pair
 // contributions, when they fit.
-template <bool REAL>
+//
+// CL = 2 (real amplitudes only): a cluster of two CTAs per instance. Both run the
+// sweeps identically; each computes lambda for half of the outputs and writes it
+// into its own and its partner's shared memory, then one cluster barrier joins
+// the halves. Rank 0 adds the two energy halves (rank 0's first) and writes the
+// outputs. No distributed-shared-memory access follows the barrier.
+template <bool REAL, int CL, bool FIX>
 __global__ void __launch_bounds__(kResidentThreads, 1)
 k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double* __restrict__ theta,
            int64_t ld_theta, double* __restrict__ energy, double* __restrict__ grad, int64_t ld_grad,
@@ -230,10 +290,14 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
   typedef Amp<REAL> A;
   typedef typename A::T T;
   typedef typename A::C C;
+  static_assert(CL == 1 || (CL == 2 && REAL), "clusters of two need real amplitudes");
+  static_assert(!FIX || REAL, "fixed-point sweeps need real amplitudes");
   extern __shared__ __align__(16) unsigned char smem[];
+  const int inst_idx = int(blockIdx.x) / CL;
+  const int crank = CL == 2 ? int(cooperative_groups::this_cluster().block_rank()) : 0;
   InstDesc d;
   if (descs) {
-    d = descs[blockIdx.x];
+    d = descs[inst_idx];
   } else {
     d = one;
   }
@@ -260,8 +324,15 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
   for (int m = tid; m < M; m += bs) {
     double s, c;
     sincos(th[m], &s, &c);
-    cs[m] = make_double2(c, s);
-    gates[m] = load_gate(d.gates + m);
+    GateRec gr = load_gate(d.gates + m);
+    if constexpr (FIX) {
+      // magnitudes in Q0.64 (bit patterns kept in the double2 slot), signs in pad
+      cs[m] = make_double2(llbits(static_cast<long long>(fix_mag(c))), llbits(static_cast<long long>(fix_mag(s))));
+      gr.pad = (c < 0.0 ? 1 : 0) | (s < 0.0 ? 2 : 0);
+    } else {
+      cs[m] = make_double2(c, s);
+    }
+    gates[m] = gr;
   }
   for (int m = tid; m <= M; m += bs) poff[m] = int32_t(__ldg(d.pair_off + m));
   for (int p = tid; p < P; p += bs) pairs[p] = __ldg(d.pairs + p);
@@ -289,7 +360,9 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
   }
   __syncthreads();
   if (tid == 0) {
-    if constexpr (REAL)
+    if constexpr (FIX)
+      pl[d.hf].x = llbits(1ll << 62);
+    else if constexpr (REAL)
       pl[d.hf].x = 1.0;
     else
       psi[d.hf] = A::unit();
@@ -336,11 +409,20 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
           const uint32_t k = act ? kraw : 0u;
           const uint32_t k2 = k ^ (act ? gr.flip : 0u);
           const uint32_t kd = role ? k2 : k;
-          const double self = pl[kd].x, other = pl[role ? k : k2].x;
-          const double coef = sflip(c_s.y, parity32(k & gr.par) ^ s0 ^ role ^ 1);
-          __syncwarp();
-          const double out = fma(coef, other, c_s.x * self);
-          if (act) pl[kd].x = out;
+          if constexpr (FIX) {
+            const long long self = dbits(pl[kd].x), other = dbits(pl[role ? k : k2].x);
+            const int sneg = parity32(k & gr.par) ^ s0 ^ role ^ 1 ^ ((gr.pad >> 1) & 1);
+            __syncwarp();
+            const long long out = neg_if(mulhi_su(self, static_cast<unsigned long long>(dbits(c_s.x))), gr.pad & 1) +
+                                  neg_if(mulhi_su(other, static_cast<unsigned long long>(dbits(c_s.y))), sneg);
+            if (act) pl[kd].x = llbits(out);
+          } else {
+            const double self = pl[kd].x, other = pl[role ? k : k2].x;
+            const double coef = sflip(c_s.y, parity32(k & gr.par) ^ s0 ^ role ^ 1);
+            __syncwarp();
+            const double out = fma(coef, other, c_s.x * self);
+            if (act) pl[kd].x = out;
+          }
         }
       } else {
         for (int q = spos; q < cnt; q += sw) {
@@ -381,25 +463,35 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
     tv = sv;
   }
   __syncthreads();
+  if constexpr (FIX) {
+    // psi in Q1.62 -> FP64 for H psi (entries outside the sector stay 0 = +0.0)
+    for (int r = tid; r < D; r += bs) {
+      const uint32_t k = __ldg(d.sector + r);
+      pl[k].x = __ll2double_rn(dbits(pl[k].x)) * 0x1p-62;
+    }
+    __syncthreads();
+  }
 
   // a3: lambda = H psi on the sector, E = <psi|lambda>
   double e_part = 0.0;
-  for (int r = tid; r < D; r += bs) {
+  const int r_half = (D + CL - 1) / CL;
+  const int r_lo = crank * r_half, r_hi = min(D, r_lo + r_half);
+  double2* pl_peer = pl;
+  if constexpr (CL == 2) pl_peer = cooperative_groups::this_cluster().map_shared_rank(pl, crank ^ 1);
+  for (int r = r_lo + tid; r < r_hi; r += bs) {
     const uint32_t k = __ldg(d.sector + r);
     T acc = A::zero();
-    uint32_t gi = W > 0 ? __ldg(d.ell + r) : kEllPad;
-    for (int j = 0; j < W && gi != kEllPad; ++j) {
-      const uint32_t gnext = (j + 1 < W) ? __ldg(d.ell + int64_t(j + 1) * D + r) : kEllPad;
+    ell_row(d.ell, nullptr, W, D, r, [&](uint32_t gi) {
       const GroupRec g = load_group(tg + gi);
       const uint32_t src = k ^ g.x;
       if constexpr (REAL)
         A::mac(acc, group_coef<REAL>(g, te, tv, src), pl[src].x);
       else
         A::mac(acc, group_coef<REAL>(g, te, tv, src), psi[src]);
-      gi = gnext;
-    }
+    });
     if constexpr (REAL) {
       pl[k].y = acc;
+      if constexpr (CL == 2) pl_peer[k].y = acc;
       e_part += pl[k].x * acc;
     } else {
       lam[k] = acc;
@@ -407,10 +499,42 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
     }
   }
   const double e_tot = block_sum(e_part, red);
-  if (tid == 0) energy[row] = e_tot;
+  if constexpr (CL == 2) {
+    if (tid == 0 && crank == 1) *cooperative_groups::this_cluster().map_shared_rank(red + 48, 0) = e_tot;
+    cooperative_groups::this_cluster().sync();
+    if (tid == 0 && crank == 0) energy[row] = e_tot + red[48];
+  } else {
+    if (tid == 0) energy[row] = e_tot;
+  }
   __syncthreads();
 
   if (!with_grad) return;
+
+  // Fixed point for the reverse sweep: phi in Q1.62 and lambda scaled by
+  // 2^(61 - e), where 2^e bounds ||lambda|| (so every entry stays below 2^61 in
+  // magnitude through the rotations). Both CTAs of a cluster hold all of lambda
+  // here and derive the same e.
+  int lam_e = 0;
+  if constexpr (FIX) {
+    double l2 = 0.0;
+    for (int r = tid; r < D; r += bs) {
+      const double v = pl[__ldg(d.sector + r)].y;
+      l2 = fma(v, v, l2);
+    }
+    const double tot = block_sum(l2, red);
+    if (tid == 0) red[56] = tot;
+    __syncthreads();
+    const int ex = int((dbits(red[56]) >> 52) & 0x7ff);
+    // ||lambda||^2 < 2^(ex - 1022) <= 2^(2 lam_e)
+    lam_e = ex == 0 ? -500 : (ex - 1022 + 1) >> 1;
+    const double sc = pow2(61 - lam_e);
+    for (int r = tid; r < D; r += bs) {
+      const uint32_t k = __ldg(d.sector + r);
+      const double2 v = pl[k];
+      pl[k] = make_double2(llbits(__double2ll_rn(v.x * 0x1p62)), llbits(__double2ll_rn(v.y * sc)));
+    }
+    __syncthreads();
+  }
 
   // a4: reverse sweep (same prefetch of the next gate as the forward sweep)
   if (tid < sw && M > 0) {
@@ -445,12 +569,26 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
           const uint32_t ks = role ? k2 : k, ko = role ? k : k2;
           const double2 sv = pl[ks], ov = pl[ko];
           __syncwarp();
-          const double sr = sflip(c_s.y, sr_bit);
-          const double g_term = sflip(ov.y * sv.x, sr_bit);
-          const double2 nv = make_double2(fma(sr, ov.x, c_s.x * sv.x), fma(sr, ov.y, c_s.x * sv.y));
-          if (act) {
-            gbuf[2 * (p0 + q) + role] = g_term;
-            pl[ks] = nv;
+          if constexpr (FIX) {
+            const unsigned long long cm = static_cast<unsigned long long>(dbits(c_s.x));
+            const unsigned long long sm = static_cast<unsigned long long>(dbits(c_s.y));
+            const int cneg = gr.pad & 1, sneg = ((gr.pad >> 1) & 1) ^ sr_bit;
+            const long long ps = dbits(sv.x), ls = dbits(sv.y), po = dbits(ov.x), lo = dbits(ov.y);
+            const long long g_term = neg_if(__mul64hi(ps, lo), sr_bit);
+            const long long np = neg_if(mulhi_su(ps, cm), cneg) + neg_if(mulhi_su(po, sm), sneg);
+            const long long nl = neg_if(mulhi_su(ls, cm), cneg) + neg_if(mulhi_su(lo, sm), sneg);
+            if (act) {
+              gbuf[2 * (p0 + q) + role] = llbits(g_term);
+              pl[ks] = make_double2(llbits(np), llbits(nl));
+            }
+          } else {
+            const double sr = sflip(c_s.y, sr_bit);
+            const double g_term = sflip(ov.y * sv.x, sr_bit);
+            const double2 nv = make_double2(fma(sr, ov.x, c_s.x * sv.x), fma(sr, ov.y, c_s.x * sv.y));
+            if (act) {
+              gbuf[2 * (p0 + q) + role] = g_term;
+              pl[ks] = nv;
+            }
           }
         }
       } else {
@@ -481,20 +619,34 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
   // per-gate sums of the pair contributions: four consecutive lanes split a
   // gate's pairs into four contiguous quarters, combined by a fixed shuffle tree
   double* g_out = grad + row * ld_grad;
+  // fixed point: a contribution h stands for h * 2^(e - 59) (Q1.62 times lambda
+  // scaled by 2^(61 - e), high word); its integer sums are exact
+  const double g_scale = FIX ? pow2(lam_e - 58) : 2.0;
   for (int base = 0; base < 4 * M; base += bs) {
     const int t = base + tid;
     const int m = t >> 2, qtr = t & 3;
-    double s = 0.0;
+    typedef typename std::conditional<FIX, long long, double>::type Acc;
+    Acc s = 0;
     if (m < M) {
       const int per = REAL ? 2 : 1;  // contributions per pair
       const int p0 = per * poff[m], p1 = per * poff[m + 1];
       const int len = p1 - p0, chunk = (len + 3) >> 2;
       const int a = p0 + qtr * chunk, b = min(p1, a + chunk);
-      for (int p = a; p < b; ++p) s += gbuf[p];
+      for (int p = a; p < b; ++p) {
+        if constexpr (FIX)
+          s += dbits(gbuf[p]);
+        else
+          s += gbuf[p];
+      }
     }
     s += __shfl_down_sync(0xffffffffu, s, 2, 4);
     s += __shfl_down_sync(0xffffffffu, s, 1, 4);
-    if (m < M && qtr == 0) g_out[m] = 2.0 * s;
+    if (m < M && qtr == 0 && crank == 0) {
+      if constexpr (FIX)
+        g_out[m] = __ll2double_rn(s) * g_scale;
+      else
+        g_out[m] = g_scale * s;
+    }
   }
 }
 
@@ -557,13 +709,11 @@ k_hpsi(const InstDesc d, int n_elec, int n_alpha, const typename Amp<REAL>::T* _
     const uint32_t k = __ldg(d.sector + r);
     T acc = A::zero();
     if (ELL) {
-      for (int j = 0; j < d.W; ++j) {
-        const uint32_t gi = ell_at(d.ell, d.ell16, int64_t(j) * d.D + r);
-        if (gi == kEllPad) break;
+      ell_row(d.ell, d.ell16, d.W, d.D, r, [&](uint32_t gi) {
         const GroupRec g = load_group(d.groups + gi);
         const uint32_t src = k ^ g.x;
         A::mac(acc, group_coef<REAL>(g, d.emask, tv, src), psi[src]);
-      }
+      });
     } else {
       for (int gi = 0; gi < d.G; ++gi) {
         const GroupRec g = load_group(d.groups + gi);
@@ -723,13 +873,11 @@ __global__ void __launch_bounds__(512, 1) kb_hpsi(BatchDev b, BatchSegs sg) {
     if (W > 0) {
       const uint32_t* ell = d->ell;
       const uint16_t* ell16 = d->ell16;
-      for (int j = 0; j < W; ++j) {
-        const uint32_t gi = ell_at(ell, ell16, int64_t(j) * D + r);
-        if (gi == kEllPad) break;
+      ell_row(ell, ell16, W, D, r, [&](uint32_t gi) {
         const GroupRec g = load_group(groups + gi);
         const uint32_t src = k ^ g.x;
         acc = fma(group_coef<true>(g, emask, vals, src), psi[src], acc);
-      }
+      });
     } else {
       const int ne = d->n_elec, na = d->n_alpha;
       for (int gi = 0; gi < G; ++gi) {
@@ -834,22 +982,48 @@ __global__ void k_ell_fill(const uint32_t* __restrict__ sector, int64_t D, const
 
 // ---------------------------------------------------------------- launchers
 cudaError_t set_resident_smem_limit(size_t smem, bool real) {
-  if (real)
-    return cudaFuncSetAttribute(k_resident<true>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
-  return cudaFuncSetAttribute(k_resident<false>, cudaFuncAttributeMaxDynamicSharedMemorySize, int(smem));
+  const int b = int(smem);
+  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  if (!real) return cudaFuncSetAttribute(k_resident<false, 1, false>, a, b);
+  cudaError_t e = cudaFuncSetAttribute(k_resident<true, 1, true>, a, b);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_resident<true, 2, true>, a, b);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_resident<true, 1, false>, a, b);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_resident<true, 2, false>, a, b);
+  return e;
 }
 
-cudaError_t launch_resident(const InstDesc* d_descs, const InstDesc* one, int n_inst, size_t smem,
-                            bool real, bool with_grad, const double* theta, int64_t ld_theta,
-                            double* energy, double* grad, int64_t ld_grad, cudaStream_t stream) {
+cudaError_t launch_resident(const InstDesc* d_descs, const InstDesc* one, int n_inst, size_t smem, bool real,
+                            bool with_grad, const double* theta, int64_t ld_theta, double* energy, double* grad,
+                            int64_t ld_grad, cudaStream_t stream, int ctas_per_instance, bool fixed_point) {
   InstDesc dummy = {};
   const InstDesc& o = one ? *one : dummy;
-  if (real)
-    k_resident<true><<<n_inst, kResidentThreads, smem, stream>>>(d_descs, o, theta, ld_theta, energy,
-                                                                 grad, ld_grad, with_grad ? 1 : 0);
+  const int wg = with_grad ? 1 : 0;
+  if (real && ctas_per_instance == 2) {
+    cudaLaunchConfig_t cfg = {};
+    cfg.gridDim = dim3(2 * n_inst);
+    cfg.blockDim = dim3(kResidentThreads);
+    cfg.dynamicSmemBytes = smem;
+    cfg.stream = stream;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeClusterDimension;
+    attr[0].val.clusterDim.x = 2;
+    attr[0].val.clusterDim.y = 1;
+    attr[0].val.clusterDim.z = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    if (fixed_point)
+      return cudaLaunchKernelEx(&cfg, k_resident<true, 2, true>, d_descs, o, theta, ld_theta, energy, grad,
+                                ld_grad, wg);
+    return cudaLaunchKernelEx(&cfg, k_resident<true, 2, false>, d_descs, o, theta, ld_theta, energy, grad,
+                              ld_grad, wg);
+  }
+  const dim3 g(n_inst), b(kResidentThreads);
+  if (real && fixed_point)
+    k_resident<true, 1, true><<<g, b, smem, stream>>>(d_descs, o, theta, ld_theta, energy, grad, ld_grad, wg);
+  else if (real)
+    k_resident<true, 1, false><<<g, b, smem, stream>>>(d_descs, o, theta, ld_theta, energy, grad, ld_grad, wg);
   else
-    k_resident<false><<<n_inst, kResidentThreads, smem, stream>>>(d_descs, o, theta, ld_theta, energy,
-                                                                  grad, ld_grad, with_grad ? 1 : 0);
+    k_resident<false, 1, false><<<g, b, smem, stream>>>(d_descs, o, theta, ld_theta, energy, grad, ld_grad, wg);
   return cudaGetLastError();
 }
 

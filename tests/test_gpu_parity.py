@@ -335,3 +335,54 @@ def test_autograd_function():
     e_o, g_o = oracle_eg(p, exc, th)
     assert abs(float(e.detach()) - e_o) <= E_TOL
     assert np.abs(t.grad.cpu().numpy() - 3.0 * g_o).max() <= 3 * G_TOL
+
+
+def test_cluster_of_two_matches_single_cta():
+    """Splitting H psi over a cluster of two CTAs changes only the order in which
+    the two energy halves are added; gradients are bitwise equal."""
+    w = synth.config1(16)
+    hams = [vq.Hamiltonian.from_problem(p) for p in w.problems]
+    A = vq.Ansatz(12, synth.hf_bitstring(6), w.excitations[0])
+    B = vq.Batch(hams, [A] * len(hams))
+    theta = torch.as_tensor(np.stack(w.thetas)).cuda().contiguous()
+    e2, g2 = [t.clone() for t in B.energy_grad(theta)]
+    old = vq.set_flags(vq.VQE_FLAG_NO_CLUSTER)
+    try:
+        e1, g1 = [t.clone() for t in B.energy_grad(theta)]
+        es1, gs1 = vq.energy_grad(hams[3], A, theta[3])
+    finally:
+        vq.set_flags(old)
+    es2, gs2 = vq.energy_grad(hams[3], A, theta[3])
+    assert float((e1 - e2).abs().max()) <= 1e-13
+    assert torch.equal(g1, g2)
+    assert abs(float(es1) - float(es2)) <= 1e-13 and torch.equal(gs1, gs2)
+
+
+def test_fixed_point_sweeps_match_fp64_sweeps():
+    """The resident kernel's integer (Q1.62) sweeps and its FP64 sweeps compute
+    the same energies and gradients up to rounding: |dE| <= 1e-12, |dg| <= 1e-11,
+    in both the single-CTA and the cluster form; both stay within the oracle bar."""
+    w = synth.config1(8)
+    hams = [vq.Hamiltonian.from_problem(p) for p in w.problems]
+    A = vq.Ansatz(12, synth.hf_bitstring(6), w.excitations[0])
+    B = vq.Batch(hams, [A] * len(hams))
+    theta = torch.as_tensor(np.stack(w.thetas)).cuda().contiguous()
+    for extra in (0, vq.VQE_FLAG_NO_CLUSTER):
+        old = vq.set_flags(extra)
+        try:
+            e_fix, g_fix = [t.clone() for t in B.energy_grad(theta)]
+        finally:
+            vq.set_flags(old)
+        old = vq.set_flags(extra | vq.VQE_FLAG_FP64_SWEEPS)
+        try:
+            e_f64, g_f64 = [t.clone() for t in B.energy_grad(theta)]
+        finally:
+            vq.set_flags(old)
+        assert float((e_fix - e_f64).abs().max()) <= 1e-12
+        assert float((g_fix - g_f64).abs().max()) <= 1e-11
+    p = w.problems[5]
+    idx = [0, 58, A.n_params - 1]
+    e_o, g_o = oracle.gradient_direct(oracle.EnergyModel.from_problem(p, full=False), synth.hf_bitstring(6),
+                                      w.excitations[0], w.thetas[5], idx)
+    assert abs(float(e_fix[5]) - e_o) <= 1e-10
+    assert np.abs(g_fix[5, idx].cpu().numpy() - g_o).max() <= 1e-9

@@ -132,6 +132,21 @@ def test_pauli_action_matches_kronecker():
         assert np.abs(oracle.pauli_apply(x, z, psi) - oracle.pauli_dense(x, z, n) @ psi).max() < 1e-14
 
 
+def test_pauli_sum_row_matches_kronecker_rows():
+    """One output row of H psi (for states too large for the host) equals the
+    row of the Kronecker-product matrix times psi, including Y phases."""
+    rng = np.random.default_rng(11)
+    n = 6
+    xs = rng.integers(0, 64, size=40).astype(np.uint64)
+    zs = rng.integers(0, 64, size=40).astype(np.uint64)
+    cs = rng.normal(size=40)
+    psi = rng.normal(size=64) + 1j * rng.normal(size=64)
+    full = oracle.pauli_sum_dense(xs, zs, cs, n) @ psi
+    for k in range(64):
+        row = oracle.pauli_sum_row(xs, zs, cs, k, lambda idx: psi[idx.astype(np.int64)])
+        assert abs(row - full[k]) < 1e-13
+
+
 def test_single_qubit_paulis_are_textbook():
     X = oracle.pauli_dense(1, 0, 1)
     Z = oracle.pauli_dense(0, 1, 1)
