@@ -284,6 +284,12 @@ struct vqe_ansatz_s {
   std::vector<int64_t> pair_off;
   std::vector<uint32_t> pairs;
   std::vector<uint32_t> sector;
+  int lo_bits = 0;                    // rank(k) = rank_hi[k >> lo_bits] + rank_lo[k & (2^lo_bits - 1)]
+  std::vector<uint32_t> rank_hi, rank_lo;
+  std::vector<uint2> rpairs;          // (rank(k) | sign << 31, rank(k ^ flip)) per pair
+  uint32_t* d_rank_hi = nullptr;
+  uint32_t* d_rank_lo = nullptr;
+  uint2* d_rpairs = nullptr;
   std::vector<int32_t> nb_rows;
   GateRec* d_gates = nullptr;
   int64_t* d_pair_off = nullptr;
@@ -297,6 +303,9 @@ struct vqe_ansatz_s {
     dfree(d_pair_off);
     dfree(d_pairs);
     dfree(d_sector);
+    dfree(d_rank_hi);
+    dfree(d_rank_lo);
+    dfree(d_rpairs);
     dfree(d_nb_rows);
   }
 };
@@ -537,6 +546,10 @@ InstDesc make_desc(vqe_hamiltonian_t h, vqe_ansatz_t a, const vqe_hamiltonian_s:
   d.hf = uint32_t(a->hf);
   d.D = int64_t(a->sector.size());
   d.sector = a->d_sector;
+  d.rpairs = a->d_rpairs;
+  d.rank_hi = a->d_rank_hi;
+  d.rank_lo = a->d_rank_lo;
+  d.lo_bits = a->lo_bits;
   d.gates = a->d_gates;
   d.pair_off = a->d_pair_off;
   d.pairs = a->d_pairs;
@@ -591,7 +604,7 @@ struct WsLayout {
 WsLayout ws_layout(vqe_ansatz_t a, bool complex_amp, bool with_grad) {
   WsLayout L;
   const size_t amp = complex_amp ? 16 : 8;
-  const size_t vec = align256((size_t(1) << a->n) * amp);
+  const size_t vec = align256(std::max<size_t>(a->sector.size(), 1) * amp);  // compressed to the sector
   L.psi = 0;
   L.lam = vec;
   L.cs = 2 * vec;
@@ -1145,6 +1158,58 @@ int vqe_create_ansatz(int n_qubits, uint64_t hf_bits, int32_t n_exc, const int32
   A->pairs.resize(size_t(A->pair_off[n_exc]));
   for (int m = 0; m < n_exc; ++m)
     std::copy(per[m].begin(), per[m].end(), A->pairs.begin() + A->pair_off[m]);
+  // Rank tables of the sorted sector. A state k splits into a high part h =
+  // k >> L and a low part v = k & (2^L - 1); sorted order compares h first, so
+  // rank(k) = #{sector states with a smaller high part} + #{low parts below v
+  // with the same electron counts as v}. The counts are (alpha, beta) for a
+  // spin sector (even / odd qubits) and N otherwise.
+  {
+    const int L = (n + 1) / 2, Hb = n - L;
+    A->lo_bits = L;
+    const bool spin = A->n_alpha >= 0;
+    const uint32_t lo_mask = uint32_t((uint64_t(1) << L) - 1);
+    auto binom = [](int a, int b) -> uint64_t {
+      if (b < 0 || b > a) return 0;
+      uint64_t r = 1;
+      for (int i = 1; i <= b; ++i) r = r * uint64_t(a - b + i) / uint64_t(i);
+      return r;
+    };
+    const int lo_even = (L + 1) / 2, lo_odd = L / 2;
+    A->rank_lo.assign(size_t(1) << L, 0u);
+    std::vector<uint32_t> counter(33 * 33, 0u);
+    for (uint32_t v = 0; v <= lo_mask; ++v) {
+      const int key = spin ? pc32(v & even) * 33 + pc32(v & odd) : pc32(v);
+      A->rank_lo[v] = counter[size_t(key)]++;
+      if (v == lo_mask) break;
+    }
+    A->rank_hi.assign(size_t(1) << Hb, 0u);
+    uint64_t acc = 0;
+    const int n_beta = A->n_elec - A->n_alpha;
+    for (uint64_t h = 0; h < (uint64_t(1) << Hb); ++h) {
+      A->rank_hi[size_t(h)] = uint32_t(acc);
+      const uint32_t hk = uint32_t(h << L);
+      if (spin)
+        acc += binom(lo_even, A->n_alpha - pc32(hk & even)) * binom(lo_odd, n_beta - pc32(hk & odd));
+      else
+        acc += binom(L, A->n_elec - pc32(hk));
+    }
+    if (acc != uint64_t(A->sector.size()) || A->sector.size() >= (size_t(1) << 31))
+      return fail(VQE_ERR_UNSUPPORTED, "sector rank tables do not cover the sector");
+    auto rank = [&](uint32_t k) { return A->rank_hi[k >> L] + A->rank_lo[k & lo_mask]; };
+    for (size_t r = 0; r < A->sector.size(); ++r)
+      if (rank(A->sector[r]) != uint32_t(r)) return fail(VQE_ERR_UNSUPPORTED, "sector rank mismatch");
+    A->rpairs.resize(A->pairs.size());
+    parallel_for(n_exc, [&](int64_t lo, int64_t hi) {
+      for (int64_t m = lo; m < hi; ++m) {
+        const GateRec& g = A->gates[size_t(m)];
+        for (int64_t p = A->pair_off[m]; p < A->pair_off[m + 1]; ++p) {
+          const uint32_t k = A->pairs[size_t(p)];
+          const uint32_t sb = uint32_t((pc32(k & g.par) & 1) ^ (g.sign0 < 0 ? 1 : 0));
+          A->rpairs[size_t(p)] = make_uint2(rank(k) | (sb << 31), rank(k ^ g.flip));
+        }
+      }
+    });
+  }
   A->nb_rows.resize(size_t(n_exc) + 1);
   for (int m = 0; m < n_exc; ++m) A->nb_rows[m] = vqe::stream_grid(A->pair_off[m + 1] - A->pair_off[m]);
   A->nb_rows[n_exc] = vqe::stream_grid(int64_t(A->sector.size()));
@@ -1153,11 +1218,16 @@ int vqe_create_ansatz(int n_qubits, uint64_t hf_bits, int32_t n_exc, const int32
   if ((rc = upload(A->pair_off, &A->d_pair_off))) return rc;
   if ((rc = upload(A->pairs, &A->d_pairs))) return rc;
   if ((rc = upload(A->sector, &A->d_sector))) return rc;
+  if ((rc = upload(A->rank_hi, &A->d_rank_hi))) return rc;
+  if ((rc = upload(A->rank_lo, &A->d_rank_lo))) return rc;
+  if (!A->rpairs.empty() && (rc = upload(A->rpairs, &A->d_rpairs))) return rc;
   if ((rc = upload(A->nb_rows, &A->d_nb_rows))) return rc;
   if (A->pairs.empty()) {
-    // keep a valid (never read) pair pointer for kernels
+    // keep valid (never read) pair pointers for kernels
     std::vector<uint32_t> one(1, 0);
     if ((rc = upload(one, &A->d_pairs))) return rc;
+    std::vector<uint2> one2(1, make_uint2(0, 0));
+    if ((rc = upload(one2, &A->d_rpairs))) return rc;
   }
   A->serial = next_serial();
   *out = A.release();
@@ -1241,7 +1311,7 @@ static int build_stream_batch(vqe_batch_s* B) {
   int64_t eb = 0, gb = 0;
   for (int s = 0; s < n; ++s) {
     vqe_ansatz_t a = B->ans[sb.slots[s]];
-    const size_t vec = align256((size_t(1) << a->n) * 8);
+    const size_t vec = align256(std::max<size_t>(a->sector.size(), 1) * 8);
     sb.psi_off.push_back(int64_t(off));
     sb.lam_off.push_back(int64_t(off + vec));
     off += 2 * vec;

@@ -57,6 +57,12 @@ struct InstDesc {
   const GateRec* gates;      // [M]
   const int64_t* pair_off;   // [M+1]
   const uint32_t* pairs;     // [pair_off[M]] lower index k of each pair
+  const uint2* rpairs;       // [pair_off[M]] (rank(k) | sign << 31, rank(k ^ flip)); sign: (-1)-bit of T|k>
+  // rank(k) = rank_hi[k >> lo_bits] + rank_lo[k & (2^lo_bits - 1)] is the position
+  // of sector state k in sector[]; the streaming kernels store amplitudes there
+  const uint32_t* rank_hi;
+  const uint32_t* rank_lo;
+  int32_t lo_bits, pad1;
   // Hamiltonian
   int32_t G, W;              // groups, connectivity slots per output
   const GroupRec* groups;    // [G]

@@ -204,9 +204,63 @@ __device__ __forceinline__ typename Amp<REAL>::C group_coef(const GroupRec& g, c
   return sflip(f, parity32(src & z0));
 }
 
+// group_coef split at its first table term: v0 = vals[vbeg + u] and z = emask[ebeg]
+// (the first entry's value and mask in the entry form, B[u] or Q[0] and z0 in the
+// occupation forms) are loaded by the caller ahead of time; this adds the rest in
+// the same order as group_coef, so the result is bitwise the same.
+template <bool REAL>
+__device__ __forceinline__ typename Amp<REAL>::C group_coef_rest(const GroupRec& g, const uint32_t* emask,
+                                                                 const typename Amp<REAL>::C* vals, uint32_t src,
+                                                                 typename Amp<REAL>::C v0, uint32_t z) {
+  typedef typename Amp<REAL>::C C;
+  if (g.kind == 0) {
+    const uint32_t u = pattern_of(src, g.upos, g.ubits);
+    const C* vp = vals + g.vbeg + u;
+    C f = sflip(v0, parity32(src & z));
+    for (int e = g.ebeg + 1, j = 1; e < g.eend; ++e, ++j)
+      cadd(f, sflip(vp[j << g.ubits], parity32(src & emask[e])));
+    return f;
+  }
+  uint32_t m = src & emask[g.ebeg + 1];
+  C f = v0;
+  if (g.kind == 1) {
+    const uint32_t u = pattern_of(src, g.upos, g.ubits);
+    const C* vp = vals + g.vbeg + u;
+    while (m) {
+      const int r = __ffs(m) - 1;
+      m &= m - 1;
+      cadd(f, vp[(1 + r) << g.ubits]);
+    }
+  } else {
+    const C* q = vals + g.vbeg;
+    const int nq = g.nq;
+    while (m) {
+      const int pb = __ffs(m) - 1;
+      m &= m - 1;
+      cadd(f, q[1 + pb]);
+      const C* row = q + 1 + nq + pb * nq;
+      uint32_t m2 = m;
+      while (m2) {
+        const int qb = __ffs(m2) - 1;
+        m2 &= m2 - 1;
+        cadd(f, row[qb]);
+      }
+    }
+  }
+  return sflip(f, parity32(src & z));
+}
+
+
 __device__ __forceinline__ bool in_sector(uint32_t k, int n_elec, int n_alpha) {
   if (__popc(k) != n_elec) return false;
   return n_alpha < 0 || __popc(k & 0x55555555u) == n_alpha;
+}
+
+// Position of basis state k in the sector's sorted list (k must be in the
+// sector): the count of sector states with a smaller high part, plus the rank
+// of the low part among low parts with the same electron counts.
+__device__ __forceinline__ uint32_t sector_rank(const InstDesc& d, uint32_t k) {
+  return __ldg(d.rank_hi + (k >> d.lo_bits)) + __ldg(d.rank_lo + (k & ((1u << d.lo_bits) - 1u)));
 }
 
 // Entry j of output r's connectivity row (kEllPad past the row's end).
@@ -218,30 +272,96 @@ __device__ __forceinline__ uint32_t ell_at(const uint32_t* ell, const uint16_t* 
   return __ldg(ell + idx);
 }
 
-// Calls f(gi) for the group indices of output r's connectivity row, in row
-// order, up to the first pad. The indices are read in chunks of kEllChunk and
-// the next chunk is requested before the current one is used, so a thread has
-// a chunk of loads in flight instead of one L2 round trip per entry.
+// Calls f(gi) for the group indices of output r's connectivity row at slots
+// j = first, first + step, ... in order, up to the first pad. The indices are
+// read in chunks of kEllChunk and the next chunk is requested before the
+// current one is used, so a thread has a chunk of loads in flight instead of
+// one L2 round trip per entry.
 constexpr int kEllChunk = 8;
 template <class F>
 __device__ __forceinline__ void ell_row(const uint32_t* ell, const uint16_t* ell16, int W, int64_t D, int64_t r,
-                                       F&& f) {
-  uint32_t cur[kEllChunk];
+                                       int first, int step, F&& f) {
+  constexpr int U = kEllChunk;
+  uint32_t cur[U];
 #pragma unroll
-  for (int u = 0; u < kEllChunk; ++u) cur[u] = u < W ? ell_at(ell, ell16, int64_t(u) * D + r) : kEllPad;
-  for (int j0 = 0; j0 < W; j0 += kEllChunk) {
-    const bool more = cur[kEllChunk - 1] != kEllPad && j0 + kEllChunk < W;
-    uint32_t nxt[kEllChunk];
+  for (int u = 0; u < U; ++u) {
+    const int j = first + u * step;
+    cur[u] = j < W ? ell_at(ell, ell16, int64_t(j) * D + r) : kEllPad;
+  }
+  for (int j0 = first; j0 < W; j0 += U * step) {
+    const bool more = cur[U - 1] != kEllPad && j0 + U * step < W;
+    uint32_t nxt[U];
 #pragma unroll
-    for (int u = 0; u < kEllChunk; ++u)
-      nxt[u] = (more && j0 + kEllChunk + u < W) ? ell_at(ell, ell16, int64_t(j0 + kEllChunk + u) * D + r) : kEllPad;
+    for (int u = 0; u < U; ++u) {
+      const int j = j0 + (U + u) * step;
+      nxt[u] = (more && j < W) ? ell_at(ell, ell16, int64_t(j) * D + r) : kEllPad;
+    }
 #pragma unroll
-    for (int u = 0; u < kEllChunk; ++u)
+    for (int u = 0; u < U; ++u)
       if (cur[u] != kEllPad) f(cur[u]);
     if (!more) break;
 #pragma unroll
-    for (int u = 0; u < kEllChunk; ++u) cur[u] = nxt[u];
+    for (int u = 0; u < U; ++u) cur[u] = nxt[u];
   }
+}
+
+// One output row of H psi over the compressed state (entry r of psi is sector
+// state r): sum over the row's connectivity entries j of f_{g_j}(src) psi[rank(src)],
+// src = k ^ x_{g_j}, in row order. Entries are taken in chunks of U: first every
+// entry's group record, source rank, psi value and first table term are loaded
+// (independent loads, all in flight together), then the chunk is combined in
+// order; only groups with more than one table term go back to memory there.
+template <bool REAL, int U>
+__device__ __forceinline__ typename Amp<REAL>::T hpsi_row(const uint32_t* ell, const uint16_t* ell16, int W, int64_t D,
+                                                          int64_t r, uint32_t k, const GroupRec* groups,
+                                                          const uint32_t* emask, const typename Amp<REAL>::C* vals,
+                                                          const typename Amp<REAL>::T* psi, const uint32_t* rank_hi,
+                                                          const uint32_t* rank_lo, int lo_bits) {
+  typedef Amp<REAL> A;
+  typedef typename A::T T;
+  typedef typename A::C C;
+  const uint32_t lo_mask = (1u << lo_bits) - 1u;
+  T acc = A::zero();
+  uint32_t cur[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) cur[u] = u < W ? ell_at(ell, ell16, int64_t(u) * D + r) : kEllPad;
+  for (int j0 = 0; j0 < W; j0 += U) {
+    const bool more = cur[U - 1] != kEllPad && j0 + U < W;
+    uint32_t nxt[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      nxt[u] = (more && j0 + U + u < W) ? ell_at(ell, ell16, int64_t(j0 + U + u) * D + r) : kEllPad;
+    uint32_t src[U], z[U], extra = 0;
+    T pv[U];
+    C v0[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const bool live = cur[u] != kEllPad;
+      const GroupRec g = load_group(groups + (live ? cur[u] : 0u));
+      src[u] = k ^ g.x;
+      // a pad slot reads row r itself (a valid index) and is dropped below
+      const uint32_t rs = live ? __ldg(rank_hi + (src[u] >> lo_bits)) + __ldg(rank_lo + (src[u] & lo_mask))
+                               : uint32_t(r);
+      pv[u] = psi[rs];
+      v0[u] = vals[g.vbeg + int(pattern_of(src[u], g.upos, g.ubits))];
+      z[u] = emask[g.ebeg];
+      if (g.kind != 0 || g.eend > g.ebeg + 1) extra |= 1u << u;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      if (cur[u] == kEllPad) continue;
+      C f;
+      if ((extra >> u) & 1u)
+        f = group_coef_rest<REAL>(load_group(groups + cur[u]), emask, vals, src[u], v0[u], z[u]);
+      else
+        f = sflip(v0[u], parity32(src[u] & z[u]));
+      A::mac(acc, f, pv[u]);
+    }
+    if (!more) break;
+#pragma unroll
+    for (int u = 0; u < U; ++u) cur[u] = nxt[u];
+  }
+  return acc;
 }
 
 // Deterministic block sum; the result is valid in thread 0.
@@ -478,24 +598,40 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
   const int r_lo = crank * r_half, r_hi = min(D, r_lo + r_half);
   double2* pl_peer = pl;
   if constexpr (CL == 2) pl_peer = cooperative_groups::this_cluster().map_shared_rank(pl, crank ^ 1);
-  for (int r = r_lo + tid; r < r_hi; r += bs) {
+  // Real amplitudes: two threads per output row, one on the row's even slots and
+  // one on its odd slots, added (even + odd) by a fixed shuffle; the split
+  // depends on nothing but the row, so every launch form gives the same bits.
+  constexpr int TPR = REAL ? 2 : 1;
+  const int rows = r_hi - r_lo, per_pass = bs / TPR, half = tid % TPR;
+  for (int base = 0; base < rows; base += per_pass) {  // same trip count in every thread
+    const int lr = base + tid / TPR;
+    const bool live = lr < rows;
+    const int r = r_lo + (live ? lr : 0);
     const uint32_t k = __ldg(d.sector + r);
     T acc = A::zero();
-    ell_row(d.ell, nullptr, W, D, r, [&](uint32_t gi) {
-      const GroupRec g = load_group(tg + gi);
-      const uint32_t src = k ^ g.x;
-      if constexpr (REAL)
-        A::mac(acc, group_coef<REAL>(g, te, tv, src), pl[src].x);
-      else
-        A::mac(acc, group_coef<REAL>(g, te, tv, src), psi[src]);
-    });
-    if constexpr (REAL) {
-      pl[k].y = acc;
-      if constexpr (CL == 2) pl_peer[k].y = acc;
-      e_part += pl[k].x * acc;
-    } else {
-      lam[k] = acc;
-      e_part += A::redot(psi[k], acc);
+    if (live) {
+      ell_row(d.ell, nullptr, W, D, r, half, TPR, [&](uint32_t gi) {
+        const GroupRec g = load_group(tg + gi);
+        const uint32_t src = k ^ g.x;
+        if constexpr (REAL)
+          A::mac(acc, group_coef<REAL>(g, te, tv, src), pl[src].x);
+        else
+          A::mac(acc, group_coef<REAL>(g, te, tv, src), psi[src]);
+      });
+    }
+    if constexpr (TPR == 2) {
+      const double odd = __shfl_xor_sync(0xffffffffu, acc, 1);
+      acc = acc + odd;  // used by the even-slot thread only
+    }
+    if (live && half == 0) {
+      if constexpr (REAL) {
+        pl[k].y = acc;
+        if constexpr (CL == 2) pl_peer[k].y = acc;
+        e_part += pl[k].x * acc;
+      } else {
+        lam[k] = acc;
+        e_part += A::redot(psi[k], acc);
+      }
     }
   }
   const double e_tot = block_sum(e_part, red);
@@ -660,6 +796,8 @@ __global__ void k_trig(const double* __restrict__ theta, int M, double2* __restr
   }
 }
 
+// The streaming kernels keep psi, phi and lambda compressed to the sector:
+// entry r is the amplitude of basis state sector[r].
 template <bool REAL>
 __global__ void k_init_sector(const uint32_t* __restrict__ sector, int64_t D, uint32_t hf,
                               typename Amp<REAL>::T* __restrict__ psi) {
@@ -667,28 +805,27 @@ __global__ void k_init_sector(const uint32_t* __restrict__ sector, int64_t D, ui
   for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < D;
        r += int64_t(gridDim.x) * blockDim.x) {
     const uint32_t k = __ldg(sector + r);
-    psi[k] = (k == hf) ? A::unit() : A::zero();
+    psi[r] = (k == hf) ? A::unit() : A::zero();
   }
 }
 
+// rp[p] = (rank(k) | sign << 31, rank(k ^ flip)) of pair p; sign = (-1)-bit of T|k>
 template <bool REAL>
-__global__ void k_gate_fwd(const uint32_t* __restrict__ pairs, int64_t P, const GateRec* __restrict__ gate,
-                           const double2* __restrict__ cs, typename Amp<REAL>::T* __restrict__ psi) {
+__global__ void k_gate_fwd(const uint2* __restrict__ rp, int64_t P, const double2* __restrict__ cs,
+                           typename Amp<REAL>::T* __restrict__ psi) {
   typedef Amp<REAL> A;
   typedef typename A::T T;
-  const GateRec gr = load_gate(gate);
   const double2 c_s = __ldg(cs);
-  const int s0 = gr.sign0 < 0;
   for (int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; p < P;
        p += int64_t(gridDim.x) * blockDim.x) {
-    const uint32_t k = __ldg(pairs + p);
-    const uint32_t k2 = k ^ gr.flip;
-    const int sb = parity32(k & gr.par) ^ s0;
+    const uint2 pr = __ldg(rp + p);
+    const uint32_t ra = pr.x & 0x7fffffffu, rb = pr.y;
+    const int sb = int(pr.x >> 31);
     const double ss = sflip(c_s.y, sb), nss = sflip(c_s.y, sb ^ 1);
-    T a = psi[k], b = psi[k2];
+    T a = psi[ra], b = psi[rb];
     A::rot(a, b, c_s.x, ss, nss);
-    psi[k] = a;
-    psi[k2] = b;
+    psi[ra] = a;
+    psi[rb] = b;
   }
 }
 
@@ -709,21 +846,18 @@ k_hpsi(const InstDesc d, int n_elec, int n_alpha, const typename Amp<REAL>::T* _
     const uint32_t k = __ldg(d.sector + r);
     T acc = A::zero();
     if (ELL) {
-      ell_row(d.ell, d.ell16, d.W, d.D, r, [&](uint32_t gi) {
-        const GroupRec g = load_group(d.groups + gi);
-        const uint32_t src = k ^ g.x;
-        A::mac(acc, group_coef<REAL>(g, d.emask, tv, src), psi[src]);
-      });
+      acc = hpsi_row<REAL, 4>(d.ell, d.ell16, d.W, d.D, r, k, d.groups, d.emask, tv, psi, d.rank_hi,
+                                         d.rank_lo, d.lo_bits);
     } else {
       for (int gi = 0; gi < d.G; ++gi) {
         const GroupRec g = load_group(d.groups + gi);
         const uint32_t src = k ^ g.x;
         if (!in_sector(src, n_elec, n_alpha)) continue;
-        A::mac(acc, group_coef<REAL>(g, d.emask, tv, src), psi[src]);
+        A::mac(acc, group_coef<REAL>(g, d.emask, tv, src), psi[sector_rank(d, src)]);
       }
     }
-    lam[k] = acc;
-    e_part += A::redot(psi[k], acc);
+    lam[r] = acc;
+    e_part += A::redot(psi[r], acc);
   }
   const double s = block_sum(e_part, red);
   if (threadIdx.x == 0) epart[blockIdx.x] = s;
@@ -731,30 +865,28 @@ k_hpsi(const InstDesc d, int n_elec, int n_alpha, const typename Amp<REAL>::T* _
 
 template <bool REAL>
 __global__ void __launch_bounds__(kStreamThreads, 1)
-k_gate_adj(const uint32_t* __restrict__ pairs, int64_t P, const GateRec* __restrict__ gate,
-           const double2* __restrict__ cs, typename Amp<REAL>::T* __restrict__ phi,
-           typename Amp<REAL>::T* __restrict__ lam, double* __restrict__ gpart) {
+k_gate_adj(const uint2* __restrict__ rp, int64_t P, const double2* __restrict__ cs,
+           typename Amp<REAL>::T* __restrict__ phi, typename Amp<REAL>::T* __restrict__ lam,
+           double* __restrict__ gpart) {
   typedef Amp<REAL> A;
   typedef typename A::T T;
   __shared__ double red[32];
-  const GateRec gr = load_gate(gate);
   const double2 c_s = __ldg(cs);
-  const int s0 = gr.sign0 < 0;
   double acc = 0.0;
   for (int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; p < P;
        p += int64_t(gridDim.x) * blockDim.x) {
-    const uint32_t k = __ldg(pairs + p);
-    const uint32_t k2 = k ^ gr.flip;
-    const int sb = parity32(k & gr.par) ^ s0;
+    const uint2 pr = __ldg(rp + p);
+    const uint32_t ra = pr.x & 0x7fffffffu, rb = pr.y;
+    const int sb = int(pr.x >> 31);
     const double ss = sflip(c_s.y, sb), nss = sflip(c_s.y, sb ^ 1);
-    T pa = phi[k], pb = phi[k2], la = lam[k], lb = lam[k2];
+    T pa = phi[ra], pb = phi[rb], la = lam[ra], lb = lam[rb];
     acc += sflip(A::cross(lb, pa, la, pb), sb);
     A::rot(pa, pb, c_s.x, nss, ss);
     A::rot(la, lb, c_s.x, nss, ss);
-    phi[k] = pa;
-    phi[k2] = pb;
-    lam[k] = la;
-    lam[k2] = lb;
+    phi[ra] = pa;
+    phi[rb] = pb;
+    lam[ra] = la;
+    lam[rb] = lb;
   }
   const double s = block_sum(acc, red);
   if (threadIdx.x == 0) gpart[blockIdx.x] = s;
@@ -781,7 +913,7 @@ __global__ void k_scatter_out(const uint32_t* __restrict__ sector, int64_t D,
   for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < D;
        r += int64_t(gridDim.x) * blockDim.x) {
     const uint32_t k = __ldg(sector + r);
-    out[k] = Amp<REAL>::to_c(v[k]);
+    out[k] = Amp<REAL>::to_c(v[r]);
   }
 }
 
@@ -790,7 +922,7 @@ __global__ void k_gather_in(const uint32_t* __restrict__ sector, int64_t D, cons
   for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < D;
        r += int64_t(gridDim.x) * blockDim.x) {
     const uint32_t k = __ldg(sector + r);
-    v[k] = in[k];
+    v[r] = in[k];
   }
 }
 
@@ -831,7 +963,7 @@ __global__ void kb_init(BatchDev b, BatchSegs sg) {
     const InstDesc* d = b.desc + i;
     double* psi = reinterpret_cast<double*>(b.ws + b.psi_off[i]);
     const uint32_t k = __ldg(d->sector + r);
-    psi[k] = (k == d->hf) ? 1.0 : 0.0;
+    psi[r] = (k == d->hf) ? 1.0 : 0.0;
   }
 }
 
@@ -842,16 +974,15 @@ __global__ void __launch_bounds__(512) kb_gate_fwd(int m, BatchDev b, BatchSegs 
     const int64_t q = t - __ldg(sg.pref + s);
     const InstDesc* d = b.desc + i;
     double* psi = reinterpret_cast<double*>(b.ws + b.psi_off[i]);
-    const GateRec gr = load_gate(d->gates + m);
     const double2 c_s = b.cs[int64_t(i) * b.Mmax + m];
-    const uint32_t k = __ldg(d->pairs + __ldg(d->pair_off + m) + q);
-    const uint32_t k2 = k ^ gr.flip;
-    const int sb = parity32(k & gr.par) ^ (gr.sign0 < 0);
+    const uint2 pr = __ldg(d->rpairs + __ldg(d->pair_off + m) + q);
+    const uint32_t ra = pr.x & 0x7fffffffu, rb = pr.y;
+    const int sb = int(pr.x >> 31);
     const double ss = sflip(c_s.y, sb), nss = sflip(c_s.y, sb ^ 1);
-    double a = psi[k], bb = psi[k2];
+    double a = psi[ra], bb = psi[rb];
     Amp<true>::rot(a, bb, c_s.x, ss, nss);
-    psi[k] = a;
-    psi[k2] = bb;
+    psi[ra] = a;
+    psi[rb] = bb;
   }
 }
 
@@ -873,22 +1004,19 @@ __global__ void __launch_bounds__(512, 1) kb_hpsi(BatchDev b, BatchSegs sg) {
     if (W > 0) {
       const uint32_t* ell = d->ell;
       const uint16_t* ell16 = d->ell16;
-      ell_row(ell, ell16, W, D, r, [&](uint32_t gi) {
-        const GroupRec g = load_group(groups + gi);
-        const uint32_t src = k ^ g.x;
-        acc = fma(group_coef<true>(g, emask, vals, src), psi[src], acc);
-      });
+      acc = hpsi_row<true, 4>(ell, ell16, W, D, r, k, groups, emask, vals, psi, d->rank_hi, d->rank_lo,
+                              d->lo_bits);
     } else {
       const int ne = d->n_elec, na = d->n_alpha;
       for (int gi = 0; gi < G; ++gi) {
         const GroupRec g = load_group(groups + gi);
         const uint32_t src = k ^ g.x;
         if (!in_sector(src, ne, na)) continue;
-        acc = fma(group_coef<true>(g, emask, vals, src), psi[src], acc);
+        acc = fma(group_coef<true>(g, emask, vals, src), psi[sector_rank(*d, src)], acc);
       }
     }
-    lam[k] = acc;
-    b.ebuf[b.ebase[i] + r] = psi[k] * acc;
+    lam[r] = acc;
+    b.ebuf[b.ebase[i] + r] = psi[r] * acc;
   }
 }
 
@@ -912,21 +1040,20 @@ __global__ void __launch_bounds__(512) kb_gate_adj(int m, BatchDev b, BatchSegs 
     const InstDesc* d = b.desc + i;
     double* phi = reinterpret_cast<double*>(b.ws + b.psi_off[i]);
     double* lam = reinterpret_cast<double*>(b.ws + b.lam_off[i]);
-    const GateRec gr = load_gate(d->gates + m);
     const double2 c_s = b.cs[int64_t(i) * b.Mmax + m];
     const int64_t p = __ldg(d->pair_off + m) + q;
-    const uint32_t k = __ldg(d->pairs + p);
-    const uint32_t k2 = k ^ gr.flip;
-    const int sb = parity32(k & gr.par) ^ (gr.sign0 < 0);
+    const uint2 pr = __ldg(d->rpairs + p);
+    const uint32_t ra = pr.x & 0x7fffffffu, rb = pr.y;
+    const int sb = int(pr.x >> 31);
     const double ss = sflip(c_s.y, sb), nss = sflip(c_s.y, sb ^ 1);
-    double pa = phi[k], pb = phi[k2], la = lam[k], lb = lam[k2];
+    double pa = phi[ra], pb = phi[rb], la = lam[ra], lb = lam[rb];
     b.gbuf[b.gbase[i] + p] = sflip(Amp<true>::cross(lb, pa, la, pb), sb);
     Amp<true>::rot(pa, pb, c_s.x, nss, ss);
     Amp<true>::rot(la, lb, c_s.x, nss, ss);
-    phi[k] = pa;
-    phi[k2] = pb;
-    lam[k] = la;
-    lam[k2] = lb;
+    phi[ra] = pa;
+    phi[rb] = pb;
+    lam[ra] = la;
+    lam[rb] = lb;
   }
 }
 
@@ -1039,8 +1166,7 @@ cudaError_t stream_forward(const InstDesc& d, const StreamPlan& sp, const Stream
   for (int m = 0; m < d.M; ++m) {
     const int64_t p0 = sp.pair_off_host[m], p1 = sp.pair_off_host[m + 1];
     if (p1 > p0)
-      k_gate_fwd<REAL><<<stream_grid(p1 - p0), nt, 0, stream>>>(d.pairs + p0, p1 - p0, d.gates + m,
-                                                                b.cs + m, psi);
+      k_gate_fwd<REAL><<<stream_grid(p1 - p0), nt, 0, stream>>>(d.rpairs + p0, p1 - p0, b.cs + m, psi);
   }
   return cudaGetLastError();
 }
@@ -1069,8 +1195,8 @@ cudaError_t stream_adjoint(const InstDesc& d, const StreamPlan& sp, const Stream
   for (int m = d.M - 1; m >= 0; --m) {
     const int64_t p0 = sp.pair_off_host[m], p1 = sp.pair_off_host[m + 1];
     double* gp = b.gpart + int64_t(m) * kMaxPartials;
-    k_gate_adj<REAL><<<stream_grid(p1 - p0), kStreamThreads, 0, stream>>>(
-        d.pairs + p0, p1 - p0, d.gates + m, b.cs + m, phi, lam, gp);
+    k_gate_adj<REAL><<<stream_grid(p1 - p0), kStreamThreads, 0, stream>>>(d.rpairs + p0, p1 - p0, b.cs + m,
+                                                                          phi, lam, gp);
   }
   if (d.M > 0) k_finalize<<<d.M, 32, 0, stream>>>(b.gpart, sp.d_nb_rows, d.M, 2.0, grad);
   return cudaGetLastError();

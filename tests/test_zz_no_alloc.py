@@ -67,9 +67,9 @@ def test_noalloc_matches_regular_entry_on_two_calls(lib):
 
 
 def test_noalloc_rejects_instances_beyond_the_scratch(lib):
-    n = 22
+    n = 26  # 13 electrons: 1716 x 1716 sector states, 47 MB of real amplitudes > 16 MiB
     H = vq.Hamiltonian(n, [0], [1], [1.0])
-    A = vq.Ansatz(n, synth.hf_bitstring(11), [[0, 12, -1, -1]])
+    A = vq.Ansatz(n, synth.hf_bitstring(13), [[0, 14, -1, -1]])
     theta = torch.zeros(1, dtype=torch.float64, device="cuda")
     e = torch.zeros(1, dtype=torch.float64, device="cuda")
     g = torch.zeros(1, dtype=torch.float64, device="cuda")
