@@ -550,6 +550,7 @@ InstDesc make_desc(vqe_hamiltonian_t h, vqe_ansatz_t a, const vqe_hamiltonian_s:
   d.rank_hi = a->d_rank_hi;
   d.rank_lo = a->d_rank_lo;
   d.lo_bits = a->lo_bits;
+  d.hf_rank = int32_t(a->rank_hi[a->hf >> a->lo_bits] + a->rank_lo[a->hf & ((1u << a->lo_bits) - 1u)]);
   d.gates = a->d_gates;
   d.pair_off = a->d_pair_off;
   d.pairs = a->d_pairs;
@@ -579,6 +580,7 @@ bool use_fixed(bool real) { return real && (g_flags & VQE_FLAG_FP64_SWEEPS) == 0
 bool resident_fit(vqe_ansatz_t a, const vqe_hamiltonian_s::Ell* e, bool real, InstDesc* d, size_t* smem) {
   if (g_flags & VQE_FLAG_FORCE_STREAMING) return false;
   if (!e->use_ell || !e->d_ell || a->n > 16) return false;
+  if (a->sector.size() > 32767) return false;  // 15-bit ranks in the staged pair list
   if (a->pairs.size() > (size_t(1) << 24) || d->S > (1 << 24) || d->G > (1 << 20)) return false;
   int dev = 0, optin = 0;
   if (cudaGetDevice(&dev) != cudaSuccess) return false;
@@ -586,7 +588,8 @@ bool resident_fit(vqe_ansatz_t a, const vqe_hamiltonian_s::Ell* e, bool real, In
     return false;
   const int P = int(a->pairs.size());
   for (int stage = 1; stage >= 0; --stage) {
-    const vqe::ResidentLayout L = vqe::resident_layout(a->n, a->M, P, d->G, d->E, d->S, real, stage != 0);
+    const vqe::ResidentLayout L = vqe::resident_layout(a->n, a->M, P, d->G, d->E, d->S, int(a->sector.size()),
+                                                       a->lo_bits, real, stage != 0);
     if (L.total <= uint32_t(optin)) {
       d->stage_tables = stage;
       d->sweep_threads = 128;

@@ -62,7 +62,7 @@ struct InstDesc {
   // of sector state k in sector[]; the streaming kernels store amplitudes there
   const uint32_t* rank_hi;
   const uint32_t* rank_lo;
-  int32_t lo_bits, pad1;
+  int32_t lo_bits, hf_rank;  // hf_rank = rank(hf)
   // Hamiltonian
   int32_t G, W;              // groups, connectivity slots per output
   const GroupRec* groups;    // [G]
@@ -109,39 +109,43 @@ cudaError_t batch_stream_run(const BatchDev& b, const BatchSegs* gate_segs, cons
                              int64_t ld_grad, int threads, cudaStream_t stream);
 
 // Shared-memory layout of the resident kernel (byte offsets), computed the same
-// way on the host (to size the launch) and on the device (to carve it).
+// way on the host (to size the launch) and on the device (to carve it). The
+// state is compressed to the sector (D entries): real amplitudes as D double2
+// {psi, lambda}, complex ones as psi[D] and lambda[D].
 struct ResidentLayout {
-  uint32_t psi, lam, cs, gates, poff, pairs, uni, red, total;
+  uint32_t psi, lam, cs, gates, poff, pairs, rank, gbuf, tab, red, total;
 };
 
 __host__ __device__ inline uint32_t align_up(uint32_t v, uint32_t a) { return (v + a - 1) / a * a; }
 
-// Table part of the union region: groups, then entry masks, then values.
+// Staged H psi tables: groups, then entry masks, then values.
 __host__ __device__ inline uint32_t staged_table_bytes(int G, int E, int S, bool real) {
   return uint32_t(G) * 32u + align_up(uint32_t(E) * 4u, 16u) + uint32_t(S) * (real ? 8u : 16u);
 }
 
-__host__ __device__ inline ResidentLayout resident_layout(int n, int M, int P, int G, int E, int S,
+__host__ __device__ inline ResidentLayout resident_layout(int n, int M, int P, int G, int E, int S, int D, int lo_bits,
                                                           bool real, bool stage) {
   ResidentLayout L;
-  const uint32_t amp = real ? 8u : 16u, dim = 1u << n;
   L.psi = 0;
-  L.lam = dim * amp;
-  uint32_t o = 2u * dim * amp;
+  L.lam = real ? 0u : uint32_t(D) * 16u;
+  uint32_t o = (real ? 1u : 2u) * uint32_t(D) * 16u;
   L.cs = align_up(o, 16u);
   o = L.cs + uint32_t(M) * 16u;
   L.gates = align_up(o, 16u);
   o = L.gates + uint32_t(M) * 16u;
   L.poff = o;
   o += uint32_t(M + 1) * 4u;
-  L.pairs = align_up(o, 16u);
+  L.pairs = align_up(o, 16u);  // ra | sign << 15 | rb << 16 per pair
   o = L.pairs + uint32_t(P) * 4u;
-  L.uni = align_up(o, 16u);
-  // gradient contributions of the reverse sweep: two per pair with real amplitudes
-  // (one per lane of the pair), one per pair with complex amplitudes
-  const uint32_t gb = uint32_t(P) * (real ? 16u : 8u);
-  const uint32_t tb = stage ? staged_table_bytes(G, E, S, real) : 0u;  // tables (H psi)
-  o = L.uni + (gb > tb ? gb : tb);
+  L.rank = align_up(o, 16u);   // u16 rank tables: high part, then low part
+  o = L.rank + ((1u << (n - lo_bits)) + (1u << lo_bits)) * 2u;
+  // per-pair slots: with real amplitudes two per pair (one per lane of the pair),
+  // holding the forward sweep's output and later the gradient contribution; with
+  // complex amplitudes one gradient contribution per pair
+  L.gbuf = align_up(o, 16u);
+  o = L.gbuf + uint32_t(P) * (real ? 16u : 8u);
+  L.tab = align_up(o, 16u);
+  o = L.tab + (stage ? staged_table_bytes(G, E, S, real) : 0u);
   L.red = align_up(o, 16u);
   L.total = L.red + 64u * 8u;
   return L;

@@ -387,15 +387,20 @@ __device__ __forceinline__ void sweep_barrier(int nthreads) {
   asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
 }
 
-// One CTA evaluates one instance with psi and lambda in shared memory: HF
-// init, forward sweep, H psi with the energy, and the reverse sweep with
-// per-pair gradient contributions summed per gate in pair order at the end.
-// Gate records, cos/sin, pair offsets and pair lists are staged in shared
-// memory first. The sweeps run on the first `sweep_threads` threads (one warp
-// per SM sub-partition or more) with a named barrier between gates; the
-// instance's pairs are dealt round-robin over those warps. The H psi tables
-// are staged into the region the reverse sweep later uses for its per-pair
-// contributions, when they fit.
+// One CTA evaluates one instance with its state in shared memory, compressed to
+// the sector (entry r is the amplitude of sector[r]): HF init, forward sweep,
+// H psi with the energy, and the reverse sweep with per-pair gradient
+// contributions summed per gate in pair order at the end. Gate records,
+// cos/sin, pair offsets, pair lists (two ranks and the JW sign per pair) and
+// the rank tables are staged in shared memory first; H psi finds a source
+// k ^ x through the rank tables. The sweeps run on the first `sweep_threads`
+// threads (one warp per SM sub-partition or more) with a named barrier between
+// gates; the instance's pairs are dealt round-robin over those warps.
+//
+// Real amplitudes: two lanes per pair. The forward sweep also keeps each lane's
+// output in that lane's per-pair slot: it is phi at that gate, which the
+// reverse sweep then reads instead of un-rotating phi, so the reverse sweep
+// rotates lambda only and leaves the gradient contribution in the same slot.
 //
 // CL = 2 (real amplitudes only): a cluster of two CTAs per instance. Both run the
 // sweeps identically; each computes lambda for half of the outputs and writes it
@@ -423,19 +428,23 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
   }
   const int tid = threadIdx.x, bs = blockDim.x;
   const int n = d.n, M = d.M, G = d.G, W = d.W;
-  const uint32_t dim = 1u << n;
   const int D = int(d.D);
   const int P = int(d.pair_off[M]);
   const bool stage = d.stage_tables != 0;
   const int sw = d.sweep_threads;
-  const ResidentLayout L = resident_layout(n, M, P, G, d.E, d.S, REAL, stage);
+  const int lb = d.lo_bits, hb = n - lb;
+  const uint32_t lo_mask = (1u << lb) - 1u;
+  const ResidentLayout L = resident_layout(n, M, P, G, d.E, d.S, D, lb, REAL, stage);
   T* psi = reinterpret_cast<T*>(smem + L.psi);
   T* lam = reinterpret_cast<T*>(smem + L.lam);
+  double2* pl = reinterpret_cast<double2*>(smem + L.psi);  // real: pl[r] = {psi_r, lambda_r}
   double2* cs = reinterpret_cast<double2*>(smem + L.cs);
   GateRec* gates = reinterpret_cast<GateRec*>(smem + L.gates);
   int32_t* poff = reinterpret_cast<int32_t*>(smem + L.poff);
-  uint32_t* pairs = reinterpret_cast<uint32_t*>(smem + L.pairs);
-  double* gbuf = reinterpret_cast<double*>(smem + L.uni);
+  uint32_t* rp = reinterpret_cast<uint32_t*>(smem + L.pairs);
+  uint16_t* rhi = reinterpret_cast<uint16_t*>(smem + L.rank);
+  uint16_t* rlo = rhi + (1 << hb);
+  double* gbuf = reinterpret_cast<double*>(smem + L.gbuf);
   double* red = reinterpret_cast<double*>(smem + L.red);
   const int64_t row = d.inst;
   const double* th = theta + row * ld_theta;
@@ -455,16 +464,18 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
     gates[m] = gr;
   }
   for (int m = tid; m <= M; m += bs) poff[m] = int32_t(__ldg(d.pair_off + m));
-  for (int p = tid; p < P; p += bs) pairs[p] = __ldg(d.pairs + p);
-  // real amplitudes: psi and lambda interleaved, pl[k] = {psi_k, lambda_k}, so
-  // the reverse sweep moves both with one 16-byte access
-  double2* pl = reinterpret_cast<double2*>(smem + L.psi);
+  for (int p = tid; p < P; p += bs) {
+    const uint2 e = __ldg(d.rpairs + p);
+    rp[p] = (e.x & 0x7fffu) | ((e.x >> 31) << 15) | (e.y << 16);
+  }
+  for (int i = tid; i < (1 << hb); i += bs) rhi[i] = uint16_t(__ldg(d.rank_hi + i));
+  for (int i = tid; i < (1 << lb); i += bs) rlo[i] = uint16_t(__ldg(d.rank_lo + i));
   if constexpr (REAL) {
-    for (uint32_t k = tid; k < dim; k += bs) pl[k] = make_double2(0.0, 0.0);
+    for (int r = tid; r < D; r += bs) pl[r] = make_double2(0.0, 0.0);
   } else {
-    for (uint32_t k = tid; k < dim; k += bs) {
-      psi[k] = A::zero();
-      lam[k] = A::zero();
+    for (int r = tid; r < D; r += bs) {
+      psi[r] = A::zero();
+      lam[r] = A::zero();
     }
   }
   // pull the tables H psi reads later into L2 while the forward sweep runs
@@ -481,16 +492,16 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
   __syncthreads();
   if (tid == 0) {
     if constexpr (FIX)
-      pl[d.hf].x = llbits(1ll << 62);
+      pl[d.hf_rank].x = llbits(1ll << 62);
     else if constexpr (REAL)
-      pl[d.hf].x = 1.0;
+      pl[d.hf_rank].x = 1.0;
     else
-      psi[d.hf] = A::unit();
+      psi[d.hf_rank] = A::unit();
   }
   __syncthreads();
 
   // lane-interleaved position of this thread in the sweep: consecutive pairs go
-  // to consecutive warps so every sub-partition gets FP64 work on small gates
+  // to consecutive warps so every sub-partition gets work on small gates
   const int swarps = sw >> 5;
   // complex: one lane per pair, consecutive pairs on consecutive warps;
   // real: two adjacent lanes per pair (role 0 and 1), pairs dealt the same way
@@ -498,62 +509,68 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
   const int pstride = REAL ? (sw >> 1) : sw;
   const int spos = REAL ? (((tid & 31) >> 1) * swarps + (tid >> 5)) : ((tid & 31) * swarps + (tid >> 5));
 
-  // a2: forward sweep. The next gate's record, cos/sin and first pair index
-  // are loaded before the current gate runs, off the barrier-to-barrier path.
+  // a2: forward sweep. The next gate's record, cos/sin and first pair are
+  // loaded before the current gate runs, off the barrier-to-barrier path.
   if (tid < sw && M > 0) {
     GateRec gr = gates[0];
     int p0 = poff[0], cnt = poff[1] - p0;
     double2 c_s = cs[0];
-    uint32_t kf = (spos < cnt) ? pairs[p0 + spos] : 0u;
+    uint32_t ef = (spos < cnt) ? rp[p0 + spos] : 0u;
     for (int m = 0; m < M; ++m) {
       GateRec grn = gr;
       int p0n = 0, cntn = 0;
       double2 c_sn = c_s;
-      uint32_t kfn = 0u;
+      uint32_t efn = 0u;
       if (m + 1 < M) {
         grn = gates[m + 1];
         p0n = poff[m + 1];
         cntn = poff[m + 2] - p0n;
         c_sn = cs[m + 1];
-        if (spos < cntn) kfn = pairs[p0n + spos];
+        if (spos < cntn) efn = rp[p0n + spos];
       }
-      const int s0 = gr.sign0 < 0;
       if constexpr (REAL) {
-        // two lanes per pair: role 0 writes c a - s b to k, role 1 writes c b + s a
-        // to k2; both lanes read before either writes (warp-uniform trip count,
-        // lanes past the gate's end read index 0 and store nothing)
+        // two lanes per pair: role 0 writes c a - s b at ra, role 1 writes c b + s a
+        // at rb; both lanes read before either writes (warp-uniform trip count,
+        // lanes past the gate's end read entry 0 and store nothing)
         for (int q0 = 0; q0 < cnt; q0 += pstride) {
           const int q = q0 + spos;
           const bool act = q < cnt;
-          const uint32_t kraw = (q0 == 0) ? kf : pairs[p0 + min(q, cnt - 1)];
-          const uint32_t k = act ? kraw : 0u;
-          const uint32_t k2 = k ^ (act ? gr.flip : 0u);
-          const uint32_t kd = role ? k2 : k;
+          const uint32_t e = (q0 == 0) ? ef : rp[p0 + min(q, cnt - 1)];
+          const uint32_t ra = e & 0x7fffu, rb = e >> 16;
+          const int sgn = int((e >> 15) & 1u);
+          const uint32_t kd = role ? rb : ra, ko = role ? ra : rb;
+          const int slot = 2 * (p0 + q) + role;
           if constexpr (FIX) {
-            const long long self = dbits(pl[kd].x), other = dbits(pl[role ? k : k2].x);
-            const int sneg = parity32(k & gr.par) ^ s0 ^ role ^ 1 ^ ((gr.pad >> 1) & 1);
+            const long long self = dbits(pl[kd].x), other = dbits(pl[ko].x);
+            const int sneg = sgn ^ role ^ 1 ^ ((gr.pad >> 1) & 1);
             __syncwarp();
             const long long out = neg_if(mulhi_su(self, static_cast<unsigned long long>(dbits(c_s.x))), gr.pad & 1) +
                                   neg_if(mulhi_su(other, static_cast<unsigned long long>(dbits(c_s.y))), sneg);
-            if (act) pl[kd].x = llbits(out);
+            if (act) {
+              pl[kd].x = llbits(out);
+              gbuf[slot] = llbits(out);
+            }
           } else {
-            const double self = pl[kd].x, other = pl[role ? k : k2].x;
-            const double coef = sflip(c_s.y, parity32(k & gr.par) ^ s0 ^ role ^ 1);
+            const double self = pl[kd].x, other = pl[ko].x;
+            const double coef = sflip(c_s.y, sgn ^ role ^ 1);
             __syncwarp();
             const double out = fma(coef, other, c_s.x * self);
-            if (act) pl[kd].x = out;
+            if (act) {
+              pl[kd].x = out;
+              gbuf[slot] = out;
+            }
           }
         }
       } else {
         for (int q = spos; q < cnt; q += sw) {
-          const uint32_t k = (q == spos) ? kf : pairs[p0 + q];
-          const uint32_t k2 = k ^ gr.flip;
-          const int sb = parity32(k & gr.par) ^ s0;
+          const uint32_t e = (q == spos) ? ef : rp[p0 + q];
+          const uint32_t ra = e & 0x7fffu, rb = e >> 16;
+          const int sb = int((e >> 15) & 1u);
           const double ss = sflip(c_s.y, sb), nss = sflip(c_s.y, sb ^ 1);
-          T a = psi[k], b = psi[k2];
+          T a = psi[ra], b = psi[rb];
           A::rot(a, b, c_s.x, ss, nss);
-          psi[k] = a;
-          psi[k2] = b;
+          psi[ra] = a;
+          psi[rb] = b;
         }
       }
       sweep_barrier(sw);
@@ -561,18 +578,18 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
       p0 = p0n;
       cnt = cntn;
       c_s = c_sn;
-      kf = kfn;
+      ef = efn;
     }
   }
-  // stage the H psi tables into the union region
+  // stage the H psi tables
   const GroupRec* tg = d.groups;
   const uint32_t* te = d.emask;
   const C* tv;
   if constexpr (REAL) tv = d.vals; else tv = d.cvals;
   if (stage) {
-    GroupRec* sg = reinterpret_cast<GroupRec*>(smem + L.uni);
-    uint32_t* se = reinterpret_cast<uint32_t*>(smem + L.uni + uint32_t(G) * 32u);
-    C* sv = reinterpret_cast<C*>(smem + L.uni + uint32_t(G) * 32u + align_up(uint32_t(d.E) * 4u, 16u));
+    GroupRec* sg = reinterpret_cast<GroupRec*>(smem + L.tab);
+    uint32_t* se = reinterpret_cast<uint32_t*>(smem + L.tab + uint32_t(G) * 32u);
+    C* sv = reinterpret_cast<C*>(smem + L.tab + uint32_t(G) * 32u + align_up(uint32_t(d.E) * 4u, 16u));
     const int4* gsrc = reinterpret_cast<const int4*>(d.groups);
     int4* gdst = reinterpret_cast<int4*>(sg);
     for (int i = tid; i < 2 * G; i += bs) gdst[i] = __ldg(gsrc + i);
@@ -584,11 +601,8 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
   }
   __syncthreads();
   if constexpr (FIX) {
-    // psi in Q1.62 -> FP64 for H psi (entries outside the sector stay 0 = +0.0)
-    for (int r = tid; r < D; r += bs) {
-      const uint32_t k = __ldg(d.sector + r);
-      pl[k].x = __ll2double_rn(dbits(pl[k].x)) * 0x1p-62;
-    }
+    // psi in Q1.62 -> FP64 for H psi
+    for (int r = tid; r < D; r += bs) pl[r].x = __ll2double_rn(dbits(pl[r].x)) * 0x1p-62;
     __syncthreads();
   }
 
@@ -613,10 +627,11 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
       ell_row(d.ell, nullptr, W, D, r, half, TPR, [&](uint32_t gi) {
         const GroupRec g = load_group(tg + gi);
         const uint32_t src = k ^ g.x;
+        const uint32_t rs = uint32_t(rhi[src >> lb]) + uint32_t(rlo[src & lo_mask]);
         if constexpr (REAL)
-          A::mac(acc, group_coef<REAL>(g, te, tv, src), pl[src].x);
+          A::mac(acc, group_coef<REAL>(g, te, tv, src), pl[rs].x);
         else
-          A::mac(acc, group_coef<REAL>(g, te, tv, src), psi[src]);
+          A::mac(acc, group_coef<REAL>(g, te, tv, src), psi[rs]);
       });
     }
     if constexpr (TPR == 2) {
@@ -625,12 +640,12 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
     }
     if (live && half == 0) {
       if constexpr (REAL) {
-        pl[k].y = acc;
-        if constexpr (CL == 2) pl_peer[k].y = acc;
-        e_part += pl[k].x * acc;
+        pl[r].y = acc;
+        if constexpr (CL == 2) pl_peer[r].y = acc;
+        e_part += pl[r].x * acc;
       } else {
-        lam[k] = acc;
-        e_part += A::redot(psi[k], acc);
+        lam[r] = acc;
+        e_part += A::redot(psi[r], acc);
       }
     }
   }
@@ -646,15 +661,15 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
 
   if (!with_grad) return;
 
-  // Fixed point for the reverse sweep: phi in Q1.62 and lambda scaled by
-  // 2^(61 - e), where 2^e bounds ||lambda|| (so every entry stays below 2^61 in
-  // magnitude through the rotations). Both CTAs of a cluster hold all of lambda
-  // here and derive the same e.
+  // Fixed point for the reverse sweep: lambda scaled by 2^(61 - e), where 2^e
+  // bounds ||lambda|| (so every entry stays below 2^61 in magnitude through the
+  // rotations); phi comes from the forward sweep's per-pair slots in Q1.62.
+  // Both CTAs of a cluster hold all of lambda here and derive the same e.
   int lam_e = 0;
   if constexpr (FIX) {
     double l2 = 0.0;
     for (int r = tid; r < D; r += bs) {
-      const double v = pl[__ldg(d.sector + r)].y;
+      const double v = pl[r].y;
       l2 = fma(v, v, l2);
     }
     const double tot = block_sum(l2, red);
@@ -664,11 +679,7 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
     // ||lambda||^2 < 2^(ex - 1022) <= 2^(2 lam_e)
     lam_e = ex == 0 ? -500 : (ex - 1022 + 1) >> 1;
     const double sc = pow2(61 - lam_e);
-    for (int r = tid; r < D; r += bs) {
-      const uint32_t k = __ldg(d.sector + r);
-      const double2 v = pl[k];
-      pl[k] = make_double2(llbits(__double2ll_rn(v.x * 0x1p62)), llbits(__double2ll_rn(v.y * sc)));
-    }
+    for (int r = tid; r < D; r += bs) pl[r].y = llbits(__double2ll_rn(pl[r].y * sc));
     __syncthreads();
   }
 
@@ -678,69 +689,70 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
     GateRec gr = gates[m];
     int p0 = poff[m], cnt = poff[m + 1] - p0;
     double2 c_s = cs[m];
-    uint32_t kf = (spos < cnt) ? pairs[p0 + spos] : 0u;
+    uint32_t ef = (spos < cnt) ? rp[p0 + spos] : 0u;
     for (; m >= 0; --m) {
       GateRec grn = gr;
       int p0n = 0, cntn = 0;
       double2 c_sn = c_s;
-      uint32_t kfn = 0u;
+      uint32_t efn = 0u;
       if (m > 0) {
         grn = gates[m - 1];
         p0n = poff[m - 1];
         cntn = poff[m] - p0n;
         c_sn = cs[m - 1];
-        if (spos < cntn) kfn = pairs[p0n + spos];
+        if (spos < cntn) efn = rp[p0n + spos];
       }
-      const int s0 = gr.sign0 < 0;
       if constexpr (REAL) {
-        // two lanes per pair: role 0 keeps s lb pa and un-applies at k, role 1
-        // keeps -s la pb and un-applies at k2 (phi and lambda alike)
+        // two lanes per pair: the lane's slot holds phi at its own index (role 0
+        // at ra, role 1 at rb); role 0 keeps s lambda_b phi_a, role 1 keeps
+        // -s lambda_a phi_b, and each un-applies the gate to lambda at its index
         for (int q0 = 0; q0 < cnt; q0 += pstride) {
           const int q = q0 + spos;
           const bool act = q < cnt;
-          const uint32_t kraw = (q0 == 0) ? kf : pairs[p0 + min(q, cnt - 1)];
-          const uint32_t k = act ? kraw : 0u;
-          const uint32_t k2 = k ^ (act ? gr.flip : 0u);
-          const int sr_bit = parity32(k & gr.par) ^ s0 ^ role;
-          const uint32_t ks = role ? k2 : k, ko = role ? k : k2;
-          const double2 sv = pl[ks], ov = pl[ko];
-          __syncwarp();
+          const int qc = min(q, cnt - 1);
+          const uint32_t e = (q0 == 0) ? ef : rp[p0 + qc];
+          const uint32_t ra = e & 0x7fffu, rb = e >> 16;
+          const int sr_bit = int((e >> 15) & 1u) ^ role;
+          const uint32_t ks = role ? rb : ra, ko = role ? ra : rb;
+          const int slot = 2 * (p0 + qc) + role;
           if constexpr (FIX) {
+            const long long ph = dbits(gbuf[slot]), ls = dbits(pl[ks].y), lo = dbits(pl[ko].y);
+            __syncwarp();
             const unsigned long long cm = static_cast<unsigned long long>(dbits(c_s.x));
             const unsigned long long sm = static_cast<unsigned long long>(dbits(c_s.y));
             const int cneg = gr.pad & 1, sneg = ((gr.pad >> 1) & 1) ^ sr_bit;
-            const long long ps = dbits(sv.x), ls = dbits(sv.y), po = dbits(ov.x), lo = dbits(ov.y);
-            const long long g_term = neg_if(__mul64hi(ps, lo), sr_bit);
-            const long long np = neg_if(mulhi_su(ps, cm), cneg) + neg_if(mulhi_su(po, sm), sneg);
+            const long long g_term = neg_if(__mul64hi(ph, lo), sr_bit);
             const long long nl = neg_if(mulhi_su(ls, cm), cneg) + neg_if(mulhi_su(lo, sm), sneg);
             if (act) {
-              gbuf[2 * (p0 + q) + role] = llbits(g_term);
-              pl[ks] = make_double2(llbits(np), llbits(nl));
+              gbuf[slot] = llbits(g_term);
+              pl[ks].y = llbits(nl);
             }
           } else {
+            const double ph = gbuf[slot], ls = pl[ks].y, lo = pl[ko].y;
+            __syncwarp();
             const double sr = sflip(c_s.y, sr_bit);
-            const double g_term = sflip(ov.y * sv.x, sr_bit);
-            const double2 nv = make_double2(fma(sr, ov.x, c_s.x * sv.x), fma(sr, ov.y, c_s.x * sv.y));
+            const double g_term = sflip(lo * ph, sr_bit);
+            const double nl = fma(sr, lo, c_s.x * ls);
             if (act) {
-              gbuf[2 * (p0 + q) + role] = g_term;
-              pl[ks] = nv;
+              gbuf[slot] = g_term;
+              pl[ks].y = nl;
             }
           }
         }
       } else {
         for (int q = spos; q < cnt; q += sw) {
-          const uint32_t k = (q == spos) ? kf : pairs[p0 + q];
-          const uint32_t k2 = k ^ gr.flip;
-          const int sb = parity32(k & gr.par) ^ s0;
+          const uint32_t e = (q == spos) ? ef : rp[p0 + q];
+          const uint32_t ra = e & 0x7fffu, rb = e >> 16;
+          const int sb = int((e >> 15) & 1u);
           const double ss = sflip(c_s.y, sb), nss = sflip(c_s.y, sb ^ 1);
-          T pa = psi[k], pb = psi[k2], la = lam[k], lb = lam[k2];
+          T pa = psi[ra], pb = psi[rb], la = lam[ra], lb = lam[rb];
           gbuf[p0 + q] = sflip(A::cross(lb, pa, la, pb), sb);
           A::rot(pa, pb, c_s.x, nss, ss);
           A::rot(la, lb, c_s.x, nss, ss);
-          psi[k] = pa;
-          psi[k2] = pb;
-          lam[k] = la;
-          lam[k2] = lb;
+          psi[ra] = pa;
+          psi[rb] = pb;
+          lam[ra] = la;
+          lam[rb] = lb;
         }
       }
       sweep_barrier(sw);
@@ -748,7 +760,7 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
       p0 = p0n;
       cnt = cntn;
       c_s = c_sn;
-      kf = kfn;
+      ef = efn;
     }
   }
   __syncthreads();
