@@ -47,10 +47,11 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=None)
-    ap.add_argument("--workload", choices=["scan12", "warmstart", "config3", "config2"], default="scan12",
+    ap.add_argument("--workload", choices=["scan12", "warmstart", "config3", "config2", "q24"], default="scan12",
                     help="scan12: the throughput line (default); warmstart: the 16-qubit learned-warm-start "
                          "comparison (time to 1 mHa vs the plain HF start); config3: one 30-qubit instance; "
-                         "config2: 256 uneven 14-20-qubit instances replayed from a CUDA graph")
+                         "config2: 256 uneven 14-20-qubit instances replayed from a CUDA graph; q24: one 24-qubit "
+                         "instance (10 electrons, 256 angles)")
     ap.add_argument("--held-out", type=int, default=24, help="warmstart: held-out scan points compared")
     return ap.parse_args()
 
@@ -293,11 +294,18 @@ def run_large(args):
     vq.load()
     steps, warmup = min(args.steps, 20), max(3, min(args.warmup, 5))
     t0 = time.perf_counter()
-    if args.workload == "config3":
-        w = synth.config3()
-        p, exc, th = w.problems[0], w.excitations[0], w.thetas[0]
-        H = vq.Hamiltonian.from_problem(p, w.drop_tol)
-        A = vq.Ansatz(30, synth.hf_bitstring(10), exc)
+    if args.workload in ("config3", "q24"):
+        if args.workload == "config3":
+            w = synth.config3()
+            p, exc, th, drop, nq = w.problems[0], w.excitations[0], w.thetas[0], w.drop_tol, 30
+        else:
+            rng = np.random.default_rng(24)
+            p = synth.integrals.random_problem(rng, 12, 10, 6, label="q24")
+            pool = synth.uccsd_pool(24, 10)
+            exc = pool[rng.permutation(len(pool))[:256]]
+            th, drop, nq = rng.normal(0.0, 0.05, size=256), 1e-14, 24
+        H = vq.Hamiltonian.from_problem(p, drop)
+        A = vq.Ansatz(nq, synth.hf_bitstring(10), exc)
         ws = vq.alloc_workspace(vq.workspace_bytes(H, A, vq.VQE_WS_GRAD))
         theta = torch.as_tensor(th).cuda()
         e_buf = torch.empty(1, dtype=torch.float64, device="cuda")
@@ -306,8 +314,9 @@ def run_large(args):
         ms = _timed(lambda: vq.energy_grad(H, A, theta, workspace=ws, out=(e_buf, g_buf)), steps, warmup)
         flops, state_bytes = vq.work_estimate(H, A, True)
         units, unit = 1, "evals/s"
-        workload = "30 qubits, 10 electrons, 512 UCCSD angles (9.0M sector amplitudes)"
-        launches = 2 * len(exc) + 6
+        workload = ("30 qubits, 10 electrons, 512 UCCSD angles (9.0M sector amplitudes)" if nq == 30 else
+                    "24 qubits, 10 electrons, 256 UCCSD angles (627k sector amplitudes)")
+        launches = 2 * len(exc) + 8  # trig, init, gates, 4 H psi launches + energy sum, gates, gradient sums
     else:
         insts = [synth.config2_instance(j) for j in range(256)]
         hams = [vq.Hamiltonian.from_problem(p) for p, _, _ in insts]
@@ -436,7 +445,7 @@ def main():
         if rank == 0:
             run_warmstart(args)
         return
-    if args.workload in ("config3", "config2"):
+    if args.workload in ("config3", "config2", "q24"):
         if rank == 0:
             run_large(args)
         return

@@ -70,14 +70,17 @@ int vqe_version(void);
  *                            a cluster of two;
  *   VQE_FLAG_FP64_SWEEPS     run the resident kernel's gate sweeps in FP64
  *                            instead of 64-bit fixed point (H psi, the energy
- *                            and every streaming kernel are FP64 either way).
+ *                            and every streaming kernel are FP64 either way);
+ *   VQE_FLAG_NO_STRINGS      streaming H psi by connectivity rows (or a scan of
+ *                            all groups) instead of alpha/beta strings.
  * Returns the previous flags. Not thread-safe against concurrent compute calls.
  */
 enum {
   VQE_FLAG_FORCE_COMPLEX = 1,
   VQE_FLAG_FORCE_STREAMING = 2,
   VQE_FLAG_NO_CLUSTER = 4,
-  VQE_FLAG_FP64_SWEEPS = 8
+  VQE_FLAG_FP64_SWEEPS = 8,
+  VQE_FLAG_NO_STRINGS = 16
 };
 int vqe_set_flags(int flags);
 

@@ -6,6 +6,7 @@ from .api import (Hamiltonian, Ansatz, Batch, VQEError, energy, energy_grad, sta
                   apply_hamiltonian, jordan_wigner, workspace_bytes, alloc_workspace,
                   work_estimate, set_flags, VQE_WS_ENERGY, VQE_WS_GRAD, VQE_WS_COMPLEX,
                   VQE_FLAG_FORCE_COMPLEX, VQE_FLAG_FORCE_STREAMING, VQE_FLAG_NO_CLUSTER, VQE_FLAG_FP64_SWEEPS,
+                  VQE_FLAG_NO_STRINGS,
                   probe_fp64,
                   GraphEnergyGrad, batched_workspace_bytes, energy_grad_batched)
 from .autograd import VQEEnergy, vqe_energy
@@ -14,7 +15,7 @@ __all__ = [
     "build", "load", "Hamiltonian", "Ansatz", "Batch", "VQEError", "energy", "energy_grad",
     "state", "apply_hamiltonian", "jordan_wigner", "workspace_bytes", "alloc_workspace",
     "work_estimate", "set_flags", "VQEEnergy", "vqe_energy", "VQE_WS_ENERGY", "VQE_WS_GRAD",
-    "VQE_WS_COMPLEX", "VQE_FLAG_FORCE_COMPLEX", "VQE_FLAG_FORCE_STREAMING", "VQE_FLAG_NO_CLUSTER", "VQE_FLAG_FP64_SWEEPS",
+    "VQE_WS_COMPLEX", "VQE_FLAG_FORCE_COMPLEX", "VQE_FLAG_FORCE_STREAMING", "VQE_FLAG_NO_CLUSTER", "VQE_FLAG_FP64_SWEEPS", "VQE_FLAG_NO_STRINGS",
     "probe_fp64",
     "GraphEnergyGrad", "batched_workspace_bytes", "energy_grad_batched",
 ]

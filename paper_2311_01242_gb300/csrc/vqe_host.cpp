@@ -257,6 +257,11 @@ struct vqe_hamiltonian_s {
     uint16_t* d_ell16 = nullptr;      // device-built 16-bit table (large sectors)
     int64_t nnz = 0;                  // connected (output, group) pairs
     double extra_adds = 0;            // sum over nnz of (entries - 1)
+    // spin sectors: alpha/beta string tables of the string-driven H psi
+    bool use_str = false;
+    vqe::StrPlan str{};
+    vqe::StrPlan* d_str = nullptr;     // device copy of str (batched kernels)
+    std::vector<void*> str_alloc;      // device arrays behind str
   };
   std::mutex mu;
   std::map<std::tuple<int, int, int>, Ell> ells;
@@ -271,6 +276,7 @@ struct vqe_hamiltonian_s {
     for (auto& kv : ells) {
       ell_release(kv.second.d_ell);
       ell16_release(kv.second.d_ell16);
+      for (void* p : kv.second.str_alloc) dfree(p);
     }
   }
 };
@@ -315,7 +321,12 @@ struct vqe_ansatz_s {
 struct StreamBatch {
   std::vector<int> slots;                 // batch index of each streamed slot
   std::vector<InstDesc> descs;
-  std::vector<int64_t> psi_off, lam_off, ebase, gbase;
+  std::vector<int64_t> psi_off, lam_off, am_off, ebase, gbase;
+  vqe::BatchSegs str_segs{};               // total 0: H psi by connectivity rows
+  size_t str_smem = 0;
+  int32_t* d_str_inst = nullptr;
+  int64_t* d_str_pref = nullptr;
+  int64_t* d_am_off = nullptr;
   int Mmax = 0;
   std::vector<vqe::BatchSegs> gate_segs;  // per gate index, device pointers inside
   vqe::BatchSegs out_segs{};
@@ -338,6 +349,9 @@ struct StreamBatch {
     dfree(d_gm_gate);
     dfree(d_seg_pref);
     dfree(d_out_pref);
+    dfree(d_str_inst);
+    dfree(d_str_pref);
+    dfree(d_am_off);
   }
 };
 
@@ -437,6 +451,171 @@ double fp64_adds(vqe_hamiltonian_t h, int g, uint32_t src) {
   return r.kind == 1 ? double(k) : double(k + k * (k - 1) / 2);
 }
 
+// String tables of a spin sector (the product of alpha strings on the even
+// qubits and beta strings on the odd qubits) for the string-driven H psi:
+//  - alpha and beta strings in increasing order, and the alpha-major order's
+//    map to the sector's sorted order (perm);
+//  - groups that can connect anything (even numbers of flipped alpha and beta
+//    bits) in buckets of equal alpha mask, each bucket sorted by beta mask;
+//  - for each output alpha string and bucket, the source alpha string (or -1);
+//  - for each beta mask, the (output, source) beta string pairs in output
+//    order, with the entry range of each warp's fixed share of outputs.
+int build_strings(vqe_hamiltonian_t h, vqe_ansatz_t a, vqe_hamiltonian_s::Ell* e) {
+  const int n = a->n, Na = a->n_alpha, Nb = a->n_elec - a->n_alpha;
+  const uint32_t all = uint32_t((uint64_t(1) << n) - 1);
+  const uint32_t even = all & 0x55555555u, odd = all & 0xAAAAAAAAu;
+  auto subsets = [](uint32_t pool, int c) {
+    std::vector<uint32_t> bits, out;
+    for (int q = 0; q < 32; ++q)
+      if ((pool >> q) & 1u) bits.push_back(q);
+    const int m = int(bits.size());
+    if (c < 0 || c > m) return out;
+    // every c-subset of the pool, as masks, in increasing order
+    std::vector<uint32_t> all_masks;
+    for (uint64_t v = 0; v < (uint64_t(1) << m); ++v) {
+      if (__builtin_popcountll(v) != c) continue;
+      uint32_t w = 0;
+      for (int j = 0; j < m; ++j)
+        if ((v >> j) & 1) w |= 1u << bits[j];
+      all_masks.push_back(w);
+    }
+    std::sort(all_masks.begin(), all_masks.end());
+    return all_masks;
+  };
+  const std::vector<uint32_t> ka = subsets(even, Na), kb = subsets(odd, Nb);
+  const int64_t Da = int64_t(ka.size()), Db = int64_t(kb.size());
+  // shared memory of a block: two rows of complex amplitudes and the beta strings
+  const size_t smem = size_t(Db) * (2 * 16 + 4);
+  if (Da * Db != int64_t(a->sector.size()) || Db < vqe::kStrMinDb || Db > 65535 || smem > size_t(200) * 1024)
+    return VQE_OK;  // not used
+  {
+    static std::mutex mu;
+    static size_t set_to = 0;
+    std::lock_guard<std::mutex> lk(mu);
+    if (smem > set_to) {
+      const cudaError_t ce = vqe::set_str_smem_limit(smem);
+      if (ce != cudaSuccess) return cuda_fail(ce, "string-driven H psi shared memory");
+      set_to = smem;
+    }
+  }
+  auto index_of = [](const std::vector<uint32_t>& v, uint32_t m) -> int32_t {
+    auto it = std::lower_bound(v.begin(), v.end(), m);
+    return (it != v.end() && *it == m) ? int32_t(it - v.begin()) : -1;
+  };
+  const uint32_t lo_mask = (1u << a->lo_bits) - 1u;
+  auto rank = [&](uint32_t k) { return a->rank_hi[k >> a->lo_bits] + a->rank_lo[k & lo_mask]; };
+  std::vector<uint32_t> perm(size_t(Da * Db));
+  parallel_for(Da, [&](int64_t lo, int64_t hi) {
+    for (int64_t i = lo; i < hi; ++i)
+      for (int64_t j = 0; j < Db; ++j) perm[size_t(i * Db + j)] = rank(ka[size_t(i)] | kb[size_t(j)]);
+  });
+  // buckets of groups by alpha mask, each sorted by beta mask then index
+  const int G = int(h->groups.size());
+  std::vector<int> keep;
+  for (int g = 0; g < G; ++g) {
+    const uint32_t x = h->groups[g].x;
+    if ((pc32(x & even) & 1) == 0 && (pc32(x & odd) & 1) == 0) keep.push_back(g);
+  }
+  std::stable_sort(keep.begin(), keep.end(), [&](int p, int q) {
+    const uint32_t xp = h->groups[p].x, xq = h->groups[q].x;
+    if ((xp & even) != (xq & even)) return (xp & even) < (xq & even);
+    return (xp & odd) < (xq & odd);
+  });
+  std::vector<uint32_t> bxa;
+  std::vector<int32_t> boff, bgrp, blist;
+  std::vector<uint32_t> lxb;  // beta mask of each list
+  for (size_t i = 0; i < keep.size(); ++i) {
+    const uint32_t x = h->groups[keep[i]].x;
+    if (bxa.empty() || bxa.back() != (x & even)) {
+      bxa.push_back(x & even);
+      boff.push_back(int32_t(i));
+    }
+    const uint32_t xb = x & odd;
+    auto it = std::lower_bound(lxb.begin(), lxb.end(), xb);
+    if (it == lxb.end() || *it != xb) lxb.insert(it, xb);
+    bgrp.push_back(keep[i]);
+  }
+  boff.push_back(int32_t(keep.size()));
+  for (size_t i = 0; i < keep.size(); ++i)
+    blist.push_back(int32_t(std::lower_bound(lxb.begin(), lxb.end(), h->groups[keep[i]].x & odd) - lxb.begin()));
+  const int NB = int(bxa.size()), NL = int(lxb.size());
+  // source alpha string per (output alpha string, bucket)
+  std::vector<int32_t> ja(size_t(Da) * size_t(std::max(NB, 1)), -1);
+  parallel_for(Da, [&](int64_t lo, int64_t hi) {
+    for (int64_t i = lo; i < hi; ++i)
+      for (int b = 0; b < NB; ++b) {
+        const uint32_t src = ka[size_t(i)] ^ bxa[size_t(b)];
+        if (pc32(src) == Na) ja[size_t(i) * NB + b] = index_of(ka, src);
+      }
+  });
+  // beta pair lists in output order, with each warp's share of outputs
+  const int SW = vqe::kStrWarps;
+  const int64_t share = (Db + SW - 1) / SW;
+  std::vector<std::vector<uint32_t>> lists(static_cast<size_t>(NL));
+  parallel_for(NL, [&](int64_t lo, int64_t hi) {
+    for (int64_t l = lo; l < hi; ++l)
+      for (int64_t j = 0; j < Db; ++j) {
+        const uint32_t src = kb[size_t(j)] ^ lxb[size_t(l)];
+        if (pc32(src) == Nb) lists[size_t(l)].push_back(uint32_t(j) | (uint32_t(index_of(kb, src)) << 16));
+      }
+  });
+  std::vector<uint32_t> flat;
+  std::vector<int32_t> split(static_cast<size_t>(NL) * (SW + 1));
+  for (int l = 0; l < NL; ++l) {
+    const int64_t base = int64_t(flat.size());
+    const auto& L = lists[size_t(l)];
+    for (int w = 0; w <= SW; ++w) {
+      const uint32_t first = uint32_t(std::min<int64_t>(Db, int64_t(w) * share));
+      const int64_t pos = std::lower_bound(L.begin(), L.end(), first,
+                                           [](uint32_t ent, uint32_t v) { return (ent & 0xFFFFu) < v; }) -
+                          L.begin();
+      split[size_t(l) * (SW + 1) + w] = int32_t(base + pos);
+    }
+    flat.insert(flat.end(), L.begin(), L.end());
+  }
+  if (flat.size() >= (size_t(1) << 31)) return VQE_OK;
+  if (flat.empty()) flat.push_back(0);
+  // each bucket entry's list range per warp
+  std::vector<int32_t> bsplit(blist.size() * (SW + 1));
+  for (size_t i = 0; i < blist.size(); ++i)
+    for (int w = 0; w <= SW; ++w) bsplit[i * (SW + 1) + w] = split[size_t(blist[i]) * (SW + 1) + w];
+  if (bgrp.empty()) {
+    bgrp.push_back(0);
+    bsplit.assign(SW + 1, 0);
+  }
+  vqe::StrPlan& P = e->str;
+  P.Da = int32_t(Da);
+  P.Db = int32_t(Db);
+  P.NB = NB;
+  int rc;
+  auto up = [&](auto& vec, auto** dst) -> int {
+    int r = upload(vec, dst);
+    if (r == VQE_OK) e->str_alloc.push_back(static_cast<void*>(*dst));
+    return r;
+  };
+  uint32_t *d_ka, *d_kb, *d_lists, *d_perm;
+  int32_t *d_ja, *d_boff, *d_bgrp, *d_bsplit;
+  std::vector<uint32_t> ka_v(ka), kb_v(kb);
+  if ((rc = up(ka_v, &d_ka)) || (rc = up(kb_v, &d_kb)) || (rc = up(ja, &d_ja)) || (rc = up(boff, &d_boff)) ||
+      (rc = up(bgrp, &d_bgrp)) || (rc = up(bsplit, &d_bsplit)) || (rc = up(flat, &d_lists)) ||
+      (rc = up(perm, &d_perm)))
+    return rc;
+  P.ka = d_ka;
+  P.kb = d_kb;
+  P.ja = d_ja;
+  P.boff = d_boff;
+  P.bgrp = d_bgrp;
+  P.bsplit = d_bsplit;
+  P.lists = d_lists;
+  P.perm = d_perm;
+  std::vector<vqe::StrPlan> one(1, P);
+  vqe::StrPlan* d_plan = nullptr;
+  if ((rc = up(one, &d_plan))) return rc;
+  e->d_str = d_plan;
+  e->use_str = true;
+  return VQE_OK;
+}
+
 const vqe_hamiltonian_s::Ell* get_ell(vqe_hamiltonian_t h, vqe_ansatz_t a, int* err) {
   *err = VQE_OK;
   std::lock_guard<std::mutex> lock(h->mu);
@@ -461,7 +640,16 @@ const vqe_hamiltonian_s::Ell* get_ell(vqe_hamiltonian_t h, vqe_ansatz_t a, int* 
   // row lengths
   std::vector<int32_t> len(D, 0);
   const double cost = double(D) * double(G);
-  if (cost > 2.0e7 && G > 0 && G < 65535) {
+  if (na >= 0 && G > 0) {
+    const int rc = build_strings(h, a, &e);
+    if (rc != VQE_OK) {
+      *err = rc;
+      return nullptr;
+    }
+  }
+  if (cost > 2.0e7 && G > 0 && G < 65535 && e.use_str) {
+    // large spin sector: H psi runs string-driven; no connectivity table
+  } else if (cost > 2.0e7 && G > 0 && G < 65535) {
     const int rc = build_ell_device(h, a, order, &e);
     if (rc != VQE_OK) {
       *err = rc;
@@ -551,6 +739,7 @@ InstDesc make_desc(vqe_hamiltonian_t h, vqe_ansatz_t a, const vqe_hamiltonian_s:
   d.rank_lo = a->d_rank_lo;
   d.lo_bits = a->lo_bits;
   d.hf_rank = int32_t(a->rank_hi[a->hf >> a->lo_bits] + a->rank_lo[a->hf & ((1u << a->lo_bits) - 1u)]);
+  d.str = e->use_str ? e->d_str : nullptr;
   d.gates = a->d_gates;
   d.pair_off = a->d_pair_off;
   d.pairs = a->d_pairs;
@@ -601,7 +790,7 @@ bool resident_fit(vqe_ansatz_t a, const vqe_hamiltonian_s::Ell* e, bool real, In
 }
 
 struct WsLayout {
-  size_t psi, lam, cs, epart, gpart, total;
+  size_t psi, lam, psi_am, lam_am, cs, epart, gpart, total;
 };
 
 WsLayout ws_layout(vqe_ansatz_t a, bool complex_amp, bool with_grad) {
@@ -610,7 +799,9 @@ WsLayout ws_layout(vqe_ansatz_t a, bool complex_amp, bool with_grad) {
   const size_t vec = align256(std::max<size_t>(a->sector.size(), 1) * amp);  // compressed to the sector
   L.psi = 0;
   L.lam = vec;
-  L.cs = 2 * vec;
+  L.psi_am = 2 * vec;  // alpha-major copies for the string-driven H psi
+  L.lam_am = 3 * vec;
+  L.cs = 4 * vec;
   L.epart = L.cs + align256(size_t(std::max(a->M, 1)) * 16);
   L.gpart = L.epart + align256(size_t(vqe::kMaxPartials) * 8);
   L.total = L.gpart + (with_grad ? align256(size_t(std::max(a->M, 1)) * vqe::kMaxPartials * 8) : 0);
@@ -622,6 +813,8 @@ vqe::StreamBuffers buffers(void* ws, const WsLayout& L) {
   vqe::StreamBuffers s;
   s.psi = b + L.psi;
   s.lam = b + L.lam;
+  s.psi_am = b + L.psi_am;
+  s.lam_am = b + L.lam_am;
   s.cs = reinterpret_cast<double2*>(b + L.cs);
   s.epart = reinterpret_cast<double*>(b + L.epart);
   s.gpart = reinterpret_cast<double*>(b + L.gpart);
@@ -635,6 +828,8 @@ vqe::StreamPlan plan(vqe_ansatz_t a, const vqe_hamiltonian_s::Ell* e) {
   p.n_elec = a->n_elec;
   p.n_alpha = a->n_alpha;
   p.use_ell = e->use_ell;
+  p.use_str = e->use_str && !(g_flags & VQE_FLAG_NO_STRINGS);
+  p.str = e->str;
   return p;
 }
 
@@ -1317,7 +1512,8 @@ static int build_stream_batch(vqe_batch_s* B) {
     const size_t vec = align256(std::max<size_t>(a->sector.size(), 1) * 8);
     sb.psi_off.push_back(int64_t(off));
     sb.lam_off.push_back(int64_t(off + vec));
-    off += 2 * vec;
+    sb.am_off.push_back(int64_t(off + 2 * vec));  // alpha-major psi, then lambda (D entries on)
+    off += 2 * vec + align256(2 * std::max<size_t>(a->sector.size(), 1) * 8);
     sb.ebase.push_back(eb);
     eb += int64_t(a->sector.size());
     sb.gbase.push_back(gb);
@@ -1395,6 +1591,31 @@ static int build_stream_batch(vqe_batch_s* B) {
   sb.out_segs.pref = sb.d_out_pref;
   sb.out_segs.nseg = n;
   sb.out_segs.total = out_pref[n];
+  if ((rc = upload(sb.am_off, &sb.d_am_off))) return rc;
+  // string-driven H psi when every streamed instance has a string plan
+  bool all_str = true;
+  std::vector<int32_t> str_inst(n);
+  std::vector<int64_t> str_pref(n + 1, 0);
+  for (int s = 0; s < n; ++s) {
+    int rc2 = VQE_OK;
+    const auto* e = get_ell(B->hams[sb.slots[s]], B->ans[sb.slots[s]], &rc2);
+    if (!e) return rc2;
+    if (!e->use_str) {
+      all_str = false;
+      break;
+    }
+    str_inst[s] = s;
+    str_pref[s + 1] = str_pref[s] + e->str.Da;
+    sb.str_smem = std::max(sb.str_smem, size_t(e->str.Db) * (2 * 8 + 4));
+  }
+  if (all_str) {
+    if ((rc = upload(str_inst, &sb.d_str_inst))) return rc;
+    if ((rc = upload(str_pref, &sb.d_str_pref))) return rc;
+    sb.str_segs.inst = sb.d_str_inst;
+    sb.str_segs.pref = sb.d_str_pref;
+    sb.str_segs.nseg = n;
+    sb.str_segs.total = str_pref[n];
+  }
   return VQE_OK;
 }
 
@@ -1480,9 +1701,13 @@ static int batch_run(vqe_batch_t b, const double* theta, int64_t ld_theta, doubl
     bd.cs = reinterpret_cast<double2*>(static_cast<char*>(ws) + sb.cs_off);
     bd.ebuf = reinterpret_cast<double*>(static_cast<char*>(ws) + sb.ebuf_off);
     bd.gbuf = reinterpret_cast<double*>(static_cast<char*>(ws) + sb.gbuf_off);
+    bd.am_off = sb.d_am_off;
     bd.n = int(sb.slots.size());
     bd.Mmax = sb.Mmax;
-    cudaError_t ce = vqe::batch_stream_run(bd, sb.gate_segs.data(), sb.out_segs, sb.d_gm_inst, sb.d_gm_gate, sb.n_gm,
+    vqe::BatchSegs str_segs = sb.str_segs;
+    if (g_flags & VQE_FLAG_NO_STRINGS) str_segs.total = 0;
+    cudaError_t ce = vqe::batch_stream_run(bd, sb.gate_segs.data(), sb.out_segs, str_segs, sb.str_smem,
+                                           sb.d_gm_inst, sb.d_gm_gate, sb.n_gm,
                                            theta, ld_theta, energies, with_grad ? grads : nullptr, ld_grad,
                                            sb.threads, stream);
     if (ce != cudaSuccess) return cuda_fail(ce, "batched streaming launch");

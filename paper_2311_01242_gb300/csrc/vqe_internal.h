@@ -47,6 +47,28 @@ struct GateRec {
   int32_t pad;
 };
 
+// String-driven H psi of a spin sector: the sector is the product of alpha
+// strings (even qubits) and beta strings (odd qubits), and psi is read as a
+// Da x Db matrix in alpha-major order. Groups are bucketed by their alpha mask;
+// a bucket maps output alpha string Ia to source alpha string ja[Ia * NB + b]
+// (-1: none). Each group's beta mask selects a list of (output, source) beta
+// string pairs (Ib | Jb << 16, increasing Ib); bsplit gives, per bucket entry,
+// the entry range of its list for each of the kStrWarps warps (a fixed share of
+// the Ib range each).
+constexpr int kStrWarps = 8;
+constexpr int kStrMinDb = 512;  // smaller beta string sets keep the connectivity rows
+struct StrPlan {
+  int32_t Da, Db, NB, pad;
+  const uint32_t* ka;      // [Da] alpha strings as qubit masks, increasing
+  const uint32_t* kb;      // [Db] beta strings as qubit masks, increasing
+  const int32_t* ja;       // [Da * NB]
+  const int32_t* boff;     // [NB + 1] entry range of each bucket in bgrp
+  const int32_t* bgrp;     // group index, bucket by bucket, by beta mask
+  const int32_t* bsplit;   // [entries * (kStrWarps + 1)] absolute list offsets
+  const uint32_t* lists;   // concatenated beta lists
+  const uint32_t* perm;    // [Da * Db] alpha-major index -> position in the sorted sector
+};
+
 struct InstDesc {
   // ansatz
   int32_t n, M;
@@ -63,6 +85,7 @@ struct InstDesc {
   const uint32_t* rank_hi;
   const uint32_t* rank_lo;
   int32_t lo_bits, hf_rank;  // hf_rank = rank(hf)
+  const StrPlan* str;        // device copy of the string plan, or null
   // Hamiltonian
   int32_t G, W;              // groups, connectivity slots per output
   const GroupRec* groups;    // [G]
@@ -100,13 +123,18 @@ struct BatchDev {
   double2* cs;             // [n * Mmax] cos/sin
   double* ebuf;            // [sum D] per-output psi*lambda
   double* gbuf;            // [sum P] per-pair gradient contributions
+  const int64_t* am_off;   // [n] byte offsets of alpha-major psi, then lambda (string-driven H psi)
   int32_t n, Mmax;
 };
 
+// str_segs.total > 0: every instance has a string plan and H psi runs
+// string-driven (one block per (instance, output alpha string); str_smem bytes).
 cudaError_t batch_stream_run(const BatchDev& b, const BatchSegs* gate_segs, const BatchSegs& out_segs,
+                             const BatchSegs& str_segs, size_t str_smem,
                              const int32_t* d_gm_inst, const int32_t* d_gm_gate, int64_t n_gm,
                              const double* theta, int64_t ld_theta, double* energy, double* grad,
                              int64_t ld_grad, int threads, cudaStream_t stream);
+cudaError_t set_str_smem_limit(size_t smem);
 
 // Shared-memory layout of the resident kernel (byte offsets), computed the same
 // way on the host (to size the launch) and on the device (to carve it). The
@@ -161,8 +189,10 @@ cudaError_t launch_resident(const InstDesc* d_descs, const InstDesc* one, int n_
 cudaError_t set_resident_smem_limit(size_t smem, bool real);
 
 struct StreamBuffers {
-  void* psi;      // 2^n amplitudes (double or double2)
-  void* lam;      // 2^n amplitudes
+  void* psi = nullptr;     // D amplitudes (double or double2), sector order
+  void* lam = nullptr;     // D amplitudes
+  void* psi_am = nullptr;  // D amplitudes, alpha-major (string-driven H psi)
+  void* lam_am = nullptr;  // D amplitudes, alpha-major
   double2* cs;    // [M] (cos, sin)
   double* epart;  // [kMaxPartials]
   double* gpart;  // [M * kMaxPartials]
@@ -174,6 +204,8 @@ struct StreamPlan {
   const int32_t* d_nb_rows;      // device [M+1]: blocks of each gate's adjoint launch, then of H psi
   int n_elec, n_alpha;           // sector test (n_alpha < 0: number sector only)
   bool use_ell;
+  bool use_str;                  // string-driven H psi with `str`
+  StrPlan str;
 };
 
 // Blocks of a streaming launch over `work` items (also the partial count).

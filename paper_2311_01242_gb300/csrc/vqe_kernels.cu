@@ -904,6 +904,112 @@ k_gate_adj(const uint2* __restrict__ rp, int64_t P, const double2* __restrict__ 
   if (threadIdx.x == 0) gpart[blockIdx.x] = s;
 }
 
+// String-driven H psi row (spin sectors; see StrPlan): lambda[Ia, :] for one
+// output alpha string. For each bucket with a source alpha string Ja, the
+// source row psi[Ja, :] is staged in shared memory; then, group by group in the
+// bucket's fixed order, every warp walks its share of the group's beta pair
+// list and adds f_g(src) psi[Ja, Jb] to lambda[Ia, Ib]. A warp owns a fixed range
+// of Ib, so each output is summed by one lane in bucket and group order.
+// Needs blockDim.x == 32 * kStrWarps and 2 * Db amplitudes + Db words of shared
+// memory at smem.
+template <bool REAL>
+__device__ __forceinline__ void hpsi_str_row(const StrPlan& sp, int ia, const GroupRec* __restrict__ groups,
+                                             const uint32_t* __restrict__ emask,
+                                             const typename Amp<REAL>::C* __restrict__ vals,
+                                             const typename Amp<REAL>::T* __restrict__ psi_am,
+                                             typename Amp<REAL>::T* __restrict__ lam_am, unsigned char* smem) {
+  typedef Amp<REAL> A;
+  typedef typename A::T T;
+  const int tid = threadIdx.x, bs = blockDim.x, w = tid >> 5, lane = tid & 31;
+  const int Db = sp.Db, NB = sp.NB;
+  T* psi_s = reinterpret_cast<T*>(smem);
+  T* lam_s = psi_s + Db;
+  uint32_t* kb_s = reinterpret_cast<uint32_t*>(lam_s + Db);
+  for (int j = tid; j < Db; j += bs) {
+    lam_s[j] = A::zero();
+    kb_s[j] = __ldg(sp.kb + j);
+  }
+  for (int b = 0; b < NB; ++b) {
+    const int ja = __ldg(sp.ja + int64_t(ia) * NB + b);
+    if (ja < 0) continue;  // same for the whole block
+    __syncthreads();       // the previous source row is no longer read
+    const T* row = psi_am + int64_t(ja) * Db;
+    for (int j = tid; j < Db; j += bs) psi_s[j] = row[j];
+    __syncthreads();
+    const uint32_t ka = __ldg(sp.ka + ja);
+    const int g0 = __ldg(sp.boff + b), g1 = __ldg(sp.boff + b + 1);
+    // the next group's record and list range are loaded while the current group runs
+    if (g0 >= g1) continue;  // (buckets are never empty)
+    GroupRec g = load_group(groups + __ldg(sp.bgrp + g0));
+    int e0 = __ldg(sp.bsplit + int64_t(g0) * (kStrWarps + 1) + w);
+    int e1 = __ldg(sp.bsplit + int64_t(g0) * (kStrWarps + 1) + w + 1);
+    for (int gi = g0; gi < g1; ++gi) {
+      GroupRec gn = g;
+      int e0n = 0, e1n = 0;
+      if (gi + 1 < g1) {
+        gn = load_group(groups + __ldg(sp.bgrp + gi + 1));
+        e0n = __ldg(sp.bsplit + int64_t(gi + 1) * (kStrWarps + 1) + w);
+        e1n = __ldg(sp.bsplit + int64_t(gi + 1) * (kStrWarps + 1) + w + 1);
+      }
+      // four list entries per lane in flight, then their updates in entry order
+      for (int e = e0 + lane; e < e1; e += 4 * 32) {
+        uint32_t ent[4];
+#pragma unroll
+        for (int u = 0; u < 4; ++u) ent[u] = (e + 32 * u < e1) ? __ldg(sp.lists + e + 32 * u) : 0xFFFFFFFFu;
+#pragma unroll
+        for (int u = 0; u < 4; ++u) {
+          if (ent[u] == 0xFFFFFFFFu) break;
+          const uint32_t ib = ent[u] & 0xFFFFu, jb = ent[u] >> 16;
+          A::mac(lam_s[ib], group_coef<REAL>(g, emask, vals, ka | kb_s[jb]), psi_s[jb]);
+        }
+      }
+      __syncwarp();
+      g = gn;
+      e0 = e0n;
+      e1 = e1n;
+    }
+  }
+  __syncthreads();
+  T* out = lam_am + int64_t(ia) * Db;
+  for (int j = tid; j < Db; j += bs) out[j] = lam_s[j];
+}
+
+template <bool REAL>
+__global__ void __launch_bounds__(kStrWarps * 32, 2)
+k_hpsi_str(const StrPlan sp, const GroupRec* __restrict__ groups, const uint32_t* __restrict__ emask,
+           const typename Amp<REAL>::C* __restrict__ vals, const typename Amp<REAL>::T* __restrict__ psi_am,
+           typename Amp<REAL>::T* __restrict__ lam_am) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  hpsi_str_row<REAL>(sp, int(blockIdx.x), groups, emask, vals, psi_am, lam_am, smem);
+}
+
+// dst[i] = src[perm[i]] (sector order -> alpha-major) and the reverse scatter
+template <bool REAL>
+__global__ void k_perm_gather(const uint32_t* __restrict__ perm, int64_t D,
+                              const typename Amp<REAL>::T* __restrict__ src, typename Amp<REAL>::T* __restrict__ dst) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < D; i += int64_t(gridDim.x) * blockDim.x)
+    dst[i] = src[__ldg(perm + i)];
+}
+template <bool REAL>
+__global__ void k_perm_scatter(const uint32_t* __restrict__ perm, int64_t D,
+                               const typename Amp<REAL>::T* __restrict__ src, typename Amp<REAL>::T* __restrict__ dst) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < D; i += int64_t(gridDim.x) * blockDim.x)
+    dst[__ldg(perm + i)] = src[i];
+}
+
+// Per-block partials of Re <a|b> over D entries (fixed assignment and order).
+template <bool REAL>
+__global__ void __launch_bounds__(kStreamThreads) k_dot(const typename Amp<REAL>::T* __restrict__ a,
+                                                        const typename Amp<REAL>::T* __restrict__ b, int64_t D,
+                                                        double* __restrict__ part) {
+  __shared__ double red[32];
+  double acc = 0.0;
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < D; i += int64_t(gridDim.x) * blockDim.x)
+    acc += Amp<REAL>::redot(a[i], b[i]);
+  const double s = block_sum(acc, red);
+  if (threadIdx.x == 0) part[blockIdx.x] = s;
+}
+
 // Sums nb[i] partials of row i (row i at part + i*kMaxPartials) in a fixed
 // order: lane-strided sequential sums, then a fixed shuffle tree.
 __global__ void k_finalize(const double* __restrict__ part, const int32_t* __restrict__ nb_rows,
@@ -1032,6 +1138,49 @@ __global__ void __launch_bounds__(512, 1) kb_hpsi(BatchDev b, BatchSegs sg) {
   }
 }
 
+// String-driven H psi over the batch: block -> (instance slot, output alpha string)
+__global__ void __launch_bounds__(kStrWarps * 32, 2) kb_hpsi_str(BatchDev b, BatchSegs sg) {
+  extern __shared__ __align__(16) unsigned char smem[];
+  const int s = find_seg(sg.pref, sg.nseg, int64_t(blockIdx.x));
+  const int i = __ldg(sg.inst + s);
+  const int ia = int(int64_t(blockIdx.x) - __ldg(sg.pref + s));
+  const InstDesc* d = b.desc + i;
+  const StrPlan sp = *d->str;
+  const double* psi_am = reinterpret_cast<const double*>(b.ws + b.am_off[i]);
+  double* lam_am = reinterpret_cast<double*>(b.ws + b.am_off[i]) + d->D;
+  hpsi_str_row<true>(sp, ia, d->groups, d->emask, d->vals, psi_am, lam_am, smem);
+}
+
+// alpha-major copy of every instance's psi
+__global__ void kb_perm_gather(BatchDev b, BatchSegs sg) {
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < sg.total; t += int64_t(gridDim.x) * blockDim.x) {
+    const int s = find_seg(sg.pref, sg.nseg, t);
+    const int i = __ldg(sg.inst + s);
+    const int64_t r = t - __ldg(sg.pref + s);
+    const InstDesc* d = b.desc + i;
+    const double* psi = reinterpret_cast<const double*>(b.ws + b.psi_off[i]);
+    double* psi_am = reinterpret_cast<double*>(b.ws + b.am_off[i]);
+    psi_am[r] = psi[__ldg(d->str->perm + r)];
+  }
+}
+
+// lambda back to sector order, and the per-output energy terms psi_r lambda_r
+__global__ void kb_perm_scatter(BatchDev b, BatchSegs sg) {
+  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < sg.total; t += int64_t(gridDim.x) * blockDim.x) {
+    const int s = find_seg(sg.pref, sg.nseg, t);
+    const int i = __ldg(sg.inst + s);
+    const int64_t r = t - __ldg(sg.pref + s);
+    const InstDesc* d = b.desc + i;
+    const double* psi = reinterpret_cast<const double*>(b.ws + b.psi_off[i]);
+    double* lam = reinterpret_cast<double*>(b.ws + b.lam_off[i]);
+    const double* lam_am = reinterpret_cast<const double*>(b.ws + b.am_off[i]) + d->D;
+    const uint32_t k = __ldg(d->str->perm + r);
+    const double v = lam_am[r];
+    lam[k] = v;
+    b.ebuf[b.ebase[i] + k] = psi[k] * v;
+  }
+}
+
 // E of instance slot blockIdx.x: fixed-order sum of its per-output terms
 __global__ void kb_energy(BatchDev b, double* __restrict__ energy) {
   __shared__ double red[32];
@@ -1120,6 +1269,15 @@ __global__ void k_ell_fill(const uint32_t* __restrict__ sector, int64_t D, const
 }
 
 // ---------------------------------------------------------------- launchers
+cudaError_t set_str_smem_limit(size_t smem) {
+  const int b = int(smem);
+  const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
+  cudaError_t e = cudaFuncSetAttribute(k_hpsi_str<true>, a, b);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_hpsi_str<false>, a, b);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_hpsi_str, a, b);
+  return e;
+}
+
 cudaError_t set_resident_smem_limit(size_t smem, bool real) {
   const int b = int(smem);
   const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
@@ -1190,10 +1348,22 @@ cudaError_t stream_hpsi(const InstDesc& d, const StreamPlan& sp, const StreamBuf
   const T* psi = static_cast<const T*>(b.psi);
   T* lam = static_cast<T*>(b.lam);
   const int grid = stream_grid(d.D);
-  if (sp.use_ell)
+  if (sp.use_str) {
+    typedef typename Amp<REAL>::C C;
+    const C* tv;
+    if constexpr (REAL) tv = d.vals; else tv = d.cvals;
+    T* psi_am = static_cast<T*>(b.psi_am);
+    T* lam_am = static_cast<T*>(b.lam_am);
+    const size_t smem = size_t(sp.str.Db) * (2 * sizeof(T) + 4);
+    k_perm_gather<REAL><<<grid, kStreamThreads, 0, stream>>>(sp.str.perm, d.D, psi, psi_am);
+    k_hpsi_str<REAL><<<sp.str.Da, kStrWarps * 32, smem, stream>>>(sp.str, d.groups, d.emask, tv, psi_am, lam_am);
+    k_perm_scatter<REAL><<<grid, kStreamThreads, 0, stream>>>(sp.str.perm, d.D, lam_am, lam);
+    k_dot<REAL><<<grid, kStreamThreads, 0, stream>>>(psi, lam, d.D, b.epart);
+  } else if (sp.use_ell) {
     k_hpsi<REAL, true><<<grid, kStreamThreads, 0, stream>>>(d, sp.n_elec, sp.n_alpha, psi, lam, b.epart);
-  else
+  } else {
     k_hpsi<REAL, false><<<grid, kStreamThreads, 0, stream>>>(d, sp.n_elec, sp.n_alpha, psi, lam, b.epart);
+  }
   k_finalize<<<1, 32, 0, stream>>>(b.epart, sp.d_nb_rows + d.M, 1, 1.0, energy);
   return cudaGetLastError();
 }
@@ -1257,6 +1427,7 @@ cudaError_t stream_apply_h(const InstDesc& d, const StreamPlan& sp, const Stream
 }
 
 cudaError_t batch_stream_run(const BatchDev& b, const BatchSegs* gate_segs, const BatchSegs& out_segs,
+                             const BatchSegs& str_segs, size_t str_smem,
                              const int32_t* d_gm_inst, const int32_t* d_gm_gate, int64_t n_gm,
                              const double* theta, int64_t ld_theta, double* energy, double* grad,
                              int64_t ld_grad, int threads, cudaStream_t stream) {
@@ -1267,7 +1438,13 @@ cudaError_t batch_stream_run(const BatchDev& b, const BatchSegs* gate_segs, cons
   for (int m = 0; m < b.Mmax; ++m)
     if (gate_segs[m].total > 0)
       kb_gate_fwd<<<batch_grid(gate_segs[m].total, nt), nt, 0, stream>>>(m, b, gate_segs[m]);
-  kb_hpsi<<<batch_grid(out_segs.total, nt), nt, 0, stream>>>(b, out_segs);
+  if (str_segs.total > 0) {
+    kb_perm_gather<<<batch_grid(out_segs.total, nt), nt, 0, stream>>>(b, out_segs);
+    kb_hpsi_str<<<unsigned(str_segs.total), kStrWarps * 32, str_smem, stream>>>(b, str_segs);
+    kb_perm_scatter<<<batch_grid(out_segs.total, nt), nt, 0, stream>>>(b, out_segs);
+  } else {
+    kb_hpsi<<<batch_grid(out_segs.total, nt), nt, 0, stream>>>(b, out_segs);
+  }
   kb_energy<<<b.n, 256, 0, stream>>>(b, energy);
   if (grad) {
     for (int m = b.Mmax - 1; m >= 0; --m)

@@ -386,3 +386,53 @@ def test_fixed_point_sweeps_match_fp64_sweeps():
                                       w.excitations[0], w.thetas[5], idx)
     assert abs(float(e_fix[5]) - e_o) <= 1e-10
     assert np.abs(g_fix[5, idx].cpu().numpy() - g_o).max() <= 1e-9
+
+
+def _instance_24q(seed):
+    """24 qubits, 10 electrons (792 beta strings: the string-driven H psi),
+    64 excitations of a seeded shuffle of the spin-conserving pool."""
+    rng = np.random.default_rng([24, seed])
+    p = synth.integrals.random_problem(rng, 12, 10, 6, label=f"24q[{seed}]")
+    pool = synth.uccsd_pool(24, 10)
+    exc = pool[rng.permutation(len(pool))[:64]]
+    return p, exc, rng.normal(0.0, 0.05, size=64)
+
+
+def test_string_driven_hpsi_matches_group_scan():
+    """The alpha/beta string-driven H psi and the scan over all groups sum the
+    same terms in different orders: energies within 1e-12, gradients within
+    1e-11, single calls and a batch of two alike; H psi itself (complex, via
+    vqe_apply_hamiltonian) within 1e-12 per entry."""
+    insts = [_instance_24q(s) for s in (0, 1)]
+    hams = [vq.Hamiltonian.from_problem(p) for p, _, _ in insts]
+    ans = [vq.Ansatz(24, synth.hf_bitstring(10), e) for _, e, _ in insts]
+    B = vq.Batch(hams, ans)
+    theta = torch.as_tensor(np.stack([t for _, _, t in insts])).cuda().contiguous()
+    e_s, g_s = [t.clone() for t in B.energy_grad(theta)]
+    singles = [vq.energy_grad(h, a, theta[i]) for i, (h, a) in enumerate(zip(hams, ans))]
+    psi = vq.state(ans[1], hams[1], theta[1])
+    lam_s, _ = vq.apply_hamiltonian(hams[1], ans[1], psi)
+    old = vq.set_flags(vq.VQE_FLAG_NO_STRINGS)
+    try:
+        e_r, g_r = [t.clone() for t in B.energy_grad(theta)]
+        singles_r = [vq.energy_grad(h, a, theta[i]) for i, (h, a) in enumerate(zip(hams, ans))]
+        lam_r, _ = vq.apply_hamiltonian(hams[1], ans[1], psi)
+    finally:
+        vq.set_flags(old)
+    assert float((e_s - e_r).abs().max()) <= 1e-12
+    assert float((g_s - g_r).abs().max()) <= 1e-11
+    for i in range(2):
+        assert abs(float(singles[i][0]) - float(singles_r[i][0])) <= 1e-12
+        assert float((singles[i][1] - singles_r[i][1]).abs().max()) <= 1e-11
+        assert abs(float(singles[i][0]) - float(e_s[i])) <= 1e-12
+    assert float((lam_s - lam_r).abs().max()) <= 1e-12
+    # and the HF energy (theta = 0) equals the Slater-Condon closed form
+    p = insts[0][0]
+    occ = range(10)
+    e_hf = sum(p.h[P // 2, P // 2] for P in occ)
+    for P in occ:
+        for Q in occ:
+            e_hf += 0.5 * p.eri[P // 2, P // 2, Q // 2, Q // 2]
+            if P % 2 == Q % 2:
+                e_hf -= 0.5 * p.eri[P // 2, Q // 2, Q // 2, P // 2]
+    assert abs(float(vq.energy(hams[0], ans[0], np.zeros(64))) - e_hf) <= 1e-10
