@@ -1,6 +1,8 @@
 // Small device helpers outside the state-vector path:
 //   - refolding the Hamiltonian's group tables from new term coefficients
 //     (same Pauli structure, new geometry r along a scan, Sec. 2.1.1);
+//   - the sum of |table value| over all slots, which bounds every row sum of
+//     |H| (the fixed-point H psi scales its tables by it);
 //   - packing per-instance angle vectors given as an array of device pointers
 //     into one row-major matrix, and unpacking gradients the same way.
 //
@@ -52,7 +54,26 @@ __global__ void k_unpack_rows(RowPtrs rp, const double* __restrict__ src, int64_
     dst[k] = row[k];
 }
 
+// sum of |v| over n values, one block of 256 threads, fixed order
+__global__ void k_abs_sum(const double* __restrict__ v, int64_t n, double* __restrict__ out) {
+  __shared__ double red[256];
+  double s = 0.0;
+  for (int64_t i = threadIdx.x; i < n; i += 256) s += fabs(v[i]);
+  red[threadIdx.x] = s;
+  __syncthreads();
+  for (int w = 128; w > 0; w >>= 1) {
+    if (int(threadIdx.x) < w) red[threadIdx.x] += red[threadIdx.x + w];
+    __syncthreads();
+  }
+  if (threadIdx.x == 0) *out = red[0];
+}
+
 }  // namespace
+
+cudaError_t abs_sum(const double* v, int64_t n, double* out, cudaStream_t stream) {
+  k_abs_sum<<<1, 256, 0, stream>>>(v, n, out);
+  return cudaGetLastError();
+}
 
 cudaError_t fold_coefs(int64_t n_slots, const int64_t* off, const int32_t* term, const float* w,
                        const double* coefs, double* vals, double2* cvals, cudaStream_t stream) {

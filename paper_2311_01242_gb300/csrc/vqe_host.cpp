@@ -246,6 +246,7 @@ struct vqe_hamiltonian_s {
   int64_t* d_lin_off = nullptr;
   int32_t* d_lin_term = nullptr;
   float* d_lin_w = nullptr;
+  double* d_bound = nullptr;  // sum of |vals| over all slots (device)
   GroupRec* d_groups = nullptr;
   uint32_t* d_emask = nullptr;
   double* d_vals = nullptr;
@@ -273,6 +274,7 @@ struct vqe_hamiltonian_s {
     dfree(d_lin_off);
     dfree(d_lin_term);
     dfree(d_lin_w);
+    dfree(d_bound);
     for (auto& kv : ells) {
       ell_release(kv.second.d_ell);
       ell16_release(kv.second.d_ell16);
@@ -740,6 +742,7 @@ InstDesc make_desc(vqe_hamiltonian_t h, vqe_ansatz_t a, const vqe_hamiltonian_s:
   d.lo_bits = a->lo_bits;
   d.hf_rank = int32_t(a->rank_hi[a->hf >> a->lo_bits] + a->rank_lo[a->hf & ((1u << a->lo_bits) - 1u)]);
   d.str = e->use_str ? e->d_str : nullptr;
+  d.hbound = h->d_bound;
   d.gates = a->d_gates;
   d.pair_off = a->d_pair_off;
   d.pairs = a->d_pairs;
@@ -1189,6 +1192,13 @@ int vqe_create_hamiltonian(int n_qubits, int64_t n_terms, const uint64_t* xs, co
     if ((rc = upload(H->lin_term, &H->d_lin_term))) return rc;
     if ((rc = upload(H->lin_w, &H->d_lin_w))) return rc;
   }
+  {
+    std::vector<double> zero(1, 0.0);
+    if ((rc = upload(zero, &H->d_bound))) return rc;
+    cudaError_t ce = vqe::abs_sum(H->d_vals, int64_t(vals.size()), H->d_bound, 0);
+    if (ce == cudaSuccess) ce = cudaStreamSynchronize(0);
+    if (ce != cudaSuccess) return cuda_fail(ce, "table bound");
+  }
   H->serial = next_serial();
   *out = H.release();
   return VQE_OK;
@@ -1223,6 +1233,7 @@ int vqe_set_coefs(vqe_hamiltonian_t h, const double* coefs_dev, vqe_stream_t str
   if (n_slots <= 0 || h->lin_term.empty()) return VQE_OK;  // every term was dropped: H = 0
   cudaError_t ce = vqe::fold_coefs(n_slots, h->d_lin_off, h->d_lin_term, h->d_lin_w, coefs_dev, h->d_vals,
                                    h->d_cvals, static_cast<cudaStream_t>(stream));
+  if (ce == cudaSuccess) ce = vqe::abs_sum(h->d_vals, n_slots, h->d_bound, static_cast<cudaStream_t>(stream));
   if (ce != cudaSuccess) return cuda_fail(ce, "coefficient refold");
   return VQE_OK;
 }

@@ -86,6 +86,7 @@ struct InstDesc {
   const uint32_t* rank_lo;
   int32_t lo_bits, hf_rank;  // hf_rank = rank(hf)
   const StrPlan* str;        // device copy of the string plan, or null
+  const double* hbound;      // device: sum of |vals| (bounds every row sum of |H|)
   // Hamiltonian
   int32_t G, W;              // groups, connectivity slots per output
   const GroupRec* groups;    // [G]
@@ -244,6 +245,8 @@ int set_error(int code, const char* msg);
 // imaginary part when term[j] < 0.
 cudaError_t fold_coefs(int64_t n_slots, const int64_t* off, const int32_t* term, const float* w,
                        const double* coefs, double* vals, double2* cvals, cudaStream_t stream);
+// *out = sum |v[i]| (deterministic)
+cudaError_t abs_sum(const double* v, int64_t n, double* out, cudaStream_t stream);
 
 // Up to kRowPtrs device rows per launch, passed by value: row r (global index
 // base + r) has len[r] doubles at p[r].

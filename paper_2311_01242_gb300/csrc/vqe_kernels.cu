@@ -59,6 +59,12 @@ __device__ __forceinline__ unsigned long long fix_mag(double x) {
 }
 // 2^e as a double, for |e| < 1000
 __device__ __forceinline__ double pow2(int e) { return __longlong_as_double(static_cast<long long>(1023 + e) << 52); }
+// smallest e with b < 2^e for a finite b >= 0 (clamped to [-400, 400])
+__device__ __forceinline__ int bound_exp(double b) {
+  const int ex = int((__double_as_longlong(b) >> 52) & 0x7ff);
+  const int e = ex == 0 ? -400 : ex - 1022;
+  return e < -400 ? -400 : (e > 400 ? 400 : e);
+}
 
 __device__ __forceinline__ uint32_t pattern_of(uint32_t src, uint32_t upos, int ubits) {
   uint32_t u = 0;
@@ -303,6 +309,49 @@ __device__ __forceinline__ void ell_row(const uint32_t* ell, const uint16_t* ell
 #pragma unroll
     for (int u = 0; u < U; ++u) cur[u] = nxt[u];
   }
+}
+
+// group_coef on fixed-point tables (int64, one common scale): the same terms,
+// summed exactly in the integer pipe.
+__device__ __forceinline__ long long group_coef_int(const GroupRec& g, const uint32_t* emask, const long long* vals,
+                                                    uint32_t src) {
+  if (g.kind == 0) {
+    const uint32_t u = pattern_of(src, g.upos, g.ubits);
+    const long long* vp = vals + g.vbeg + u;
+    long long f = neg_if(vp[0], parity32(src & emask[g.ebeg]));
+    for (int e = g.ebeg + 1, j = 1; e < g.eend; ++e, ++j) f += neg_if(vp[j << g.ubits], parity32(src & emask[e]));
+    return f;
+  }
+  const uint32_t z0 = emask[g.ebeg];
+  uint32_t m = src & emask[g.ebeg + 1];
+  long long f;
+  if (g.kind == 1) {
+    const uint32_t u = pattern_of(src, g.upos, g.ubits);
+    const long long* vp = vals + g.vbeg + u;
+    f = vp[0];
+    while (m) {
+      const int r = __ffs(m) - 1;
+      m &= m - 1;
+      f += vp[(1 + r) << g.ubits];
+    }
+  } else {
+    const long long* q = vals + g.vbeg;
+    const int nq = g.nq;
+    f = q[0];
+    while (m) {
+      const int pb = __ffs(m) - 1;
+      m &= m - 1;
+      f += q[1 + pb];
+      const long long* row = q + 1 + nq + pb * nq;
+      uint32_t m2 = m;
+      while (m2) {
+        const int qb = __ffs(m2) - 1;
+        m2 &= m2 - 1;
+        f += row[qb];
+      }
+    }
+  }
+  return neg_if(f, parity32(src & z0));
 }
 
 // One output row of H psi over the compressed state (entry r of psi is sector
@@ -594,14 +643,25 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
     int4* gdst = reinterpret_cast<int4*>(sg);
     for (int i = tid; i < 2 * G; i += bs) gdst[i] = __ldg(gsrc + i);
     for (int i = tid; i < d.E; i += bs) se[i] = __ldg(d.emask + i);
-    for (int i = tid; i < d.S; i += bs) sv[i] = A::coef(d, i);
+    if constexpr (FIX) {
+      // fixed-point tables: v * 2^(62 - eh), where 2^eh bounds the sum of |v|
+      // over every slot and so every row sum of |H|
+      const int eh = bound_exp(*d.hbound);
+      const double sc = pow2(62 - eh);
+      for (int i = tid; i < d.S; i += bs) sv[i] = llbits(__double2ll_rn(__ldg(d.vals + i) * sc));
+    } else {
+      for (int i = tid; i < d.S; i += bs) sv[i] = A::coef(d, i);
+    }
     tg = sg;
     te = se;
     tv = sv;
   }
   __syncthreads();
-  if constexpr (FIX) {
-    // psi in Q1.62 -> FP64 for H psi
+  // fixed-point H psi: staged integer tables times psi in Q1.62 (needs the
+  // staged tables; otherwise psi goes to FP64 for the FP64 H psi)
+  const bool int_h = FIX && stage;
+  const int eh = int_h ? bound_exp(*d.hbound) : 0;
+  if (FIX && !int_h) {
     for (int r = tid; r < D; r += bs) pl[r].x = __ll2double_rn(dbits(pl[r].x)) * 0x1p-62;
     __syncthreads();
   }
@@ -622,6 +682,28 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
     const bool live = lr < rows;
     const int r = r_lo + (live ? lr : 0);
     const uint32_t k = __ldg(d.sector + r);
+    if constexpr (FIX) {
+      if (int_h) {
+        // lambda in units of 2^(eh - 60): the high word of (table value) x (psi)
+        long long acc = 0;
+        if (live) {
+          const long long* tvi = reinterpret_cast<const long long*>(tv);
+          ell_row(d.ell, nullptr, W, D, r, half, TPR, [&](uint32_t gi) {
+            const GroupRec g = load_group(tg + gi);
+            const uint32_t src = k ^ g.x;
+            const uint32_t rs = uint32_t(rhi[src >> lb]) + uint32_t(rlo[src & lo_mask]);
+            acc += __mul64hi(group_coef_int(g, te, tvi, src), dbits(pl[rs].x));
+          });
+        }
+        acc += __shfl_xor_sync(0xffffffffu, acc, 1);  // even + odd slots (exact)
+        if (live && half == 0) {
+          pl[r].y = llbits(acc);
+          if constexpr (CL == 2) pl_peer[r].y = llbits(acc);
+          e_part += (__ll2double_rn(dbits(pl[r].x)) * 0x1p-62) * (__ll2double_rn(acc) * pow2(eh - 60));
+        }
+        continue;
+      }
+    }
     T acc = A::zero();
     if (live) {
       ell_row(d.ell, nullptr, W, D, r, half, TPR, [&](uint32_t gi) {
@@ -666,7 +748,11 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
   // rotations); phi comes from the forward sweep's per-pair slots in Q1.62.
   // Both CTAs of a cluster hold all of lambda here and derive the same e.
   int lam_e = 0;
-  if constexpr (FIX) {
+  if (int_h) {
+    // lambda is already fixed point in units of 2^(eh - 60) = 2^(61 - lam_e):
+    // ||lambda|| <= ||H||_2 <= ||H||_inf < 2^eh keeps every entry below 2^61 of them
+    lam_e = eh + 1;
+  } else if constexpr (FIX) {
     double l2 = 0.0;
     for (int r = tid; r < D; r += bs) {
       const double v = pl[r].y;
@@ -975,7 +1061,7 @@ __device__ __forceinline__ void hpsi_str_row(const StrPlan& sp, int ia, const Gr
 }
 
 template <bool REAL>
-__global__ void __launch_bounds__(kStrWarps * 32, 2)
+__global__ void __launch_bounds__(kStrWarps * 32, 3)
 k_hpsi_str(const StrPlan sp, const GroupRec* __restrict__ groups, const uint32_t* __restrict__ emask,
            const typename Amp<REAL>::C* __restrict__ vals, const typename Amp<REAL>::T* __restrict__ psi_am,
            typename Amp<REAL>::T* __restrict__ lam_am) {
@@ -1139,7 +1225,7 @@ __global__ void __launch_bounds__(512, 1) kb_hpsi(BatchDev b, BatchSegs sg) {
 }
 
 // String-driven H psi over the batch: block -> (instance slot, output alpha string)
-__global__ void __launch_bounds__(kStrWarps * 32, 2) kb_hpsi_str(BatchDev b, BatchSegs sg) {
+__global__ void __launch_bounds__(kStrWarps * 32, 3) kb_hpsi_str(BatchDev b, BatchSegs sg) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int s = find_seg(sg.pref, sg.nseg, int64_t(blockIdx.x));
   const int i = __ldg(sg.inst + s);
