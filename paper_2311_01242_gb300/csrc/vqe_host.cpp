@@ -256,6 +256,7 @@ struct vqe_hamiltonian_s {
     bool use_ell = false;
     uint32_t* d_ell = nullptr;
     uint16_t* d_ell16 = nullptr;      // device-built 16-bit table (large sectors)
+    uint32_t* d_ellp = nullptr;       // packed entries for the resident kernel (small sectors)
     int64_t nnz = 0;                  // connected (output, group) pairs
     double extra_adds = 0;            // sum over nnz of (entries - 1)
     // spin sectors: alpha/beta string tables of the string-driven H psi
@@ -277,6 +278,7 @@ struct vqe_hamiltonian_s {
     dfree(d_bound);
     for (auto& kv : ells) {
       ell_release(kv.second.d_ell);
+      ell_release(kv.second.d_ellp);
       ell16_release(kv.second.d_ell16);
       for (void* p : kv.second.str_alloc) dfree(p);
     }
@@ -486,10 +488,9 @@ int build_strings(vqe_hamiltonian_t h, vqe_ansatz_t a, vqe_hamiltonian_s::Ell* e
   };
   const std::vector<uint32_t> ka = subsets(even, Na), kb = subsets(odd, Nb);
   const int64_t Da = int64_t(ka.size()), Db = int64_t(kb.size());
-  // shared memory of a block: two rows of complex amplitudes and the beta strings
-  const size_t smem = size_t(Db) * (2 * 16 + 4);
-  if (Da * Db != int64_t(a->sector.size()) || Db < vqe::kStrMinDb || Db > 65535 || smem > size_t(200) * 1024)
-    return VQE_OK;  // not used
+  // shared memory of a block (complex amplitudes: the larger of the two)
+  const size_t smem = vqe::str_smem_bytes(int(std::min<int64_t>(Db, 65535)), 16);
+  if (Da * Db != int64_t(a->sector.size()) || Db > 65535 || smem > size_t(200) * 1024) return VQE_OK;  // not used
   {
     static std::mutex mu;
     static size_t set_to = 0;
@@ -701,6 +702,30 @@ const vqe_hamiltonian_s::Ell* get_ell(vqe_hamiltonian_t h, vqe_ansatz_t a, int* 
         *err = rc;
         return nullptr;
       }
+      if (W > 0 && D <= 32767 && G <= 8191) {
+        // packed entries for the resident kernel: source rank, source pattern, group
+        const uint32_t lo_mask = (1u << a->lo_bits) - 1u;
+        std::vector<uint32_t> packed(ell.size(), vqe::kEllPad);
+        parallel_for(D, [&](int64_t lo, int64_t hi) {
+          for (int64_t r = lo; r < hi; ++r) {
+            const uint32_t k = a->sector[size_t(r)];
+            for (int j = 0; j < W; ++j) {
+              const uint32_t g = ell[size_t(j) * size_t(D) + size_t(r)];
+              if (g == vqe::kEllPad) break;
+              const GroupRec& gr = h->groups[g];
+              const uint32_t src = k ^ gr.x;
+              uint32_t u = 0;
+              for (int b = 0; b < gr.ubits; ++b) u |= ((src >> ((gr.upos >> (8 * b)) & 31u)) & 1u) << b;
+              const uint32_t rs = a->rank_hi[src >> a->lo_bits] + a->rank_lo[src & lo_mask];
+              packed[size_t(j) * size_t(D) + size_t(r)] = rs | (u << 15) | (g << 19);
+            }
+          }
+        });
+        if ((rc = ell_acquire(packed, &e.d_ellp)) != VQE_OK) {
+          *err = rc;
+          return nullptr;
+        }
+      }
     }
   }
   if (!e.use_ell || e.d_ell16) {
@@ -742,6 +767,7 @@ InstDesc make_desc(vqe_hamiltonian_t h, vqe_ansatz_t a, const vqe_hamiltonian_s:
   d.lo_bits = a->lo_bits;
   d.hf_rank = int32_t(a->rank_hi[a->hf >> a->lo_bits] + a->rank_lo[a->hf & ((1u << a->lo_bits) - 1u)]);
   d.str = e->use_str ? e->d_str : nullptr;
+  d.ellp = e->d_ellp;
   d.hbound = h->d_bound;
   d.gates = a->d_gates;
   d.pair_off = a->d_pair_off;
@@ -771,7 +797,7 @@ bool use_fixed(bool real) { return real && (g_flags & VQE_FLAG_FP64_SWEEPS) == 0
 // so, sets the shared-memory bytes and the descriptor's staging/sweep fields.
 bool resident_fit(vqe_ansatz_t a, const vqe_hamiltonian_s::Ell* e, bool real, InstDesc* d, size_t* smem) {
   if (g_flags & VQE_FLAG_FORCE_STREAMING) return false;
-  if (!e->use_ell || !e->d_ell || a->n > 16) return false;
+  if (!e->use_ell || !e->d_ell || !e->d_ellp || a->n > 16) return false;
   if (a->sector.size() > 32767) return false;  // 15-bit ranks in the staged pair list
   if (a->pairs.size() > (size_t(1) << 24) || d->S > (1 << 24) || d->G > (1 << 20)) return false;
   int dev = 0, optin = 0;
@@ -1616,8 +1642,8 @@ static int build_stream_batch(vqe_batch_s* B) {
       break;
     }
     str_inst[s] = s;
-    str_pref[s + 1] = str_pref[s] + e->str.Da;
-    sb.str_smem = std::max(sb.str_smem, size_t(e->str.Db) * (2 * 8 + 4));
+    str_pref[s + 1] = str_pref[s] + vqe::str_blocks(e->str.Da, e->str.Db);
+    sb.str_smem = std::max(sb.str_smem, vqe::str_smem_bytes(e->str.Db, 8));
   }
   if (all_str) {
     if ((rc = upload(str_inst, &sb.d_str_inst))) return rc;

@@ -56,7 +56,7 @@ struct GateRec {
 // the entry range of its list for each of the kStrWarps warps (a fixed share of
 // the Ib range each).
 constexpr int kStrWarps = 8;
-constexpr int kStrMinDb = 512;  // smaller beta string sets keep the connectivity rows
+constexpr int kStrMinDb = 512;  // smaller beta string sets: a warp per output alpha string
 struct StrPlan {
   int32_t Da, Db, NB, pad;
   const uint32_t* ka;      // [Da] alpha strings as qubit masks, increasing
@@ -86,6 +86,9 @@ struct InstDesc {
   const uint32_t* rank_lo;
   int32_t lo_bits, hf_rank;  // hf_rank = rank(hf)
   const StrPlan* str;        // device copy of the string plan, or null
+  // resident kernel: [W][D] packed entries rank(src) | pattern(src) << 15 | group << 19
+  // (D <= 32767, G <= 8191), pad 0xFFFFFFFF
+  const uint32_t* ellp;
   const double* hbound;      // device: sum of |vals| (bounds every row sum of |H|)
   // Hamiltonian
   int32_t G, W;              // groups, connectivity slots per output
@@ -129,7 +132,7 @@ struct BatchDev {
 };
 
 // str_segs.total > 0: every instance has a string plan and H psi runs
-// string-driven (one block per (instance, output alpha string); str_smem bytes).
+// string-driven (str_blocks blocks per instance; str_smem bytes).
 cudaError_t batch_stream_run(const BatchDev& b, const BatchSegs* gate_segs, const BatchSegs& out_segs,
                              const BatchSegs& str_segs, size_t str_smem,
                              const int32_t* d_gm_inst, const int32_t* d_gm_gate, int64_t n_gm,
@@ -146,6 +149,16 @@ struct ResidentLayout {
 };
 
 __host__ __device__ inline uint32_t align_up(uint32_t v, uint32_t a) { return (v + a - 1) / a * a; }
+
+// String-driven H psi: shared memory and blocks of its two forms (a block per
+// output alpha string when Db >= kStrMinDb, else a warp per output alpha string).
+__host__ __device__ inline size_t str_smem_bytes(int Db, size_t amp) {
+  return Db >= kStrMinDb ? size_t(Db) * (2 * amp + 4)
+                         : align_up(uint32_t(Db) * 4u, 16u) + size_t(kStrWarps) * 2 * size_t(Db) * amp;
+}
+__host__ __device__ inline int str_blocks(int Da, int Db) {
+  return Db >= kStrMinDb ? Da : (Da + kStrWarps - 1) / kStrWarps;
+}
 
 // Staged H psi tables: groups, then entry masks, then values.
 __host__ __device__ inline uint32_t staged_table_bytes(int G, int E, int S, bool real) {
@@ -166,8 +179,8 @@ __host__ __device__ inline ResidentLayout resident_layout(int n, int M, int P, i
   o += uint32_t(M + 1) * 4u;
   L.pairs = align_up(o, 16u);  // ra | sign << 15 | rb << 16 per pair
   o = L.pairs + uint32_t(P) * 4u;
-  L.rank = align_up(o, 16u);   // u16 rank tables: high part, then low part
-  o = L.rank + ((1u << (n - lo_bits)) + (1u << lo_bits)) * 2u;
+  L.rank = align_up(o, 16u);   // (no rank tables: the packed entries carry source ranks)
+  o = L.rank;
   // per-pair slots: with real amplitudes two per pair (one per lane of the pair),
   // holding the forward sweep's output and later the gradient contribution; with
   // complex amplitudes one gradient contribution per pair

@@ -165,13 +165,13 @@ __device__ __forceinline__ void cadd(C& f, const C& v) {
 
 // Folded coefficient f_g(src) of a group (all three forms of GroupRec), from
 // tables in shared or global memory. Signs are applied in the integer pipe.
+// u is the pattern of src on the group's pattern qubits (pattern_of).
 template <bool REAL>
-__device__ __forceinline__ typename Amp<REAL>::C group_coef(const GroupRec& g, const uint32_t* emask,
-                                                            const typename Amp<REAL>::C* vals,
-                                                            uint32_t src) {
+__device__ __forceinline__ typename Amp<REAL>::C group_coef_u(const GroupRec& g, const uint32_t* emask,
+                                                              const typename Amp<REAL>::C* vals, uint32_t src,
+                                                              uint32_t u) {
   typedef typename Amp<REAL>::C C;
   if (g.kind == 0) {
-    const uint32_t u = pattern_of(src, g.upos, g.ubits);
     const C* vp = vals + g.vbeg + u;
     C f = sflip(vp[0], parity32(src & emask[g.ebeg]));
     for (int e = g.ebeg + 1, j = 1; e < g.eend; ++e, ++j)
@@ -182,7 +182,6 @@ __device__ __forceinline__ typename Amp<REAL>::C group_coef(const GroupRec& g, c
   uint32_t m = src & emask[g.ebeg + 1];
   C f;
   if (g.kind == 1) {
-    const uint32_t u = pattern_of(src, g.upos, g.ubits);
     const C* vp = vals + g.vbeg + u;
     f = vp[0];
     while (m) {
@@ -208,6 +207,12 @@ __device__ __forceinline__ typename Amp<REAL>::C group_coef(const GroupRec& g, c
     }
   }
   return sflip(f, parity32(src & z0));
+}
+
+template <bool REAL>
+__device__ __forceinline__ typename Amp<REAL>::C group_coef(const GroupRec& g, const uint32_t* emask,
+                                                            const typename Amp<REAL>::C* vals, uint32_t src) {
+  return group_coef_u<REAL>(g, emask, vals, src, pattern_of(src, g.upos, g.ubits));
 }
 
 // group_coef split at its first table term: v0 = vals[vbeg + u] and z = emask[ebeg]
@@ -314,9 +319,8 @@ __device__ __forceinline__ void ell_row(const uint32_t* ell, const uint16_t* ell
 // group_coef on fixed-point tables (int64, one common scale): the same terms,
 // summed exactly in the integer pipe.
 __device__ __forceinline__ long long group_coef_int(const GroupRec& g, const uint32_t* emask, const long long* vals,
-                                                    uint32_t src) {
+                                                    uint32_t src, uint32_t u) {
   if (g.kind == 0) {
-    const uint32_t u = pattern_of(src, g.upos, g.ubits);
     const long long* vp = vals + g.vbeg + u;
     long long f = neg_if(vp[0], parity32(src & emask[g.ebeg]));
     for (int e = g.ebeg + 1, j = 1; e < g.eend; ++e, ++j) f += neg_if(vp[j << g.ubits], parity32(src & emask[e]));
@@ -326,7 +330,6 @@ __device__ __forceinline__ long long group_coef_int(const GroupRec& g, const uin
   uint32_t m = src & emask[g.ebeg + 1];
   long long f;
   if (g.kind == 1) {
-    const uint32_t u = pattern_of(src, g.upos, g.ubits);
     const long long* vp = vals + g.vbeg + u;
     f = vp[0];
     while (m) {
@@ -440,9 +443,9 @@ __device__ __forceinline__ void sweep_barrier(int nthreads) {
 // the sector (entry r is the amplitude of sector[r]): HF init, forward sweep,
 // H psi with the energy, and the reverse sweep with per-pair gradient
 // contributions summed per gate in pair order at the end. Gate records,
-// cos/sin, pair offsets, pair lists (two ranks and the JW sign per pair) and
-// the rank tables are staged in shared memory first; H psi finds a source
-// k ^ x through the rank tables. The sweeps run on the first `sweep_threads`
+// cos/sin, pair offsets and pair lists (two ranks and the JW sign per pair)
+// are staged in shared memory first; H psi reads packed connectivity entries
+// (source rank, source pattern, group), so a source needs no lookup. The sweeps run on the first `sweep_threads`
 // threads (one warp per SM sub-partition or more) with a named barrier between
 // gates; the instance's pairs are dealt round-robin over those warps.
 //
@@ -481,9 +484,7 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
   const int P = int(d.pair_off[M]);
   const bool stage = d.stage_tables != 0;
   const int sw = d.sweep_threads;
-  const int lb = d.lo_bits, hb = n - lb;
-  const uint32_t lo_mask = (1u << lb) - 1u;
-  const ResidentLayout L = resident_layout(n, M, P, G, d.E, d.S, D, lb, REAL, stage);
+  const ResidentLayout L = resident_layout(n, M, P, G, d.E, d.S, D, d.lo_bits, REAL, stage);
   T* psi = reinterpret_cast<T*>(smem + L.psi);
   T* lam = reinterpret_cast<T*>(smem + L.lam);
   double2* pl = reinterpret_cast<double2*>(smem + L.psi);  // real: pl[r] = {psi_r, lambda_r}
@@ -491,8 +492,6 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
   GateRec* gates = reinterpret_cast<GateRec*>(smem + L.gates);
   int32_t* poff = reinterpret_cast<int32_t*>(smem + L.poff);
   uint32_t* rp = reinterpret_cast<uint32_t*>(smem + L.pairs);
-  uint16_t* rhi = reinterpret_cast<uint16_t*>(smem + L.rank);
-  uint16_t* rlo = rhi + (1 << hb);
   double* gbuf = reinterpret_cast<double*>(smem + L.gbuf);
   double* red = reinterpret_cast<double*>(smem + L.red);
   const int64_t row = d.inst;
@@ -517,8 +516,6 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
     const uint2 e = __ldg(d.rpairs + p);
     rp[p] = (e.x & 0x7fffu) | ((e.x >> 31) << 15) | (e.y << 16);
   }
-  for (int i = tid; i < (1 << hb); i += bs) rhi[i] = uint16_t(__ldg(d.rank_hi + i));
-  for (int i = tid; i < (1 << lb); i += bs) rlo[i] = uint16_t(__ldg(d.rank_lo + i));
   if constexpr (REAL) {
     for (int r = tid; r < D; r += bs) pl[r] = make_double2(0.0, 0.0);
   } else {
@@ -529,7 +526,7 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
   }
   // pull the tables H psi reads later into L2 while the forward sweep runs
   {
-    const char* ell_b = reinterpret_cast<const char*>(d.ell);
+    const char* ell_b = reinterpret_cast<const char*>(d.ellp);
     const int64_t ell_bytes = int64_t(W) * D * 4;
     for (int64_t o = int64_t(tid) * 128; o < ell_bytes; o += int64_t(bs) * 128) prefetch_l2(ell_b + o);
     const char* val_b = REAL ? reinterpret_cast<const char*>(d.vals) : reinterpret_cast<const char*>(d.cvals);
@@ -688,11 +685,9 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
         long long acc = 0;
         if (live) {
           const long long* tvi = reinterpret_cast<const long long*>(tv);
-          ell_row(d.ell, nullptr, W, D, r, half, TPR, [&](uint32_t gi) {
-            const GroupRec g = load_group(tg + gi);
-            const uint32_t src = k ^ g.x;
-            const uint32_t rs = uint32_t(rhi[src >> lb]) + uint32_t(rlo[src & lo_mask]);
-            acc += __mul64hi(group_coef_int(g, te, tvi, src), dbits(pl[rs].x));
+          ell_row(d.ellp, nullptr, W, D, r, half, TPR, [&](uint32_t e) {
+            const GroupRec g = load_group(tg + (e >> 19));
+            acc += __mul64hi(group_coef_int(g, te, tvi, k ^ g.x, (e >> 15) & 15u), dbits(pl[e & 0x7fffu].x));
           });
         }
         acc += __shfl_xor_sync(0xffffffffu, acc, 1);  // even + odd slots (exact)
@@ -706,14 +701,13 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
     }
     T acc = A::zero();
     if (live) {
-      ell_row(d.ell, nullptr, W, D, r, half, TPR, [&](uint32_t gi) {
-        const GroupRec g = load_group(tg + gi);
-        const uint32_t src = k ^ g.x;
-        const uint32_t rs = uint32_t(rhi[src >> lb]) + uint32_t(rlo[src & lo_mask]);
+      ell_row(d.ellp, nullptr, W, D, r, half, TPR, [&](uint32_t e) {
+        const GroupRec g = load_group(tg + (e >> 19));
+        const C f = group_coef_u<REAL>(g, te, tv, k ^ g.x, (e >> 15) & 15u);
         if constexpr (REAL)
-          A::mac(acc, group_coef<REAL>(g, te, tv, src), pl[rs].x);
+          A::mac(acc, f, pl[e & 0x7fffu].x);
         else
-          A::mac(acc, group_coef<REAL>(g, te, tv, src), psi[rs]);
+          A::mac(acc, f, psi[e & 0x7fffu]);
       });
     }
     if constexpr (TPR == 2) {
@@ -990,14 +984,56 @@ k_gate_adj(const uint2* __restrict__ rp, int64_t P, const double2* __restrict__ 
   if (threadIdx.x == 0) gpart[blockIdx.x] = s;
 }
 
-// String-driven H psi row (spin sectors; see StrPlan): lambda[Ia, :] for one
-// output alpha string. For each bucket with a source alpha string Ja, the
-// source row psi[Ja, :] is staged in shared memory; then, group by group in the
-// bucket's fixed order, every warp walks its share of the group's beta pair
-// list and adds f_g(src) psi[Ja, Jb] to lambda[Ia, Ib]. A warp owns a fixed range
-// of Ib, so each output is summed by one lane in bucket and group order.
-// Needs blockDim.x == 32 * kStrWarps and 2 * Db amplitudes + Db words of shared
-// memory at smem.
+// Groups gi in [g0, g1) of one bucket against a staged source row: for each
+// group in order, lanes walk list entries [e0, e1) (this warp's share, or the
+// whole list) and add f_g(src) psi_s[Jb] into lam_s[Ib]. The next group's
+// record and range are loaded while the current group runs; four list entries
+// per lane are in flight. Entries of one list have distinct Ib, and __syncwarp
+// separates the groups, so each output is updated by one lane at a time, in
+// group order.
+template <bool REAL>
+__device__ __forceinline__ void str_groups(const StrPlan& sp, int g0, int g1, int w_lo, int w_hi, uint32_t ka,
+                                           const GroupRec* __restrict__ groups, const uint32_t* __restrict__ emask,
+                                           const typename Amp<REAL>::C* __restrict__ vals, const uint32_t* kb_s,
+                                           const typename Amp<REAL>::T* psi_s, typename Amp<REAL>::T* lam_s,
+                                           int lane) {
+  typedef Amp<REAL> A;
+  if (g0 >= g1) return;
+  GroupRec g = load_group(groups + __ldg(sp.bgrp + g0));
+  int e0 = __ldg(sp.bsplit + int64_t(g0) * (kStrWarps + 1) + w_lo);
+  int e1 = __ldg(sp.bsplit + int64_t(g0) * (kStrWarps + 1) + w_hi);
+  for (int gi = g0; gi < g1; ++gi) {
+    GroupRec gn = g;
+    int e0n = 0, e1n = 0;
+    if (gi + 1 < g1) {
+      gn = load_group(groups + __ldg(sp.bgrp + gi + 1));
+      e0n = __ldg(sp.bsplit + int64_t(gi + 1) * (kStrWarps + 1) + w_lo);
+      e1n = __ldg(sp.bsplit + int64_t(gi + 1) * (kStrWarps + 1) + w_hi);
+    }
+    for (int e = e0 + lane; e < e1; e += 4 * 32) {
+      uint32_t ent[4];
+#pragma unroll
+      for (int u = 0; u < 4; ++u) ent[u] = (e + 32 * u < e1) ? __ldg(sp.lists + e + 32 * u) : 0xFFFFFFFFu;
+#pragma unroll
+      for (int u = 0; u < 4; ++u) {
+        if (ent[u] == 0xFFFFFFFFu) break;
+        const uint32_t ib = ent[u] & 0xFFFFu, jb = ent[u] >> 16;
+        A::mac(lam_s[ib], group_coef<REAL>(g, emask, vals, ka | kb_s[jb]), psi_s[jb]);
+      }
+    }
+    __syncwarp();
+    g = gn;
+    e0 = e0n;
+    e1 = e1n;
+  }
+}
+
+// String-driven H psi (spin sectors; see StrPlan), block form for large beta
+// string sets: lambda[Ia, :] for one output alpha string per block. For each
+// bucket with a source alpha string Ja, the source row psi[Ja, :] is staged in
+// shared memory; then every warp walks its share (a fixed Ib range) of each
+// group's beta pair list. Needs blockDim.x == 32 * kStrWarps and 2 * Db
+// amplitudes + Db words of shared memory.
 template <bool REAL>
 __device__ __forceinline__ void hpsi_str_row(const StrPlan& sp, int ia, const GroupRec* __restrict__ groups,
                                              const uint32_t* __restrict__ emask,
@@ -1022,42 +1058,49 @@ __device__ __forceinline__ void hpsi_str_row(const StrPlan& sp, int ia, const Gr
     const T* row = psi_am + int64_t(ja) * Db;
     for (int j = tid; j < Db; j += bs) psi_s[j] = row[j];
     __syncthreads();
-    const uint32_t ka = __ldg(sp.ka + ja);
-    const int g0 = __ldg(sp.boff + b), g1 = __ldg(sp.boff + b + 1);
-    // the next group's record and list range are loaded while the current group runs
-    if (g0 >= g1) continue;  // (buckets are never empty)
-    GroupRec g = load_group(groups + __ldg(sp.bgrp + g0));
-    int e0 = __ldg(sp.bsplit + int64_t(g0) * (kStrWarps + 1) + w);
-    int e1 = __ldg(sp.bsplit + int64_t(g0) * (kStrWarps + 1) + w + 1);
-    for (int gi = g0; gi < g1; ++gi) {
-      GroupRec gn = g;
-      int e0n = 0, e1n = 0;
-      if (gi + 1 < g1) {
-        gn = load_group(groups + __ldg(sp.bgrp + gi + 1));
-        e0n = __ldg(sp.bsplit + int64_t(gi + 1) * (kStrWarps + 1) + w);
-        e1n = __ldg(sp.bsplit + int64_t(gi + 1) * (kStrWarps + 1) + w + 1);
-      }
-      // four list entries per lane in flight, then their updates in entry order
-      for (int e = e0 + lane; e < e1; e += 4 * 32) {
-        uint32_t ent[4];
-#pragma unroll
-        for (int u = 0; u < 4; ++u) ent[u] = (e + 32 * u < e1) ? __ldg(sp.lists + e + 32 * u) : 0xFFFFFFFFu;
-#pragma unroll
-        for (int u = 0; u < 4; ++u) {
-          if (ent[u] == 0xFFFFFFFFu) break;
-          const uint32_t ib = ent[u] & 0xFFFFu, jb = ent[u] >> 16;
-          A::mac(lam_s[ib], group_coef<REAL>(g, emask, vals, ka | kb_s[jb]), psi_s[jb]);
-        }
-      }
-      __syncwarp();
-      g = gn;
-      e0 = e0n;
-      e1 = e1n;
-    }
+    str_groups<REAL>(sp, __ldg(sp.boff + b), __ldg(sp.boff + b + 1), w, w + 1, __ldg(sp.ka + ja), groups, emask,
+                     vals, kb_s, psi_s, lam_s, lane);
   }
   __syncthreads();
   T* out = lam_am + int64_t(ia) * Db;
   for (int j = tid; j < Db; j += bs) out[j] = lam_s[j];
+}
+
+// Warp form for small beta string sets: each warp owns one output alpha string
+// (ia0 + warp), stages its own source rows and walks whole lists; the same
+// per-output order as the block form, so the same bits. Shared memory: Db
+// words of beta strings, then 2 * Db amplitudes per warp.
+template <bool REAL>
+__device__ __forceinline__ void hpsi_str_warps(const StrPlan& sp, int ia0, const GroupRec* __restrict__ groups,
+                                               const uint32_t* __restrict__ emask,
+                                               const typename Amp<REAL>::C* __restrict__ vals,
+                                               const typename Amp<REAL>::T* __restrict__ psi_am,
+                                               typename Amp<REAL>::T* __restrict__ lam_am, unsigned char* smem) {
+  typedef Amp<REAL> A;
+  typedef typename A::T T;
+  const int tid = threadIdx.x, bs = blockDim.x, w = tid >> 5, lane = tid & 31;
+  const int Db = sp.Db, NB = sp.NB;
+  uint32_t* kb_s = reinterpret_cast<uint32_t*>(smem);
+  T* psi_s = reinterpret_cast<T*>(smem + align_up(uint32_t(Db) * 4u, 16u)) + int64_t(w) * 2 * Db;
+  T* lam_s = psi_s + Db;
+  for (int j = tid; j < Db; j += bs) kb_s[j] = __ldg(sp.kb + j);
+  __syncthreads();
+  const int ia = ia0 + w;
+  if (ia >= sp.Da) return;  // no block-wide barrier follows
+  for (int j = lane; j < Db; j += 32) lam_s[j] = A::zero();
+  for (int b = 0; b < NB; ++b) {
+    const int ja = __ldg(sp.ja + int64_t(ia) * NB + b);
+    if (ja < 0) continue;  // same for the whole warp
+    __syncwarp();
+    const T* row = psi_am + int64_t(ja) * Db;
+    for (int j = lane; j < Db; j += 32) psi_s[j] = row[j];
+    __syncwarp();
+    str_groups<REAL>(sp, __ldg(sp.boff + b), __ldg(sp.boff + b + 1), 0, kStrWarps, __ldg(sp.ka + ja), groups, emask,
+                     vals, kb_s, psi_s, lam_s, lane);
+  }
+  __syncwarp();
+  T* out = lam_am + int64_t(ia) * Db;
+  for (int j = lane; j < Db; j += 32) out[j] = lam_s[j];
 }
 
 template <bool REAL>
@@ -1066,7 +1109,10 @@ k_hpsi_str(const StrPlan sp, const GroupRec* __restrict__ groups, const uint32_t
            const typename Amp<REAL>::C* __restrict__ vals, const typename Amp<REAL>::T* __restrict__ psi_am,
            typename Amp<REAL>::T* __restrict__ lam_am) {
   extern __shared__ __align__(16) unsigned char smem[];
-  hpsi_str_row<REAL>(sp, int(blockIdx.x), groups, emask, vals, psi_am, lam_am, smem);
+  if (sp.Db >= kStrMinDb)
+    hpsi_str_row<REAL>(sp, int(blockIdx.x), groups, emask, vals, psi_am, lam_am, smem);
+  else
+    hpsi_str_warps<REAL>(sp, int(blockIdx.x) * kStrWarps, groups, emask, vals, psi_am, lam_am, smem);
 }
 
 // dst[i] = src[perm[i]] (sector order -> alpha-major) and the reverse scatter
@@ -1225,16 +1271,19 @@ __global__ void __launch_bounds__(512, 1) kb_hpsi(BatchDev b, BatchSegs sg) {
 }
 
 // String-driven H psi over the batch: block -> (instance slot, output alpha string)
-__global__ void __launch_bounds__(kStrWarps * 32, 3) kb_hpsi_str(BatchDev b, BatchSegs sg) {
+__global__ void __launch_bounds__(kStrWarps * 32, 2) kb_hpsi_str(BatchDev b, BatchSegs sg) {
   extern __shared__ __align__(16) unsigned char smem[];
   const int s = find_seg(sg.pref, sg.nseg, int64_t(blockIdx.x));
   const int i = __ldg(sg.inst + s);
-  const int ia = int(int64_t(blockIdx.x) - __ldg(sg.pref + s));
+  const int blk = int(int64_t(blockIdx.x) - __ldg(sg.pref + s));
   const InstDesc* d = b.desc + i;
   const StrPlan sp = *d->str;
   const double* psi_am = reinterpret_cast<const double*>(b.ws + b.am_off[i]);
   double* lam_am = reinterpret_cast<double*>(b.ws + b.am_off[i]) + d->D;
-  hpsi_str_row<true>(sp, ia, d->groups, d->emask, d->vals, psi_am, lam_am, smem);
+  if (sp.Db >= kStrMinDb)
+    hpsi_str_row<true>(sp, blk, d->groups, d->emask, d->vals, psi_am, lam_am, smem);
+  else
+    hpsi_str_warps<true>(sp, blk * kStrWarps, d->groups, d->emask, d->vals, psi_am, lam_am, smem);
 }
 
 // alpha-major copy of every instance's psi
@@ -1440,9 +1489,10 @@ cudaError_t stream_hpsi(const InstDesc& d, const StreamPlan& sp, const StreamBuf
     if constexpr (REAL) tv = d.vals; else tv = d.cvals;
     T* psi_am = static_cast<T*>(b.psi_am);
     T* lam_am = static_cast<T*>(b.lam_am);
-    const size_t smem = size_t(sp.str.Db) * (2 * sizeof(T) + 4);
+    const size_t smem = str_smem_bytes(sp.str.Db, sizeof(T));
     k_perm_gather<REAL><<<grid, kStreamThreads, 0, stream>>>(sp.str.perm, d.D, psi, psi_am);
-    k_hpsi_str<REAL><<<sp.str.Da, kStrWarps * 32, smem, stream>>>(sp.str, d.groups, d.emask, tv, psi_am, lam_am);
+    k_hpsi_str<REAL><<<str_blocks(sp.str.Da, sp.str.Db), kStrWarps * 32, smem, stream>>>(sp.str, d.groups, d.emask,
+                                                                                         tv, psi_am, lam_am);
     k_perm_scatter<REAL><<<grid, kStreamThreads, 0, stream>>>(sp.str.perm, d.D, lam_am, lam);
     k_dot<REAL><<<grid, kStreamThreads, 0, stream>>>(psi, lam, d.D, b.epart);
   } else if (sp.use_ell) {
