@@ -177,8 +177,8 @@ void vqe_destroy_ansatz(vqe_ansatz_t a);
  *   VQE_FLAG_FORCE_COMPLEX is set); modes may be OR-ed.
  * It holds two state vectors (|psi> or |phi>, and |lambda>) compressed to the
  * ansatz's sector (entry r is the amplitude of the r-th sector state in
- * increasing order), plus reduction partials. The workspace must be 256-byte
- * aligned.
+ * increasing order), their copies in alpha-major order (string-driven H psi),
+ * and reduction partials. The workspace must be 256-byte aligned.
  * The first call for a (Hamiltonian, sector) pair builds that pair's
  * connectivity table (synchronous, allocates); call it before any stream
  * capture. Returns 0 and sets the error message on failure.
@@ -337,7 +337,7 @@ int vqe_mlp_adam(int64_t n, float* params, const float* grads, float* m, float* 
  * The caller passes theta, the energy and the gradient as for vqe_energy_grad;
  * the scratch comes from one static device array of VQE_NOALLOC_SCRATCH_BYTES
  * that every GPU loading this library keeps until the process exits.
- * Limit: instances whose streaming workspace (two sector-sized vectors of
+ * Limit: instances whose streaming workspace (four sector-sized vectors of
  * 8-byte real amplitudes, the cos/sin table and 8 KiB of partials per
  * parameter) exceeds that size are rejected with VQE_ERR_INVALID_ARG and a
  * message; for example 20 qubits with 10 electrons (63,504 sector states) and
