@@ -535,7 +535,7 @@ def main():
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": max(3, args.warmup), "ms_per_step": ms_per_step, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": "f64 + i64 (Q1.62 fixed-point gate sweeps)",
+        "scaling": "weak", "vs_baseline": None, "dtype": "f64 + i64 (fixed-point gate sweeps and H psi)",
         "data": "synthetic",
         "config": {"workload": WORKLOAD, "instances_per_gpu": n_inst, "qubits": 12, "params": M,
                    "l2": "flushed between timed launches (512 MB write)", "parallelism": f"replicas x{world}"},
@@ -546,7 +546,7 @@ def main():
                      "peak_source": "derived: 2 DFMA/clk/SM (probe) x 152 SMs x 2070 MHz x 2",
                      "fp64_flops_per_launch": flops_per_launch,
                      "note": "achieved counts the method's arithmetic as FP64-equivalent flops (vqe_work_estimate); "
-                             "the gate sweeps run it on the integer pipe in Q1.62 fixed point, H psi on FP64",
+                             "the gate sweeps and H psi run it on the integer pipe in 64-bit fixed point, the energy sum in FP64",
                      "probe": {"dfma_per_clock_per_sm": probe["dfma_per_clock_per_sm"],
                                "dependent_dfma_clocks": probe["dependent_dfma_clocks"],
                                "sm_count": probe["sm_count"]}},
