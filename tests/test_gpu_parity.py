@@ -283,6 +283,52 @@ def test_identity_only_hamiltonian_and_dropped_terms():
     assert float(e0) == 0.0 and np.all(g0.cpu().numpy() == 0.0)
 
 
+PATHS = [0, vq.VQE_FLAG_FORCE_STREAMING, vq.VQE_FLAG_FORCE_STREAMING | vq.VQE_FLAG_NO_STRINGS,
+         vq.VQE_FLAG_FORCE_COMPLEX]
+
+
+@pytest.mark.parametrize("flags", PATHS, ids=["resident", "streaming-strings", "streaming-rows", "complex"])
+def test_degenerate_inputs_on_every_path(flags):
+    """No excitations, one-state sectors (no electrons, all orbitals filled),
+    an identity-only and an all-dropped Hamiltonian, and a batch mixing them
+    with a full pool, on each kernel path; against the oracle and exact values."""
+    rng = np.random.default_rng(31)
+    p = synth.random_problem(rng, 4, 4, 3)  # 8 qubits, 2 + 2 electrons
+    model = oracle.EnergyModel.from_problem(p, full=True)
+    exc = synth.uccsd_pool(8, 4)
+    th = rng.normal(0.0, 0.3, size=len(exc))
+    old = vq.set_flags(flags)
+    try:
+        H = vq.Hamiltonian.from_problem(p)
+        A0 = vq.Ansatz(8, 15, np.zeros((0, 4), dtype=np.int32))
+        e0, g0 = vq.energy_grad(H, A0, np.zeros(0))
+        assert abs(float(e0) - oracle.energy(model, 15, [], [])) <= E_TOL and g0.numel() == 0
+        for hf in (0, 255):  # sectors of a single state
+            A1 = vq.Ansatz(8, hf, np.zeros((0, 4), dtype=np.int32))
+            assert abs(float(vq.energy(H, A1, np.zeros(0))) - oracle.energy(model, hf, [], [])) <= E_TOL
+        A = vq.Ansatz(8, 15, exc)
+        Hi = vq.Hamiltonian(8, [0], [0], [2.5])
+        e, g = vq.energy_grad(Hi, A, th)
+        assert abs(float(e) - 2.5) <= 1e-12 and float(g.abs().max()) <= 1e-12
+        Hz = vq.Hamiltonian(8, [3, 3], [0, 0], [1e-20, -1e-20], drop_tol=1e-16)
+        e, g = vq.energy_grad(Hz, A, th)
+        assert float(e) == 0.0 and float(g.abs().max()) == 0.0
+        e, g = vq.energy_grad(H, A, th)
+        idx = [0, len(exc) // 2, len(exc) - 1]
+        e_o, g_o = oracle.gradient_direct(model, 15, exc, th, idx)
+        assert abs(float(e) - e_o) <= E_TOL and np.abs(g.cpu().numpy()[idx] - g_o).max() <= G_TOL
+        B = vq.Batch([H, H, Hi, Hz], [A0, A, A, A])
+        theta = torch.zeros(4, B.max_params, dtype=torch.float64)
+        for i in (1, 2, 3):
+            theta[i] = torch.as_tensor(th)
+        eb, gb = B.energy_grad(theta.cuda())
+        assert abs(float(eb[0]) - float(e0)) <= 1e-12 and abs(float(eb[1]) - float(e)) <= 1e-12
+        assert float((gb[1] - g).abs().max()) <= 1e-12
+        assert abs(float(eb[2]) - 2.5) <= 1e-12 and float(eb[3]) == 0.0
+    finally:
+        vq.set_flags(old)
+
+
 def test_non_spin_conserving_excitations_use_number_sector():
     rng = np.random.default_rng(9)
     p = synth.random_problem(rng, 3, 2, 2)
