@@ -47,11 +47,13 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=None)
-    ap.add_argument("--workload", choices=["scan12", "warmstart", "config3", "config2", "q24"], default="scan12",
+    ap.add_argument("--workload", choices=["scan12", "warmstart", "config3", "config2", "q24", "adapt30"],
+                    default="scan12",
                     help="scan12: the throughput line (default); warmstart: the 16-qubit learned-warm-start "
                          "comparison (time to 1 mHa vs the plain HF start); config3: one 30-qubit instance; "
                          "config2: 256 uneven 14-20-qubit instances replayed from a CUDA graph; q24: one 24-qubit "
-                         "instance (10 electrons, 256 angles)")
+                         "instance (10 electrons, 256 angles); adapt30: ADAPT-VQE screening of the full "
+                         "3,500-operator pool at the 30-qubit state")
     ap.add_argument("--held-out", type=int, default=24, help="warmstart: held-out scan points compared")
     return ap.parse_args()
 
@@ -354,6 +356,68 @@ def run_large(args):
     print(json.dumps(line), flush=True)
 
 
+def measured_hbm_gbs():
+    """Copy bandwidth measured on this GPU type (MEASURED_PEAKS.json), else the
+    earlier GB300 measurement 6.8 TB/s; returns (GB/s, 'measured'|'fallback')."""
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as f:
+            return float(json.load(f)["hbm_gbs"]), "measured"
+    except (OSError, KeyError, ValueError):
+        return 6800.0, "fallback"
+
+
+def run_adapt(args):
+    """ADAPT-VQE screening at 30 qubits: psi = U(theta)|HF> of the 512-angle
+    state, lambda = H psi, and the gradient of every one of the 3,500 pool
+    operators (one vqe_pool_gradients call per step). The screening kernel's
+    own time is the call's time minus that of vqe_energy on the same state
+    (the same forward sweep and H psi launches), both CUDA-event timed."""
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_2311_01242_gb300 as vq
+
+    torch.cuda.set_device(0)
+    vq.load()
+    steps, warmup = min(args.steps, 10), max(3, min(args.warmup, 5))
+    t0 = time.perf_counter()
+    w = synth.config3()
+    p, exc, th = w.problems[0], w.excitations[0], w.thetas[0]
+    pool = synth.uccsd_pool(30, 10)
+    hf = synth.hf_bitstring(10)
+    H = vq.Hamiltonian.from_problem(p, w.drop_tol)
+    A = vq.Ansatz(30, hf, exc)
+    P = vq.Ansatz(30, hf, pool)
+    t_create = time.perf_counter() - t0
+    ws = vq.alloc_workspace(max(vq.pool_workspace_bytes(H, A, P), vq.workspace_bytes(H, A, vq.VQE_WS_ENERGY)))
+    theta = torch.as_tensor(th).cuda()
+    e_buf = torch.empty(1, dtype=torch.float64, device="cuda")
+    g_buf = torch.empty(len(pool), dtype=torch.float64, device="cuda")
+    ms_pool = _timed(lambda: vq.pool_gradients(H, A, P, theta, workspace=ws, out=(e_buf, g_buf)), steps, warmup)
+    ms_e = _timed(lambda: vq.energy(H, A, theta, workspace=ws), steps, warmup)
+    ms_step, ms_fwd_h = float(np.median(ms_pool)), float(np.median(ms_e))
+    ms_screen = max(ms_step - ms_fwd_h, 1e-6)
+    n_pairs = P.info()["n_pairs"]
+    # per pair: its rank-pair record (8 B) and psi, lambda at both ranks (4 x 8 B);
+    # the per-chunk partials (one double per 4,096 pairs) add under 0.01 %
+    alg_bytes = n_pairs * 40
+    achieved = alg_bytes / (ms_screen / 1e3) / 1e9
+    peak, src = measured_hbm_gbs()
+    line = {"metric": "ADAPT pool screening passes/s [adapt30]", "value": 1e3 / ms_step, "unit": "screens/s",
+            "n_gpus": 1, "steps": steps, "warmup": warmup, "ms_per_step": ms_step, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+            "config": {"workload": "30 qubits, 10 electrons, 512-angle state, 3,500-operator UCCSD pool "
+                                   f"({n_pairs} amplitude pairs)",
+                       "l2": "flushed between timed steps (512 MB write)", "create_seconds": t_create,
+                       "forward_and_hpsi_ms": ms_fwd_h, "screening_kernel_ms": ms_screen},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_source": src,
+                         "kernel": "k_pool_grad + k_pool_finalize"},
+            "gpu_launches_per_step": 2 * len(exc) + 8}
+    print(json.dumps(line), flush=True)
+
+
 def run_warmstart(args):
     """16 qubits, 8 electrons, 512-point scan r in [0.7, 4.0], 360 UCCSD angles:
     plain VQE with continuation on every 4th point trains the network; at
@@ -448,6 +512,10 @@ def main():
     if args.workload in ("config3", "config2", "q24"):
         if rank == 0:
             run_large(args)
+        return
+    if args.workload == "adapt30":
+        if rank == 0:
+            run_adapt(args)
         return
 
     import numpy as np

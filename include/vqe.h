@@ -221,6 +221,31 @@ int vqe_apply_hamiltonian(vqe_hamiltonian_t h, vqe_ansatz_t a, const double* psi
                           size_t workspace_bytes, vqe_stream_t stream);
 
 /*
+ * ADAPT-VQE operator screening (Sec. 2.2, ADAPT-VQE: the ansatz grows one pool
+ * operator at a time, chosen and stopped by the energy gradients with respect
+ * to the pool). For psi = U(theta)|HF> of ansatz a and lambda = H psi, writes
+ *   pool_grad_dev[j] = 2 Re <lambda| T_j - T_j^dagger |psi>,   j < n_pool,
+ * the derivative of E at angle 0 of pool operator j appended after U(theta),
+ * and energy_dev[0] = E(theta).
+ *   pool: an ansatz handle whose excitation list is the operator pool (its
+ *     angles are not used); it must have a's qubit count and sector (the same
+ *     electron count, and the same alpha/beta counts when a is spin-conserving),
+ *     else VQE_ERR_INVALID_ARG. Operators may repeat those of a.
+ *   theta_dev: a's n_params angles (may be NULL when a has none, the empty
+ *     starting ansatz of ADAPT).
+ *   pool_grad_dev: device, n_pool doubles, caller-owned (may be NULL when the
+ *     pool is empty).
+ *   workspace: vqe_pool_workspace_bytes(h, a, pool) bytes, 256-byte aligned
+ *     (the sector-compressed psi and lambda plus one partial per 4096 pairs of
+ *     the pool). Asynchronous on `stream`; allocates nothing, so it can be
+ *     captured in a CUDA graph. Deterministic: fixed reduction order.
+ */
+size_t vqe_pool_workspace_bytes(vqe_hamiltonian_t h, vqe_ansatz_t a, vqe_ansatz_t pool);
+int vqe_pool_gradients(vqe_hamiltonian_t h, vqe_ansatz_t a, vqe_ansatz_t pool,
+                       const double* theta_dev, double* energy_dev, double* pool_grad_dev,
+                       void* workspace, size_t workspace_bytes, vqe_stream_t stream);
+
+/*
  * A batch of independent instances (the paper runs hundreds of independent
  * simulation jobs over geometries and molecules, abstract and Sec. 4),
  * evaluated by one launch for instances that fit shared memory, and by

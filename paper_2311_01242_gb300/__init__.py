@@ -8,7 +8,8 @@ from .api import (Hamiltonian, Ansatz, Batch, VQEError, energy, energy_grad, sta
                   VQE_FLAG_FORCE_COMPLEX, VQE_FLAG_FORCE_STREAMING, VQE_FLAG_NO_CLUSTER, VQE_FLAG_FP64_SWEEPS,
                   VQE_FLAG_NO_STRINGS,
                   probe_fp64,
-                  GraphEnergyGrad, batched_workspace_bytes, energy_grad_batched)
+                  GraphEnergyGrad, batched_workspace_bytes, energy_grad_batched,
+                  pool_workspace_bytes, pool_gradients)
 from .autograd import VQEEnergy, vqe_energy
 
 __all__ = [
@@ -18,4 +19,5 @@ __all__ = [
     "VQE_WS_COMPLEX", "VQE_FLAG_FORCE_COMPLEX", "VQE_FLAG_FORCE_STREAMING", "VQE_FLAG_NO_CLUSTER", "VQE_FLAG_FP64_SWEEPS", "VQE_FLAG_NO_STRINGS",
     "probe_fp64",
     "GraphEnergyGrad", "batched_workspace_bytes", "energy_grad_batched",
+    "pool_workspace_bytes", "pool_gradients",
 ]

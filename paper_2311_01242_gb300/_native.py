@@ -17,7 +17,8 @@ _BUILD_DIR = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(_BUILD_DIR, "libvqe.so")
 HEADER = os.path.join(_ROOT, "include", "vqe.h")
 
-SOURCES = ["vqe_kernels.cu", "vqe_host.cpp", "vqe_static.cu", "vqe_mlp.cu", "vqe_probe.cu", "vqe_aux.cu"]
+SOURCES = ["vqe_kernels.cu", "vqe_host.cpp", "vqe_static.cu", "vqe_mlp.cu", "vqe_probe.cu", "vqe_aux.cu",
+           "vqe_pool.cu"]
 DEPS = SOURCES + ["vqe_internal.h"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ARCH + ["-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC"]
@@ -106,6 +107,8 @@ PROTOTYPES = {
     "vqe_energy_grad": (ctypes.c_int, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_sz, c_vp]),
     "vqe_state": (ctypes.c_int, [c_vp, c_vp, c_vp, c_vp, c_vp, c_sz, c_vp]),
     "vqe_apply_hamiltonian": (ctypes.c_int, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_sz, c_vp]),
+    "vqe_pool_workspace_bytes": (c_sz, [c_vp, c_vp, c_vp]),
+    "vqe_pool_gradients": (ctypes.c_int, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_sz, c_vp]),
     "vqe_create_batch": (ctypes.c_int, [ctypes.c_int, c_vp, c_vp, P(c_vp)]),
     "vqe_batch_max_params": (c_i32, [c_vp]),
     "vqe_batch_workspace_bytes": (c_sz, [c_vp, ctypes.c_int]),

@@ -233,6 +233,30 @@ def apply_hamiltonian(h, a, psi, workspace=None, stream=None):
     return lam, e[0]
 
 
+def pool_workspace_bytes(h, a, pool):
+    nb = _lib().vqe_pool_workspace_bytes(h.handle, a.handle, pool.handle)
+    if nb == 0:
+        raise VQEError(1, _lib().vqe_last_error().decode(errors="replace"))
+    return int(nb)
+
+
+def pool_gradients(h, a, pool, theta, workspace=None, stream=None, device="cuda", out=None):
+    """ADAPT screening (vqe_pool_gradients): (E(theta), g) with
+    g[j] = 2 Re <H psi| T_j - T_j^dagger |psi> for each operator of the pool
+    handle `pool` (an Ansatz over the same sector). out=(e[1], g[>=n_pool])."""
+    theta = _as_theta(theta, device)
+    if workspace is None:
+        workspace = alloc_workspace(pool_workspace_bytes(h, a, pool), theta.device)
+    if out is None:
+        e = torch.empty(1, dtype=torch.float64, device=theta.device)
+        g = torch.empty(max(pool.n_params, 1), dtype=torch.float64, device=theta.device)
+    else:
+        e, g = out
+    _check(_lib().vqe_pool_gradients(h.handle, a.handle, pool.handle, _ptr(theta) if a.n_params else None,
+                                     _ptr(e), _ptr(g), _ptr(workspace), workspace.numel(), _stream(stream)))
+    return e[0], g[:pool.n_params]
+
+
 def work_estimate(h, a, with_grad=True):
     f = ctypes.c_double()
     b = ctypes.c_double()

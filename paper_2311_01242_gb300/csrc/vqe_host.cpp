@@ -297,6 +297,8 @@ struct vqe_ansatz_s {
   int lo_bits = 0;                    // rank(k) = rank_hi[k >> lo_bits] + rank_lo[k & (2^lo_bits - 1)]
   std::vector<uint32_t> rank_hi, rank_lo;
   std::vector<uint2> rpairs;          // (rank(k) | sign << 31, rank(k ^ flip)) per pair
+  std::vector<int64_t> chunk_off;     // [M+1] pool screening: chunks of kPoolChunk pairs before gate m
+  int64_t* d_chunk_off = nullptr;
   uint32_t* d_rank_hi = nullptr;
   uint32_t* d_rank_lo = nullptr;
   uint2* d_rpairs = nullptr;
@@ -311,6 +313,7 @@ struct vqe_ansatz_s {
   ~vqe_ansatz_s() {
     dfree(d_gates);
     dfree(d_pair_off);
+    dfree(d_chunk_off);
     dfree(d_pairs);
     dfree(d_sector);
     dfree(d_rank_hi);
@@ -1448,9 +1451,14 @@ int vqe_create_ansatz(int n_qubits, uint64_t hf_bits, int32_t n_exc, const int32
   A->nb_rows.resize(size_t(n_exc) + 1);
   for (int m = 0; m < n_exc; ++m) A->nb_rows[m] = vqe::stream_grid(A->pair_off[m + 1] - A->pair_off[m]);
   A->nb_rows[n_exc] = vqe::stream_grid(int64_t(A->sector.size()));
+  A->chunk_off.assign(size_t(n_exc) + 1, 0);
+  for (int m = 0; m < n_exc; ++m)
+    A->chunk_off[m + 1] =
+        A->chunk_off[m] + (A->pair_off[m + 1] - A->pair_off[m] + vqe::kPoolChunk - 1) / vqe::kPoolChunk;
   int rc;
   if ((rc = upload(A->gates, &A->d_gates))) return rc;
   if ((rc = upload(A->pair_off, &A->d_pair_off))) return rc;
+  if ((rc = upload(A->chunk_off, &A->d_chunk_off))) return rc;
   if ((rc = upload(A->pairs, &A->d_pairs))) return rc;
   if ((rc = upload(A->sector, &A->d_sector))) return rc;
   if ((rc = upload(A->rank_hi, &A->d_rank_hi))) return rc;
@@ -1531,6 +1539,46 @@ int vqe_apply_hamiltonian(vqe_hamiltonian_t h, vqe_ansatz_t a, const double* psi
   cudaError_t ce = vqe::stream_apply_h(d, plan(a, e), buffers(ws, L), psi, lam_out, energy,
                                        static_cast<cudaStream_t>(stream));
   if (ce != cudaSuccess) return cuda_fail(ce, "apply_hamiltonian launch");
+  return VQE_OK;
+}
+
+size_t vqe_pool_workspace_bytes(vqe_hamiltonian_t h, vqe_ansatz_t a, vqe_ansatz_t pool) {
+  if (check_pair(h, a)) return 0;
+  if (!pool) {
+    fail(VQE_ERR_INVALID_ARG, "NULL pool handle");
+    return 0;
+  }
+  int rc = VQE_OK;
+  if (!get_ell(h, a, &rc)) return 0;
+  return ws_layout(a, !use_real(), false).total + align256(size_t(std::max<int64_t>(pool->chunk_off.back(), 1)) * 8);
+}
+
+int vqe_pool_gradients(vqe_hamiltonian_t h, vqe_ansatz_t a, vqe_ansatz_t pool, const double* theta, double* energy,
+                       double* pool_grad, void* ws, size_t ws_bytes, vqe_stream_t stream) {
+  int rc = check_pair(h, a);
+  if (rc) return rc;
+  if (!pool) return fail(VQE_ERR_INVALID_ARG, "NULL pool handle");
+  if (pool->n != a->n || pool->key() != a->key())
+    return fail(VQE_ERR_INVALID_ARG,
+                "pool sector differs from the ansatz's (same qubits, electrons and spin counts needed)");
+  if ((!theta && a->M > 0) || !energy || (!pool_grad && pool->M > 0))
+    return fail(VQE_ERR_INVALID_ARG, "NULL device pointer");
+  const auto* e = get_ell(h, a, &rc);
+  if (!e) return rc;
+  const bool real = use_real();
+  const WsLayout L = ws_layout(a, !real, false);
+  const int64_t n_chunks = pool->chunk_off.back();
+  const size_t need = L.total + align256(size_t(std::max<int64_t>(n_chunks, 1)) * 8);
+  if ((rc = check_ws(ws, ws_bytes, need))) return rc;
+  const cudaStream_t st = static_cast<cudaStream_t>(stream);
+  InstDesc d = make_desc(h, a, e, 0);
+  const vqe::StreamBuffers b = buffers(ws, L);
+  cudaError_t ce = vqe::stream_energy_grad(d, plan(a, e), b, real, false, theta, energy, nullptr, st);
+  if (ce != cudaSuccess) return cuda_fail(ce, "pool screening forward / H psi launch");
+  double* part = reinterpret_cast<double*>(static_cast<char*>(ws) + L.total);
+  ce = vqe::pool_gradients(pool->d_rpairs, pool->d_pair_off, pool->d_chunk_off, pool->M, n_chunks, real, b.psi,
+                           b.lam, part, pool_grad, st);
+  if (ce != cudaSuccess) return cuda_fail(ce, "pool screening launch");
   return VQE_OK;
 }
 

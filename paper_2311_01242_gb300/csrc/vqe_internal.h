@@ -17,6 +17,7 @@ constexpr uint32_t kEllPad = 0xFFFFFFFFu;   // empty connectivity slot
 constexpr int kResidentThreads = 512;
 constexpr int kStreamThreads = 256;
 constexpr int kMaxPartials = 1024;          // per-gate reduction partials (streaming)
+constexpr int kPoolChunk = 4096;            // pairs per partial sum of the pool screening
 
 // One X-mask group of the Hamiltonian. The group adds f(src) * psi[src] to
 // lambda[src ^ x]; u is the pattern of src on the group's pattern qubits
@@ -247,6 +248,13 @@ cudaError_t ell_device_count(const uint32_t* sector, int64_t D, const GroupRec* 
 cudaError_t ell_device_fill(const uint32_t* sector, int64_t D, const GroupRec* groups, int G,
                             const int32_t* order, int n_elec, int n_alpha, int W, uint16_t* ell,
                             cudaStream_t stream);
+
+// ADAPT pool screening (vqe_pool.cu): grad[m] = 2 Re <lam| T_m - T_m^dagger |psi>
+// over the M operators of a pool handle; chunk_off[m] = sum over operators
+// before m of ceil(pairs / kPoolChunk); part holds n_chunks = chunk_off[M] doubles.
+cudaError_t pool_gradients(const uint2* rpairs, const int64_t* pair_off, const int64_t* chunk_off, int M,
+                           int64_t n_chunks, bool real, const void* psi, const void* lam, double* part,
+                           double* grad, cudaStream_t stream);
 
 // Host helpers for the allocation-free entry point (vqe_static.cu).
 int prepare_noalloc(vqe_hamiltonian_s* h, vqe_ansatz_s* a, bool with_grad, InstDesc* d, StreamPlan* sp,
