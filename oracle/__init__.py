@@ -6,7 +6,8 @@ code with the CUDA library: it builds the Hamiltonian of Eq. 2 from integrals
 by literal creation/annihilation operators, has its own Jordan-Wigner mapping,
 applies excitation rotations U = exp(theta (T - T^dagger)) (Sec. 2.1.2) through
 the same ladder operators, and evaluates E(theta) of Eq. 1 as <psi|H|psi>.
-It also holds ADAPT-VQE's pool screening and adaptive loop (Sec. 2.2).
+It also holds ADAPT-VQE's pool screening and adaptive loop (Sec. 2.2) and
+pUCCD's hard-core boson form (Sec. 2.1.2).
 Everything is numpy/scipy in float64 / complex128, dense or plain sparse, with
 no blocking or fusion.
 
@@ -23,6 +24,8 @@ from .ansatz import (excitation_ops, apply_gate, apply_generator, prepare_state,
 from .vqe import (energy, energy_pauli, gradient_direct, gradient_shift,
                   gradient_fd, exact_ground_energy, run_bfgs, EnergyModel)
 from .adapt import pool_gradients, hf_pool_gradients, adapt_vqe
+from .hcb import (pair_basis, fermion_state, hcb_hamiltonian_matrix, HcbModel, hcb_gate,
+                  hcb_generator, hcb_state, hcb_energy_grad)
 
 __all__ = [
     "popcount", "ladder", "apply_string", "fermion_matrix_op", "hamiltonian_matrix",
@@ -31,4 +34,6 @@ __all__ = [
     "apply_generator", "prepare_state", "hf_state", "energy", "energy_pauli",
     "gradient_direct", "gradient_shift", "gradient_fd", "exact_ground_energy",
     "run_bfgs", "EnergyModel", "pool_gradients", "hf_pool_gradients", "adapt_vqe",
+    "pair_basis", "fermion_state", "hcb_hamiltonian_matrix", "HcbModel", "hcb_gate", "hcb_generator",
+    "hcb_state", "hcb_energy_grad",
 ]
