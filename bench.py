@@ -47,13 +47,16 @@ def parse():
     ap.add_argument("--impl", choices=["ours", "reference"], default="ours")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=None)
-    ap.add_argument("--workload", choices=["scan12", "warmstart", "config3", "config2", "q24", "adapt30"],
+    ap.add_argument("--workload", choices=["scan12", "warmstart", "config3", "config2", "q24", "adapt30",
+                                           "puccd11", "puccd24"],
                     default="scan12",
                     help="scan12: the throughput line (default); warmstart: the 16-qubit learned-warm-start "
                          "comparison (time to 1 mHa vs the plain HF start); config3: one 30-qubit instance; "
                          "config2: 256 uneven 14-20-qubit instances replayed from a CUDA graph; q24: one 24-qubit "
                          "instance (10 electrons, 256 angles); adapt30: ADAPT-VQE screening of the full "
-                         "3,500-operator pool at the 30-qubit state")
+                         "3,500-operator pool at the 30-qubit state; puccd11: pUCCD in the hard-core boson "
+                         "form, 11 orbitals x 64 geometries in one launch; puccd24: one 24-orbital pUCCD "
+                         "instance (12 pairs, 2.7M boson states)")
     ap.add_argument("--held-out", type=int, default=24, help="warmstart: held-out scan points compared")
     return ap.parse_args()
 
@@ -296,7 +299,37 @@ def run_large(args):
     vq.load()
     steps, warmup = min(args.steps, 20), max(3, min(args.warmup, 5))
     t0 = time.perf_counter()
-    if args.workload in ("config3", "q24"):
+    if args.workload in ("puccd11", "puccd24"):
+        if args.workload == "puccd11":
+            w = synth.puccd_scan()
+            pairs = synth.hcb_pairs_of(w.excitations[0])
+            hams = [vq.Hamiltonian.from_problem_hcb(p) for p in w.problems]
+            ans = [vq.Ansatz(11, 15, pairs, hcb=True)] * len(hams)
+            thetas = np.stack(w.thetas)
+            workload = "pUCCD hard-core boson form, 11 orbitals, 4 pairs, 28 angles, 64-geometry scan"
+            units, unit = len(hams), "evals/s"
+        else:
+            w = synth.puccd_large()
+            pairs = synth.hcb_pairs_of(w.excitations[0])
+            hams = [vq.Hamiltonian.from_problem_hcb(w.problems[0])]
+            ans = [vq.Ansatz(24, (1 << 12) - 1, pairs, hcb=True)]
+            thetas = w.thetas[0][None, :]
+            workload = "pUCCD hard-core boson form, 24 orbitals, 12 pairs (2.7M states), 144 angles"
+            units, unit = 1, "evals/s"
+        B = vq.Batch(hams, ans)
+        theta = torch.as_tensor(thetas).cuda().contiguous()
+        ws = vq.alloc_workspace(B.workspace_bytes(True))
+        e_buf = torch.empty(len(hams), dtype=torch.float64, device="cuda")
+        g_buf = torch.empty(len(hams), max(B.max_params, 1), dtype=torch.float64, device="cuda")
+        t_create = time.perf_counter() - t0
+        ms = _timed(lambda: B.energy_grad(theta, e_buf, g_buf, ws), steps, warmup)
+        flops = state_bytes = 0.0
+        for h, a in zip(hams, ans):
+            f, b = vq.work_estimate(h, a, True)
+            flops += f
+            state_bytes += b
+        launches = None
+    elif args.workload in ("config3", "q24"):
         if args.workload == "config3":
             w = synth.config3()
             p, exc, th, drop, nq = w.problems[0], w.excitations[0], w.thetas[0], w.drop_tol, 30
@@ -509,7 +542,7 @@ def main():
         if rank == 0:
             run_warmstart(args)
         return
-    if args.workload in ("config3", "config2", "q24"):
+    if args.workload in ("config3", "config2", "q24", "puccd11", "puccd24"):
         if rank == 0:
             run_large(args)
         return

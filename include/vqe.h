@@ -104,6 +104,23 @@ int vqe_jordan_wigner(int n_spatial, const double* h, const double* eri, double 
                       uint64_t* z_out, double* c_out, int64_t* n_out);
 
 /*
+ * pUCCD's hard-core boson form (Sec. 2.1.2, pUCCD: half the qubits of the
+ * other UCC ansatze): the block of Eq. 2 on seniority-zero determinants (every
+ * spatial orbital empty or doubly occupied) as a Pauli sum on n_spatial qubits,
+ * qubit p set when orbital p holds a pair. With the same h, eri layout as
+ * vqe_jordan_wigner and pair occupations n_p = (1 - Z_p)/2,
+ *   H = c0 + sum_p (2 h_pp + (pp|pp)) n_p
+ *          + sum_{p<q} 2 [2 (pp|qq) - (pq|qp)] n_p n_q
+ *          + sum_{p<q} (pq|pq) (X_p X_q + Y_p Y_q) / 2,
+ * exact on that block for real orbitals (pair moves p -> q carry sign +1 in the
+ * interleaved Jordan-Wigner order, so no Z strings appear). n_spatial 1..32;
+ * output, capacity and errors as vqe_jordan_wigner (terms sorted by (x, z)).
+ */
+int vqe_hcb_hamiltonian(int n_spatial, const double* h, const double* eri, double c0,
+                        double drop_tol, int64_t capacity, uint64_t* x_masks,
+                        uint64_t* z_masks, double* coefs, int64_t* n_out);
+
+/*
  * Qubit Hamiltonian from host arrays of n_terms Pauli terms (Eq. 1's H after
  * the mapping of Sec. 2.1.1). Equal (x, z) are merged, |coef| < drop_tol
  * dropped, and terms grouped by x_mask. Each group's terms are folded into
@@ -163,6 +180,19 @@ void vqe_destroy_hamiltonian(vqe_hamiltonian_t h);
  */
 int vqe_create_ansatz(int n_qubits, uint64_t hf_bits, int32_t n_exc,
                       const int32_t* excitations, vqe_ansatz_t* out);
+
+/*
+ * pUCCD ansatz in the hard-core boson form (Sec. 2.1.2, pUCCD) for a
+ * Hamiltonian from vqe_hcb_hamiltonian: n_exc pair excitations
+ * pairs[2m] = i -> pairs[2m+1] = a, each U_m = exp(theta_m (b+_a b_i - b+_i b_a))
+ * with no parity sign (hard-core bosons on different qubits commute);
+ * hf_bits: the doubly occupied orbitals of the reference. The state lives in
+ * the sector of popcount(hf_bits) occupied qubits. The handle works with every
+ * evaluation call (energy, gradient, batches, screening). Errors as
+ * vqe_create_ansatz (distinct qubits < n_qubits <= 32).
+ */
+int vqe_create_ansatz_hcb(int n_qubits, uint64_t hf_bits, int32_t n_exc, const int32_t* pairs,
+                          vqe_ansatz_t* out);
 
 /* Sector dimension, parameter count and number of (gate, amplitude-pair) units. */
 int vqe_ansatz_info(vqe_ansatz_t a, int* n_qubits, int32_t* n_params,

@@ -94,12 +94,15 @@ PROTOTYPES = {
     "vqe_last_error": (ctypes.c_char_p, []),
     "vqe_jordan_wigner": (ctypes.c_int, [ctypes.c_int, c_vp, c_vp, c_dbl, c_dbl, c_i64, c_vp, c_vp, c_vp,
                                          P(c_i64)]),
+    "vqe_hcb_hamiltonian": (ctypes.c_int, [ctypes.c_int, c_vp, c_vp, c_dbl, c_dbl, c_i64, c_vp, c_vp, c_vp,
+                                           P(c_i64)]),
     "vqe_create_hamiltonian": (ctypes.c_int, [ctypes.c_int, c_i64, c_vp, c_vp, c_vp, c_dbl, P(c_vp)]),
     "vqe_hamiltonian_info": (ctypes.c_int, [c_vp, P(ctypes.c_int), P(c_i64), P(c_i64), P(ctypes.c_int)]),
     "vqe_hamiltonian_terms": (ctypes.c_int, [c_vp, c_vp, c_vp, c_vp]),
     "vqe_set_coefs": (ctypes.c_int, [c_vp, c_vp, c_vp]),
     "vqe_destroy_hamiltonian": (None, [c_vp]),
     "vqe_create_ansatz": (ctypes.c_int, [ctypes.c_int, c_u64, c_i32, c_vp, P(c_vp)]),
+    "vqe_create_ansatz_hcb": (ctypes.c_int, [ctypes.c_int, c_u64, c_i32, c_vp, P(c_vp)]),
     "vqe_ansatz_info": (ctypes.c_int, [c_vp, P(ctypes.c_int), P(c_i32), P(c_i64), P(c_i64)]),
     "vqe_destroy_ansatz": (None, [c_vp]),
     "vqe_workspace_bytes": (c_sz, [c_vp, c_vp, ctypes.c_int]),

@@ -47,23 +47,31 @@ def set_flags(flags: int) -> int:
     return _lib().vqe_set_flags(int(flags))
 
 
-def jordan_wigner(n_spatial, h, eri, c0=0.0, drop_tol=1e-14):
-    """Pauli sum (x_masks, z_masks, coefs) of Eq. 2's Hamiltonian (library's own mapping)."""
+def _mapped_terms(fn, n_spatial, h, eri, c0, drop_tol):
     h = np.ascontiguousarray(h, dtype=np.float64)
     eri = np.ascontiguousarray(eri, dtype=np.float64)
     n = ctypes.c_int64(0)
-    lib = _lib()
-    rc = lib.vqe_jordan_wigner(int(n_spatial), _ptr(h), _ptr(eri), float(c0), float(drop_tol), 0,
-                               None, None, None, ctypes.byref(n))
+    rc = fn(int(n_spatial), _ptr(h), _ptr(eri), float(c0), float(drop_tol), 0, None, None, None, ctypes.byref(n))
     if rc not in (0, 1):
         _check(rc)
     cnt = n.value
     xs = np.zeros(cnt, dtype=np.uint64)
     zs = np.zeros(cnt, dtype=np.uint64)
     cs = np.zeros(cnt, dtype=np.float64)
-    _check(lib.vqe_jordan_wigner(int(n_spatial), _ptr(h), _ptr(eri), float(c0), float(drop_tol), cnt,
-                                 _ptr(xs), _ptr(zs), _ptr(cs), ctypes.byref(n)))
+    _check(fn(int(n_spatial), _ptr(h), _ptr(eri), float(c0), float(drop_tol), cnt, _ptr(xs), _ptr(zs), _ptr(cs),
+              ctypes.byref(n)))
     return xs, zs, cs
+
+
+def jordan_wigner(n_spatial, h, eri, c0=0.0, drop_tol=1e-14):
+    """Pauli sum (x_masks, z_masks, coefs) of Eq. 2's Hamiltonian (library's own mapping)."""
+    return _mapped_terms(_lib().vqe_jordan_wigner, n_spatial, h, eri, c0, drop_tol)
+
+
+def hcb_hamiltonian(n_spatial, h, eri, c0=0.0, drop_tol=1e-14):
+    """Pauli sum on n_spatial qubits of Eq. 2's seniority-zero block (pUCCD's
+    hard-core boson form, vqe_hcb_hamiltonian)."""
+    return _mapped_terms(_lib().vqe_hcb_hamiltonian, n_spatial, h, eri, c0, drop_tol)
 
 
 class Hamiltonian:
@@ -90,6 +98,12 @@ class Hamiltonian:
     @classmethod
     def from_problem(cls, problem, drop_tol=1e-14):
         return cls.from_integrals(problem.n_spatial, problem.h, problem.eri, problem.c0, drop_tol)
+
+    @classmethod
+    def from_problem_hcb(cls, problem, drop_tol=1e-14):
+        """Hard-core boson form on n_spatial qubits (pUCCD)."""
+        xs, zs, cs = hcb_hamiltonian(problem.n_spatial, problem.h, problem.eri, problem.c0, drop_tol)
+        return cls(problem.n_spatial, xs, zs, cs, drop_tol)
 
     def info(self):
         n = ctypes.c_int()
@@ -137,13 +151,15 @@ class Hamiltonian:
 
 
 class Ansatz:
-    """UCCSD-type ansatz handle (vqe_create_ansatz)."""
+    """UCCSD-type ansatz handle (vqe_create_ansatz); with hcb=True, pair
+    excitations (i, a) of pUCCD's hard-core boson form (vqe_create_ansatz_hcb)."""
 
-    def __init__(self, n_qubits, hf_bits, excitations):
-        exc = np.ascontiguousarray(np.asarray(excitations, dtype=np.int32).reshape(-1, 4))
+    def __init__(self, n_qubits, hf_bits, excitations, hcb=False):
+        exc = np.ascontiguousarray(np.asarray(excitations, dtype=np.int32).reshape(-1, 2 if hcb else 4))
         self._lib = _lib()
         a = ctypes.c_void_p()
-        _check(self._lib.vqe_create_ansatz(int(n_qubits), int(hf_bits), len(exc), _ptr(exc), ctypes.byref(a)))
+        create = self._lib.vqe_create_ansatz_hcb if hcb else self._lib.vqe_create_ansatz
+        _check(create(int(n_qubits), int(hf_bits), len(exc), _ptr(exc), ctypes.byref(a)))
         self.handle = a
         self.n_qubits = int(n_qubits)
         self.n_params = len(exc)

@@ -1034,6 +1034,56 @@ int vqe_jordan_wigner(int n_spatial, const double* h, const double* eri, double 
   return VQE_OK;
 }
 
+int vqe_hcb_hamiltonian(int n_spatial, const double* h, const double* eri, double c0, double drop_tol,
+                        int64_t capacity, uint64_t* x_out, uint64_t* z_out, double* c_out, int64_t* n_out) {
+  if (n_spatial < 1 || n_spatial > vqe::kMaxQubits) return fail(VQE_ERR_INVALID_ARG, "n_spatial must be 1..32");
+  if (!h || !eri || !n_out) return fail(VQE_ERR_INVALID_ARG, "NULL input");
+  if (!(drop_tol >= 0.0) || !std::isfinite(c0)) return fail(VQE_ERR_INVALID_ARG, "bad drop_tol or c0");
+  const int ns = n_spatial;
+  auto H = [&](int p, int q) { return h[p * ns + q]; };
+  auto V = [&](int p, int q, int r, int s) { return eri[((size_t(p) * ns + q) * ns + r) * ns + s]; };
+  for (size_t i = 0; i < size_t(ns) * ns; ++i)
+    if (!std::isfinite(h[i])) return fail(VQE_ERR_INVALID_ARG, "non-finite h");
+  for (size_t i = 0; i < size_t(ns) * ns * ns * ns; ++i)
+    if (!std::isfinite(eri[i])) return fail(VQE_ERR_INVALID_ARG, "non-finite eri");
+  // Seniority-zero block of Eq. 2 with pair occupations n_p = (1 - Z_p) / 2:
+  //   sum_p eps_p n_p + sum_{p<q} W_pq n_p n_q + sum_{p<q} K_pq (b+_p b_q + b+_q b_p),
+  //   eps_p = 2 h_pp + (pp|pp), W_pq = 2 [2 (pp|qq) - (pq|qp)], K_pq = (pq|pq),
+  //   b+_p b_q + b+_q b_p = (X_p X_q + Y_p Y_q) / 2.
+  std::map<std::pair<uint64_t, uint64_t>, double> acc;  // (x, z) -> coefficient
+  double id = c0;
+  for (int p = 0; p < ns; ++p) {
+    const double eps = 2.0 * H(p, p) + V(p, p, p, p);
+    id += 0.5 * eps;
+    acc[{0, uint64_t(1) << p}] -= 0.5 * eps;
+  }
+  for (int p = 0; p < ns; ++p)
+    for (int q = p + 1; q < ns; ++q) {
+      const uint64_t pq = (uint64_t(1) << p) | (uint64_t(1) << q);
+      const double W = 2.0 * (2.0 * V(p, p, q, q) - V(p, q, q, p));
+      id += 0.25 * W;
+      acc[{0, uint64_t(1) << p}] -= 0.25 * W;
+      acc[{0, uint64_t(1) << q}] -= 0.25 * W;
+      acc[{0, pq}] += 0.25 * W;
+      const double K = V(p, q, p, q);
+      acc[{pq, 0}] += 0.5 * K;
+      acc[{pq, pq}] += 0.5 * K;
+    }
+  acc[{0, 0}] += id;
+  std::vector<std::pair<std::pair<uint64_t, uint64_t>, double>> terms;
+  for (const auto& kv : acc)
+    if (kv.second != 0.0 && std::fabs(kv.second) >= drop_tol) terms.push_back(kv);
+  *n_out = int64_t(terms.size());
+  if (capacity < int64_t(terms.size()) || !x_out || !z_out || !c_out)
+    return fail(VQE_ERR_INVALID_ARG, "capacity too small: need " + std::to_string(terms.size()));
+  for (size_t i = 0; i < terms.size(); ++i) {
+    x_out[i] = terms[i].first.first;
+    z_out[i] = terms[i].first.second;
+    c_out[i] = terms[i].second;
+  }
+  return VQE_OK;
+}
+
 int vqe_create_hamiltonian(int n_qubits, int64_t n_terms, const uint64_t* xs, const uint64_t* zs,
                            const double* cs, double drop_tol, vqe_hamiltonian_t* out) {
   if (!out) return fail(VQE_ERR_INVALID_ARG, "NULL out");
@@ -1273,6 +1323,8 @@ void vqe_destroy_hamiltonian(vqe_hamiltonian_t h) {
   delete h;
 }
 
+static int finish_ansatz(std::unique_ptr<vqe_ansatz_s> A, const std::vector<uint32_t>& occv, vqe_ansatz_t* out);
+
 int vqe_create_ansatz(int n_qubits, uint64_t hf_bits, int32_t n_exc, const int32_t* exc,
                       vqe_ansatz_t* out) {
   if (!out) return fail(VQE_ERR_INVALID_ARG, "NULL out");
@@ -1288,6 +1340,7 @@ int vqe_create_ansatz(int n_qubits, uint64_t hf_bits, int32_t n_exc, const int32
   A->exc.assign(exc, exc + 4 * size_t(n_exc));
   A->n_elec = pc64(hf_bits);
   bool spin_ok = true;
+  std::vector<uint32_t> occv;
   for (int m = 0; m < n_exc; ++m) {
     const int32_t* e = exc + 4 * m;
     const bool single = e[2] < 0;
@@ -1314,6 +1367,7 @@ int vqe_create_ansatz(int n_qubits, uint64_t hf_bits, int32_t n_exc, const int32
       flip |= 1u << orb[i];
     }
     const uint32_t occ = single ? (1u << e[0]) : ((1u << e[0]) | (1u << e[1]));
+    occv.push_back(occ);
     const uint32_t vir = flip & ~occ;
     if (pc32(occ & 0x55555555u) != pc32(vir & 0x55555555u)) spin_ok = false;
     // sign of T on k0 = occ, applying the rightmost factor first
@@ -1334,6 +1388,15 @@ int vqe_create_ansatz(int n_qubits, uint64_t hf_bits, int32_t n_exc, const int32
     A->gates.push_back(g);
   }
   A->n_alpha = spin_ok ? pc32(uint32_t(hf_bits) & 0x55555555u) : -1;
+  return finish_ansatz(std::move(A), occv, out);
+}
+
+// Sector, pair lists, rank tables and device copies of an ansatz whose gates
+// (A->gates) and annihilated-orbital masks (occv) are set; A->n_alpha < 0
+// selects the electron-number sector, else the (N, N_alpha) spin sector.
+static int finish_ansatz(std::unique_ptr<vqe_ansatz_s> A, const std::vector<uint32_t>& occv, vqe_ansatz_t* out) {
+  const int n_qubits = A->n, n_exc = A->M;
+  const uint64_t full = (uint64_t(1) << n_qubits) - 1;
   // sector enumeration
   const int n = n_qubits;
   auto subsets = [](uint32_t pool, int c, std::vector<uint32_t>& outv) {
@@ -1386,11 +1449,7 @@ int vqe_create_ansatz(int n_qubits, uint64_t hf_bits, int32_t n_exc, const int32
   A->pair_off.assign(size_t(n_exc) + 1, 0);
   std::vector<std::vector<uint32_t>> per(n_exc);
   parallel_for(n_exc, [&](int64_t lo, int64_t hi) {
-    for (int64_t m = lo; m < hi; ++m) {
-      const int32_t* e = exc + 4 * m;
-      const uint32_t occ = (e[2] < 0) ? (1u << e[0]) : ((1u << e[0]) | (1u << e[1]));
-      enumerate(occ, A->gates[m].flip, per[m]);
-    }
+    for (int64_t m = lo; m < hi; ++m) enumerate(occv[size_t(m)], A->gates[m].flip, per[m]);
   });
   for (int m = 0; m < n_exc; ++m) A->pair_off[m + 1] = A->pair_off[m] + int64_t(per[m].size());
   A->pairs.resize(size_t(A->pair_off[n_exc]));
@@ -1475,6 +1534,37 @@ int vqe_create_ansatz(int n_qubits, uint64_t hf_bits, int32_t n_exc, const int32
   A->serial = next_serial();
   *out = A.release();
   return VQE_OK;
+}
+
+int vqe_create_ansatz_hcb(int n_qubits, uint64_t hf_bits, int32_t n_exc, const int32_t* pairs, vqe_ansatz_t* out) {
+  if (!out) return fail(VQE_ERR_INVALID_ARG, "NULL out");
+  *out = nullptr;
+  if (n_qubits < 1 || n_qubits > vqe::kMaxQubits) return fail(VQE_ERR_INVALID_ARG, "n_qubits must be 1..32");
+  const uint64_t full = (uint64_t(1) << n_qubits) - 1;
+  if (hf_bits & ~full) return fail(VQE_ERR_INVALID_ARG, "hf_bits has a bit >= n_qubits");
+  if (n_exc < 0 || (n_exc > 0 && !pairs)) return fail(VQE_ERR_INVALID_ARG, "bad pair-excitation list");
+  std::unique_ptr<vqe_ansatz_s> A(new vqe_ansatz_s);
+  A->n = n_qubits;
+  A->M = n_exc;
+  A->hf = hf_bits;
+  A->n_elec = pc64(hf_bits);  // boson (electron-pair) count
+  A->n_alpha = -1;            // sector: the number of occupied qubits only
+  std::vector<uint32_t> occv;
+  for (int m = 0; m < n_exc; ++m) {
+    const int i = pairs[2 * m], a = pairs[2 * m + 1];
+    if (i < 0 || i >= n_qubits || a < 0 || a >= n_qubits || i == a)
+      return fail(VQE_ERR_INVALID_ARG, "pair excitation " + std::to_string(m) + " needs two distinct qubits");
+    A->exc.insert(A->exc.end(), {i, a, -1, -1});
+    // b+_a b_i: hard-core bosons on different qubits commute, so no parity string
+    GateRec g;
+    g.flip = (1u << i) | (1u << a);
+    g.par = 0;
+    g.sign0 = 1;
+    g.pad = 0;
+    A->gates.push_back(g);
+    occv.push_back(1u << i);
+  }
+  return finish_ansatz(std::move(A), occv, out);
 }
 
 int vqe_ansatz_info(vqe_ansatz_t a, int* n_qubits, int32_t* n_params, int64_t* sector_dim, int64_t* n_pairs) {

@@ -12,6 +12,11 @@ config3: 30 qubits, 10 electrons, K=8, 512 excitations of a seeded shuffle of
          are dropped.
 config4: 16 qubits, 8 electrons, K=8, 512-point scan r in [0.7, 4.0], full pool
          (360 excitations), seed 4.
+puccd_scan: pUCCD at the CH3F frozen-core active-space size: 11 spatial
+         orbitals, 8 electrons (4 pairs), K=6, 64-point scan r in [0.8, 3.0],
+         the 28 pair excitations, theta ~ N(0, 0.05) per geometry, seed 5.
+puccd_large: pUCCD, 24 spatial orbitals, 24 electrons (12 pairs, 2.7M boson
+         states), K=8, the 144 pair excitations, theta ~ N(0, 0.05), seed 6.
 """
 from dataclasses import dataclass, field
 from typing import List
@@ -19,7 +24,7 @@ from typing import List
 import numpy as np
 
 from .integrals import Problem, random_problem, draw_scan, ScanProblem
-from .pools import uccsd_pool
+from .pools import uccsd_pool, puccd_pool
 
 
 @dataclass
@@ -101,3 +106,22 @@ def config4() -> Workload:
     scan = draw_scan(rng, 8, 8, 8, rs)
     exc = uccsd_pool(16, 8)
     return Workload("16 qubits scan, 512 points", [], [exc], [], scan=scan)
+
+
+def puccd_scan(n_geom: int = 64) -> Workload:
+    rng = np.random.default_rng(5)
+    rs = np.linspace(0.8, 3.0, 64)[:n_geom]
+    scan = draw_scan(rng, 11, 8, 6, rs)
+    exc = puccd_pool(22, 8)
+    thetas = rng.normal(0.0, 0.05, size=(64, len(exc)))[:n_geom]
+    probs = scan.problems()
+    return Workload("pUCCD, 11 orbitals x 64 geometries, 28 pair excitations", probs,
+                    [exc] * len(probs), list(thetas), scan=scan)
+
+
+def puccd_large() -> Workload:
+    rng = np.random.default_rng(6)
+    p = random_problem(rng, 24, 24, 8, label="puccd_large")
+    exc = puccd_pool(48, 24)
+    theta = rng.normal(0.0, 0.05, size=len(exc))
+    return Workload("pUCCD, 24 orbitals, 12 pairs, 144 pair excitations", [p], [exc], [theta])

@@ -72,3 +72,9 @@ def puccd_pool(n_qubits: int, n_elec: int):
 def hcb_pair_pool(n_s: int, n_pairs: int):
     """pUCCD pair excitations i -> a (i < n_pairs <= a) as (i, a) on n_s boson qubits."""
     return np.array([(i, a) for i in range(n_pairs) for a in range(n_pairs, n_s)], dtype=np.int32).reshape(-1, 2)
+
+
+def hcb_pairs_of(puccd_excitations):
+    """(i, a) boson pairs of fermionic pair doubles (2i, 2i+1, 2a, 2a+1)."""
+    e = np.asarray(puccd_excitations, dtype=np.int32).reshape(-1, 4)
+    return np.ascontiguousarray(e[:, [0, 2]] // 2)

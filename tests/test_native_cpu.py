@@ -106,3 +106,29 @@ def test_mlp_param_count_matches_oracle_layout(lib):
         assert lib.vqe_mlp_param_count(*dims) == omlp.layout(*dims)[1]
     assert lib.vqe_mlp_param_count(9, 20, 5) == 0  # hidden width must be a multiple of 16
     assert lib.vqe_mlp_workspace_bytes(128, 9, 256, 360) > 0
+
+
+@pytest.mark.parametrize("seed,n_s,n_pairs", [(90, 2, 1), (91, 4, 2), (92, 6, 3), (93, 7, 2)])
+def test_hcb_hamiltonian_matches_oracle_block(lib, seed, n_s, n_pairs):
+    """vqe_hcb_hamiltonian's Pauli sum, restricted to n_pairs occupied qubits,
+    equals the oracle's seniority-zero block of Eq. 2 (built from the ladder
+    operators), and it conserves the pair number."""
+    prob = synth.random_problem(np.random.default_rng(seed), n_s, 2 * n_pairs, 3)
+    prob.c0 = 0.25
+    xs, zs, cs = api.hcb_hamiltonian(n_s, prob.h, prob.eri, prob.c0)
+    dense = oracle.pauli_sum_dense(xs, zs, cs, n_s)
+    block, bos = oracle.hcb_hamiltonian_matrix(prob, n_pairs)
+    idx = bos.astype(np.int64)
+    assert np.abs(dense[np.ix_(idx, idx)] - block.toarray()).max() < 1e-12
+    ks = np.arange(1 << n_s)
+    pc = np.array([bin(k).count("1") for k in ks])
+    assert np.abs(dense[pc[:, None] != pc[None, :]]).max() == 0.0
+
+
+def test_hcb_ansatz_rejects_bad_pairs(lib):
+    a = ctypes.c_void_p()
+    pairs = np.array([[1, 1]], dtype=np.int32)
+    assert lib.vqe_create_ansatz_hcb(4, 3, 1, api._ptr(pairs), ctypes.byref(a)) == 1
+    pairs = np.array([[0, 9]], dtype=np.int32)
+    assert lib.vqe_create_ansatz_hcb(4, 3, 1, api._ptr(pairs), ctypes.byref(a)) == 1
+    assert lib.vqe_create_ansatz_hcb(33, 3, 0, None, ctypes.byref(a)) == 1
