@@ -6,8 +6,9 @@ code with the CUDA library: it builds the Hamiltonian of Eq. 2 from integrals
 by literal creation/annihilation operators, has its own Jordan-Wigner mapping,
 applies excitation rotations U = exp(theta (T - T^dagger)) (Sec. 2.1.2) through
 the same ladder operators, and evaluates E(theta) of Eq. 1 as <psi|H|psi>.
-It also holds ADAPT-VQE's pool screening and adaptive loop (Sec. 2.2) and
-pUCCD's hard-core boson form (Sec. 2.1.2).
+It also holds ADAPT-VQE's pool screening and adaptive loop (Sec. 2.1.1) and
+pUCCD's hard-core boson form (Sec. 2.1.2), and the frozen-core folding of
+Eq. 3 (Sec. 2.1.3).
 Everything is numpy/scipy in float64 / complex128, dense or plain sparse, with
 no blocking or fusion.
 
@@ -24,6 +25,7 @@ from .ansatz import (excitation_ops, apply_gate, apply_generator, prepare_state,
 from .vqe import (energy, energy_pauli, gradient_direct, gradient_shift,
                   gradient_fd, exact_ground_energy, run_bfgs, EnergyModel)
 from .adapt import pool_gradients, hf_pool_gradients, adapt_vqe
+from .frozen import fold_frozen
 from .hcb import (pair_basis, fermion_state, hcb_hamiltonian_matrix, HcbModel, hcb_gate,
                   hcb_generator, hcb_state, hcb_energy_grad)
 
@@ -35,5 +37,5 @@ __all__ = [
     "gradient_direct", "gradient_shift", "gradient_fd", "exact_ground_energy",
     "run_bfgs", "EnergyModel", "pool_gradients", "hf_pool_gradients", "adapt_vqe",
     "pair_basis", "fermion_state", "hcb_hamiltonian_matrix", "HcbModel", "hcb_gate", "hcb_generator",
-    "hcb_state", "hcb_energy_grad",
+    "hcb_state", "hcb_energy_grad", "fold_frozen",
 ]
