@@ -251,7 +251,7 @@ int vqe_apply_hamiltonian(vqe_hamiltonian_t h, vqe_ansatz_t a, const double* psi
                           size_t workspace_bytes, vqe_stream_t stream);
 
 /*
- * ADAPT-VQE operator screening (Sec. 2.2, ADAPT-VQE: the ansatz grows one pool
+ * ADAPT-VQE operator screening (Sec. 2.1.1, ADAPT-VQE: the ansatz grows one pool
  * operator at a time, chosen and stopped by the energy gradients with respect
  * to the pool). For psi = U(theta)|HF> of ansatz a and lambda = H psi, writes
  *   pool_grad_dev[j] = 2 Re <lambda| T_j - T_j^dagger |psi>,   j < n_pool,

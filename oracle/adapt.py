@@ -1,4 +1,4 @@
-"""ADAPT-VQE operator screening and the adaptive loop (Sec. 2.2, ADAPT-VQE).
+"""ADAPT-VQE operator screening and the adaptive loop (Sec. 2.1.1, ADAPT-VQE).
 
 ADAPT grows the ansatz one operator at a time from a pool: each round it
 measures, for every pool operator A_j = T_j - T_j^dagger, the derivative of the

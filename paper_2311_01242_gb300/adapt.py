@@ -1,4 +1,4 @@
-"""ADAPT-VQE (Sec. 2.2, ADAPT-VQE) over the library's screening and
+"""ADAPT-VQE (Sec. 2.1.1, ADAPT-VQE) over the library's screening and
 energy+gradient calls.
 
 Each round screens the whole pool with one vqe_pool_gradients call (forward

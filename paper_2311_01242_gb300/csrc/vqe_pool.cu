@@ -1,4 +1,4 @@
-// ADAPT-VQE operator screening (Sec. 2.2, ADAPT-VQE): after the forward sweep
+// ADAPT-VQE operator screening (Sec. 2.1.1, ADAPT-VQE): after the forward sweep
 // and H psi, the energy gradient of every pool operator appended at angle 0,
 //   g_j = 2 Re <lambda| T_j - T_j^dagger |psi>,   lambda = H psi,
 // in one launch over the pool's amplitude pairs plus one finalising launch.

@@ -1,4 +1,4 @@
-"""ADAPT-VQE screening (Sec. 2.2, ADAPT-VQE) through the C ABI against the oracle.
+"""ADAPT-VQE screening (Sec. 2.1.1, ADAPT-VQE) through the C ABI against the oracle.
 
 vqe_pool_gradients returns E(theta) and g_j = 2 Re <H psi| T_j - T_j^dagger |psi>
 for every operator of a pool. Bar: |dE| <= 1e-10 Ha, |dg_j| <= 1e-9, as for the

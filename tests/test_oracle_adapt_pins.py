@@ -1,4 +1,4 @@
-"""Pins of the oracle's ADAPT-VQE screening (Sec. 2.2, ADAPT-VQE) against facts
+"""Pins of the oracle's ADAPT-VQE screening (Sec. 2.1.1, ADAPT-VQE) against facts
 fixed outside it: the exact four-point shift rule of the extended ansatz, the
 Slater-Condon closed form at the reference state, the identity between the pool
 gradient of the last gate's own operator and that gate's angle derivative, and
