@@ -104,6 +104,24 @@ int vqe_jordan_wigner(int n_spatial, const double* h, const double* eri, double 
                       uint64_t* z_out, double* c_out, int64_t* n_out);
 
 /*
+ * Frozen-core folding (Sec. 2.1.3, Eq. 3), host only, synchronous: the
+ * integrals of a smaller problem on the active spatial orbitals, with the
+ * frozen ones doubly occupied in every determinant. Same h, eri layout as
+ * vqe_jordan_wigner; frozen[n_frozen] and active[n_active] list distinct
+ * orbitals < n_spatial (active in the order of the new problem).
+ *   h_out[x*n_active+y] = h[p][q] + sum_{c frozen} (2 (pq|cc) - (pc|cq)),
+ *       p = active[x], q = active[y];
+ *   eri_out = eri on the active orbitals;
+ *   *c0_out = c0 + sum_{c frozen} 2 h_cc + sum_{c,d frozen} (2 (cc|dd) - (cd|dc)).
+ * Eq. 3's constant lists only the one-body core sum; the core-core two-body
+ * energy is part of it as well (without it the folded energies shift by a
+ * constant). Returns VQE_ERR_INVALID_ARG for bad counts, indices or NULLs.
+ */
+int vqe_fold_frozen(int n_spatial, const double* h, const double* eri, double c0, int n_frozen,
+                    const int32_t* frozen, int n_active, const int32_t* active, double* h_out,
+                    double* eri_out, double* c0_out);
+
+/*
  * pUCCD's hard-core boson form (Sec. 2.1.2, pUCCD: half the qubits of the
  * other UCC ansatze): the block of Eq. 2 on seniority-zero determinants (every
  * spatial orbital empty or doubly occupied) as a Pauli sum on n_spatial qubits,

@@ -94,6 +94,8 @@ PROTOTYPES = {
     "vqe_last_error": (ctypes.c_char_p, []),
     "vqe_jordan_wigner": (ctypes.c_int, [ctypes.c_int, c_vp, c_vp, c_dbl, c_dbl, c_i64, c_vp, c_vp, c_vp,
                                          P(c_i64)]),
+    "vqe_fold_frozen": (ctypes.c_int, [ctypes.c_int, c_vp, c_vp, c_dbl, ctypes.c_int, c_vp, ctypes.c_int, c_vp,
+                                       c_vp, c_vp, P(c_dbl)]),
     "vqe_hcb_hamiltonian": (ctypes.c_int, [ctypes.c_int, c_vp, c_vp, c_dbl, c_dbl, c_i64, c_vp, c_vp, c_vp,
                                            P(c_i64)]),
     "vqe_create_hamiltonian": (ctypes.c_int, [ctypes.c_int, c_i64, c_vp, c_vp, c_vp, c_dbl, P(c_vp)]),

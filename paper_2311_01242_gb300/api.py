@@ -68,6 +68,22 @@ def jordan_wigner(n_spatial, h, eri, c0=0.0, drop_tol=1e-14):
     return _mapped_terms(_lib().vqe_jordan_wigner, n_spatial, h, eri, c0, drop_tol)
 
 
+def fold_frozen(h, eri, c0, frozen, active):
+    """Frozen-core folding of Eq. 3 (vqe_fold_frozen): (h', eri', c0') on the
+    active orbitals, in the order given."""
+    h = np.ascontiguousarray(h, dtype=np.float64)
+    eri = np.ascontiguousarray(eri, dtype=np.float64)
+    fr = np.ascontiguousarray(frozen, dtype=np.int32)
+    ac = np.ascontiguousarray(active, dtype=np.int32)
+    na = len(ac)
+    h_out = np.zeros((na, na))
+    eri_out = np.zeros((na,) * 4)
+    c0_out = ctypes.c_double()
+    _check(_lib().vqe_fold_frozen(h.shape[0], _ptr(h), _ptr(eri), float(c0), len(fr), _ptr(fr) if len(fr) else None,
+                                  na, _ptr(ac) if na else None, _ptr(h_out), _ptr(eri_out), ctypes.byref(c0_out)))
+    return h_out, eri_out, c0_out.value
+
+
 def hcb_hamiltonian(n_spatial, h, eri, c0=0.0, drop_tol=1e-14):
     """Pauli sum on n_spatial qubits of Eq. 2's seniority-zero block (pUCCD's
     hard-core boson form, vqe_hcb_hamiltonian)."""

@@ -1034,6 +1034,50 @@ int vqe_jordan_wigner(int n_spatial, const double* h, const double* eri, double 
   return VQE_OK;
 }
 
+int vqe_fold_frozen(int n_spatial, const double* h, const double* eri, double c0, int n_frozen,
+                    const int32_t* frozen, int n_active, const int32_t* active, double* h_out, double* eri_out,
+                    double* c0_out) {
+  if (n_spatial < 1 || n_frozen < 0 || n_active < 0 || n_frozen + n_active > n_spatial)
+    return fail(VQE_ERR_INVALID_ARG, "bad orbital counts");
+  if (!h || !eri || !c0_out || (n_frozen > 0 && !frozen) || (n_active > 0 && (!active || !h_out || !eri_out)))
+    return fail(VQE_ERR_INVALID_ARG, "NULL input");
+  std::vector<char> seen(size_t(n_spatial), 0);
+  for (int i = 0; i < n_frozen + n_active; ++i) {
+    const int o = i < n_frozen ? frozen[i] : active[i - n_frozen];
+    if (o < 0 || o >= n_spatial || seen[size_t(o)]) return fail(VQE_ERR_INVALID_ARG, "orbital out of range or listed twice");
+    seen[size_t(o)] = 1;
+  }
+  const size_t ns = size_t(n_spatial);
+  auto H = [&](int p, int q) { return h[size_t(p) * ns + size_t(q)]; };
+  auto V = [&](int p, int q, int r, int t) { return eri[((size_t(p) * ns + size_t(q)) * ns + size_t(r)) * ns + size_t(t)]; };
+  // core energy: one-body and the frozen pairs' mutual Coulomb minus exchange
+  double e = c0;
+  for (int i = 0; i < n_frozen; ++i) {
+    const int c = frozen[i];
+    e += 2.0 * H(c, c);
+    for (int j = 0; j < n_frozen; ++j) {
+      const int d = frozen[j];
+      e += 2.0 * V(c, c, d, d) - V(c, d, d, c);
+    }
+  }
+  // effective one-body term on the active orbitals (Eq. 3's fold over the core)
+  const size_t na = size_t(n_active);
+  for (size_t x = 0; x < na; ++x)
+    for (size_t y = 0; y < na; ++y) {
+      const int p = active[x], q = active[y];
+      double v = H(p, q);
+      for (int i = 0; i < n_frozen; ++i) v += 2.0 * V(p, q, frozen[i], frozen[i]) - V(p, frozen[i], frozen[i], q);
+      h_out[x * na + y] = v;
+    }
+  for (size_t a = 0; a < na; ++a)
+    for (size_t b = 0; b < na; ++b)
+      for (size_t c = 0; c < na; ++c)
+        for (size_t d = 0; d < na; ++d)
+          eri_out[((a * na + b) * na + c) * na + d] = V(active[a], active[b], active[c], active[d]);
+  *c0_out = e;
+  return VQE_OK;
+}
+
 int vqe_hcb_hamiltonian(int n_spatial, const double* h, const double* eri, double c0, double drop_tol,
                         int64_t capacity, uint64_t* x_out, uint64_t* z_out, double* c_out, int64_t* n_out) {
   if (n_spatial < 1 || n_spatial > vqe::kMaxQubits) return fail(VQE_ERR_INVALID_ARG, "n_spatial must be 1..32");

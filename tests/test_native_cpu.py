@@ -132,3 +132,26 @@ def test_hcb_ansatz_rejects_bad_pairs(lib):
     pairs = np.array([[0, 9]], dtype=np.int32)
     assert lib.vqe_create_ansatz_hcb(4, 3, 1, api._ptr(pairs), ctypes.byref(a)) == 1
     assert lib.vqe_create_ansatz_hcb(33, 3, 0, None, ctypes.byref(a)) == 1
+
+
+@pytest.mark.parametrize("seed,n_s,n_elec,frozen,active", [(120, 5, 6, [0], [1, 2, 3, 4]),
+                                                           (121, 6, 8, [0, 1], [2, 3, 4, 5]),
+                                                           (122, 6, 6, [0, 2], [1, 3, 5]),
+                                                           (123, 4, 4, [], [3, 1, 0, 2])])
+def test_fold_frozen_matches_oracle(lib, seed, n_s, n_elec, frozen, active):
+    prob = synth.random_problem(np.random.default_rng(seed), n_s, n_elec, 3)
+    prob.c0 = -0.5
+    h2, e2, c2 = api.fold_frozen(prob.h, prob.eri, prob.c0, frozen, active)
+    red = oracle.fold_frozen(prob, frozen, active)
+    assert np.abs(h2 - red.h).max() < 1e-13
+    assert np.array_equal(e2, red.eri)
+    assert abs(c2 - red.c0) < 1e-12
+
+
+def test_fold_frozen_rejects_overlap_and_range(lib):
+    h = np.zeros((3, 3))
+    e = np.zeros((3, 3, 3, 3))
+    with pytest.raises(api.VQEError):
+        api.fold_frozen(h, e, 0.0, [0], [0, 1])
+    with pytest.raises(api.VQEError):
+        api.fold_frozen(h, e, 0.0, [5], [0, 1])
