@@ -284,8 +284,8 @@ int vqe_apply_hamiltonian(vqe_hamiltonian_t h, vqe_ansatz_t a, const double* psi
  *   pool_grad_dev: device, n_pool doubles, caller-owned (may be NULL when the
  *     pool is empty).
  *   workspace: vqe_pool_workspace_bytes(h, a, pool) bytes, 256-byte aligned
- *     (the sector-compressed psi and lambda plus one partial per 4096 pairs of
- *     the pool). Asynchronous on `stream`; allocates nothing, so it can be
+ *     (the sector-compressed psi and lambda, a copy of both side by side, and
+ *     one partial per 4096 pairs of the pool). Asynchronous on `stream`; allocates nothing, so it can be
  *     captured in a CUDA graph. Deterministic: fixed reduction order.
  */
 size_t vqe_pool_workspace_bytes(vqe_hamiltonian_t h, vqe_ansatz_t a, vqe_ansatz_t pool);

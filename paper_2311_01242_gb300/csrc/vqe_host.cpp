@@ -1684,7 +1684,9 @@ size_t vqe_pool_workspace_bytes(vqe_hamiltonian_t h, vqe_ansatz_t a, vqe_ansatz_
   }
   int rc = VQE_OK;
   if (!get_ell(h, a, &rc)) return 0;
-  return ws_layout(a, !use_real(), false).total + align256(size_t(std::max<int64_t>(pool->chunk_off.back(), 1)) * 8);
+  const bool real = use_real();
+  return ws_layout(a, !real, false).total + align256(size_t(std::max<int64_t>(pool->chunk_off.back(), 1)) * 8) +
+         align256(std::max<size_t>(a->sector.size(), 1) * (real ? 16 : 32));
 }
 
 int vqe_pool_gradients(vqe_hamiltonian_t h, vqe_ansatz_t a, vqe_ansatz_t pool, const double* theta, double* energy,
@@ -1702,7 +1704,8 @@ int vqe_pool_gradients(vqe_hamiltonian_t h, vqe_ansatz_t a, vqe_ansatz_t pool, c
   const bool real = use_real();
   const WsLayout L = ws_layout(a, !real, false);
   const int64_t n_chunks = pool->chunk_off.back();
-  const size_t need = L.total + align256(size_t(std::max<int64_t>(n_chunks, 1)) * 8);
+  const size_t part_bytes = align256(size_t(std::max<int64_t>(n_chunks, 1)) * 8);
+  const size_t need = L.total + part_bytes + align256(std::max<size_t>(a->sector.size(), 1) * (real ? 16 : 32));
   if ((rc = check_ws(ws, ws_bytes, need))) return rc;
   const cudaStream_t st = static_cast<cudaStream_t>(stream);
   InstDesc d = make_desc(h, a, e, 0);
@@ -1710,8 +1713,9 @@ int vqe_pool_gradients(vqe_hamiltonian_t h, vqe_ansatz_t a, vqe_ansatz_t pool, c
   cudaError_t ce = vqe::stream_energy_grad(d, plan(a, e), b, real, false, theta, energy, nullptr, st);
   if (ce != cudaSuccess) return cuda_fail(ce, "pool screening forward / H psi launch");
   double* part = reinterpret_cast<double*>(static_cast<char*>(ws) + L.total);
+  void* pl = static_cast<char*>(ws) + L.total + part_bytes;
   ce = vqe::pool_gradients(pool->d_rpairs, pool->d_pair_off, pool->d_chunk_off, pool->M, n_chunks, real, b.psi,
-                           b.lam, part, pool_grad, st);
+                           b.lam, int64_t(a->sector.size()), pl, part, pool_grad, st);
   if (ce != cudaSuccess) return cuda_fail(ce, "pool screening launch");
   return VQE_OK;
 }

@@ -251,10 +251,11 @@ cudaError_t ell_device_fill(const uint32_t* sector, int64_t D, const GroupRec* g
 
 // ADAPT pool screening (vqe_pool.cu): grad[m] = 2 Re <lam| T_m - T_m^dagger |psi>
 // over the M operators of a pool handle; chunk_off[m] = sum over operators
-// before m of ceil(pairs / kPoolChunk); part holds n_chunks = chunk_off[M] doubles.
+// before m of ceil(pairs / kPoolChunk); part holds n_chunks = chunk_off[M] doubles;
+// pl (16-byte aligned) receives psi and lam side by side, D * 2 amplitudes.
 cudaError_t pool_gradients(const uint2* rpairs, const int64_t* pair_off, const int64_t* chunk_off, int M,
-                           int64_t n_chunks, bool real, const void* psi, const void* lam, double* part,
-                           double* grad, cudaStream_t stream);
+                           int64_t n_chunks, bool real, const void* psi, const void* lam, int64_t D, void* pl,
+                           double* part, double* grad, cudaStream_t stream);
 
 // Host helpers for the allocation-free entry point (vqe_static.cu).
 int prepare_noalloc(vqe_hamiltonian_s* h, vqe_ansatz_s* a, bool with_grad, InstDesc* d, StreamPlan* sp,

@@ -10,6 +10,10 @@
 // the sign in bit 31), so psi and lambda are read in the compressed sector
 // layout the streaming kernels leave them in.
 //
+// psi and lambda are first copied side by side (entry r = {psi[r], lambda[r]}),
+// so each rank of a pair costs one 16-byte (real) or 32-byte (complex) gather
+// from one L2 sector instead of two gathers from two sectors.
+//
 // Work split: operator j's pairs are cut into chunks of kPoolChunk; a block
 // sums one chunk (thread-strided, then a fixed shuffle/shared-memory tree) and
 // writes one partial; the finaliser adds operator j's partials in chunk order.
@@ -51,11 +55,32 @@ __device__ __forceinline__ int owner_of(const int64_t* __restrict__ chunk_off, i
   return lo;
 }
 
+// psi and lambda of one sector entry, side by side
+template <typename T> struct alignas(2 * sizeof(T)) PsiLam {
+  T p, l;
+};
+
+__device__ __forceinline__ PsiLam<double> load_pl(const PsiLam<double>* v) {
+  const double2 t = __ldg(reinterpret_cast<const double2*>(v));
+  return {t.x, t.y};
+}
+__device__ __forceinline__ PsiLam<double2> load_pl(const PsiLam<double2>* v) {
+  const double2* q = reinterpret_cast<const double2*>(v);
+  return {__ldg(q), __ldg(q + 1)};
+}
+
+template <typename T>
+__global__ void k_interleave(const T* __restrict__ psi, const T* __restrict__ lam, int64_t D,
+                             PsiLam<T>* __restrict__ out) {
+  for (int64_t r = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; r < D; r += int64_t(gridDim.x) * blockDim.x)
+    out[r] = PsiLam<T>{psi[r], lam[r]};
+}
+
 template <typename T>
 __global__ void __launch_bounds__(kPoolThreads) k_pool_grad(const uint2* __restrict__ rp,
                                                             const int64_t* __restrict__ pair_off,
                                                             const int64_t* __restrict__ chunk_off, int M,
-                                                            const T* __restrict__ psi, const T* __restrict__ lam,
+                                                            const PsiLam<T>* __restrict__ pl,
                                                             double* __restrict__ part) {
   __shared__ double red[kPoolThreads / 32];
   const int64_t n_chunks = __ldg(chunk_off + M);
@@ -72,19 +97,16 @@ __global__ void __launch_bounds__(kPoolThreads) k_pool_grad(const uint2* __restr
         const int64_t p = base + int64_t(u) * kPoolThreads;
         pr[u] = p < p1 ? __ldg(rp + p) : make_uint2(0u, 0u);
       }
-      T pa[kPoolUnroll], pb[kPoolUnroll], la[kPoolUnroll], lb[kPoolUnroll];
+      PsiLam<T> a[kPoolUnroll], b[kPoolUnroll];
 #pragma unroll
       for (int u = 0; u < kPoolUnroll; ++u) {
-        const uint32_t ra = pr[u].x & 0x7fffffffu, rb = pr[u].y;
-        pa[u] = __ldg(psi + ra);
-        pb[u] = __ldg(psi + rb);
-        la[u] = __ldg(lam + ra);
-        lb[u] = __ldg(lam + rb);
+        a[u] = load_pl(pl + (pr[u].x & 0x7fffffffu));
+        b[u] = load_pl(pl + pr[u].y);
       }
 #pragma unroll
       for (int u = 0; u < kPoolUnroll; ++u) {
         const int64_t p = base + int64_t(u) * kPoolThreads;
-        if (p < p1) acc += flip_sign(pair_term(lb[u], pa[u], la[u], pb[u]), pr[u].x >> 31);
+        if (p < p1) acc += flip_sign(pair_term(b[u].l, a[u].p, a[u].l, b[u].p), pr[u].x >> 31);
       }
     }
 #pragma unroll
@@ -117,8 +139,8 @@ __global__ void k_pool_finalize(const double* __restrict__ part, const int64_t* 
 }  // namespace
 
 cudaError_t pool_gradients(const uint2* rpairs, const int64_t* pair_off, const int64_t* chunk_off, int M,
-                           int64_t n_chunks, bool real, const void* psi, const void* lam, double* part,
-                           double* grad, cudaStream_t stream) {
+                           int64_t n_chunks, bool real, const void* psi, const void* lam, int64_t D, void* pl,
+                           double* part, double* grad, cudaStream_t stream) {
   if (M <= 0) return cudaSuccess;
   if (n_chunks > 0) {
     int dev = 0, sms = 0;
@@ -128,14 +150,19 @@ cudaError_t pool_gradients(const uint2* rpairs, const int64_t* pair_off, const i
     if (e != cudaSuccess) return e;
     const int64_t cap = int64_t(sms) * 8;  // 8 resident blocks of 256 threads per SM
     const unsigned grid = unsigned(n_chunks < cap ? n_chunks : cap);
-    if (real)
-      k_pool_grad<double><<<grid, kPoolThreads, 0, stream>>>(rpairs, pair_off, chunk_off, M,
-                                                             static_cast<const double*>(psi),
-                                                             static_cast<const double*>(lam), part);
-    else
-      k_pool_grad<double2><<<grid, kPoolThreads, 0, stream>>>(rpairs, pair_off, chunk_off, M,
-                                                              static_cast<const double2*>(psi),
-                                                              static_cast<const double2*>(lam), part);
+    const int64_t ib = (D + 255) / 256;
+    const unsigned igrid = unsigned(ib < cap ? ib : cap);
+    if (real) {
+      auto* v = static_cast<PsiLam<double>*>(pl);
+      k_interleave<double><<<igrid, 256, 0, stream>>>(static_cast<const double*>(psi),
+                                                      static_cast<const double*>(lam), D, v);
+      k_pool_grad<double><<<grid, kPoolThreads, 0, stream>>>(rpairs, pair_off, chunk_off, M, v, part);
+    } else {
+      auto* v = static_cast<PsiLam<double2>*>(pl);
+      k_interleave<double2><<<igrid, 256, 0, stream>>>(static_cast<const double2*>(psi),
+                                                       static_cast<const double2*>(lam), D, v);
+      k_pool_grad<double2><<<grid, kPoolThreads, 0, stream>>>(rpairs, pair_off, chunk_off, M, v, part);
+    }
   }
   k_pool_finalize<<<unsigned(M), 32, 0, stream>>>(part, chunk_off, M, grad);
   return cudaGetLastError();
