@@ -48,16 +48,19 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--workload", choices=["scan12", "warmstart", "config3", "config2", "q24", "adapt30",
-                                           "puccd11", "puccd24"],
+                                           "puccd11", "puccd24", "adapt24"],
                     default="scan12",
                     help="scan12: the throughput line (default); warmstart: the 16-qubit learned-warm-start "
                          "comparison (time to 1 mHa vs the plain HF start); config3: one 30-qubit instance; "
                          "config2: 256 uneven 14-20-qubit instances replayed from a CUDA graph; q24: one 24-qubit "
                          "instance (10 electrons, 256 angles); adapt30: ADAPT-VQE screening of the full "
-                         "3,500-operator pool at the 30-qubit state; puccd11: pUCCD in the hard-core boson "
+                         "3,500-operator pool at the 30-qubit state (adapt24: the same at the 24-qubit "
+                         "state); puccd11: pUCCD in the hard-core boson "
                          "form, 11 orbitals x 64 geometries in one launch; puccd24: one 24-orbital pUCCD "
                          "instance (12 pairs, 2.7M boson states)")
     ap.add_argument("--held-out", type=int, default=24, help="warmstart: held-out scan points compared")
+    ap.add_argument("--pool-ops", type=int, default=None,
+                    help="adapt30/adapt24: screen only the first N pool operators (a small profiling case)")
     return ap.parse_args()
 
 
@@ -402,7 +405,8 @@ def measured_hbm_gbs():
 def run_adapt(args):
     """ADAPT-VQE screening at 30 qubits: psi = U(theta)|HF> of the 512-angle
     state, lambda = H psi, and the gradient of every one of the 3,500 pool
-    operators (one vqe_pool_gradients call per step). The screening kernel's
+    operators (one vqe_pool_gradients call per step); adapt24: the same at the
+    24-qubit, 256-angle state with its full pool. The screening kernel's
     own time is the call's time minus that of vqe_energy on the same state
     (the same forward sweep and H psi launches), both CUDA-event timed."""
     import numpy as np
@@ -415,13 +419,25 @@ def run_adapt(args):
     vq.load()
     steps, warmup = min(args.steps, 10), max(3, min(args.warmup, 5))
     t0 = time.perf_counter()
-    w = synth.config3()
-    p, exc, th = w.problems[0], w.excitations[0], w.thetas[0]
-    pool = synth.uccsd_pool(30, 10)
+    if args.workload == "adapt30":
+        w = synth.config3()
+        p, exc, th, drop, nq = w.problems[0], w.excitations[0], w.thetas[0], w.drop_tol, 30
+        desc = "30 qubits, 10 electrons, 512-angle state, 3,500-operator UCCSD pool"
+    else:
+        rng = np.random.default_rng(24)
+        p = synth.integrals.random_problem(rng, 12, 10, 6, label="q24")
+        pool24 = synth.uccsd_pool(24, 10)
+        exc = pool24[rng.permutation(len(pool24))[:256]]
+        th, drop, nq = rng.normal(0.0, 0.05, size=256), 1e-14, 24
+        desc = f"24 qubits, 10 electrons, 256-angle state, {len(pool24)}-operator UCCSD pool"
+    pool = synth.uccsd_pool(nq, 10)
+    if args.pool_ops is not None:
+        pool = pool[:args.pool_ops]
+        desc += f", first {len(pool)} operators screened"
     hf = synth.hf_bitstring(10)
-    H = vq.Hamiltonian.from_problem(p, w.drop_tol)
-    A = vq.Ansatz(30, hf, exc)
-    P = vq.Ansatz(30, hf, pool)
+    H = vq.Hamiltonian.from_problem(p, drop)
+    A = vq.Ansatz(nq, hf, exc)
+    P = vq.Ansatz(nq, hf, pool)
     t_create = time.perf_counter() - t0
     ws = vq.alloc_workspace(max(vq.pool_workspace_bytes(H, A, P), vq.workspace_bytes(H, A, vq.VQE_WS_ENERGY)))
     theta = torch.as_tensor(th).cuda()
@@ -437,11 +453,10 @@ def run_adapt(args):
     alg_bytes = n_pairs * 40
     achieved = alg_bytes / (ms_screen / 1e3) / 1e9
     peak, src = measured_hbm_gbs()
-    line = {"metric": "ADAPT pool screening passes/s [adapt30]", "value": 1e3 / ms_step, "unit": "screens/s",
+    line = {"metric": f"ADAPT pool screening passes/s [{args.workload}]", "value": 1e3 / ms_step, "unit": "screens/s",
             "n_gpus": 1, "steps": steps, "warmup": warmup, "ms_per_step": ms_step, "higher_is_better": True,
             "scaling": "weak", "vs_baseline": None, "dtype": "f64", "data": "synthetic",
-            "config": {"workload": "30 qubits, 10 electrons, 512-angle state, 3,500-operator UCCSD pool "
-                                   f"({n_pairs} amplitude pairs)",
+            "config": {"workload": f"{desc} ({n_pairs} amplitude pairs)",
                        "l2": "flushed between timed steps (512 MB write)", "create_seconds": t_create,
                        "forward_and_hpsi_ms": ms_fwd_h, "screening_kernel_ms": ms_screen},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
@@ -546,7 +561,7 @@ def main():
         if rank == 0:
             run_large(args)
         return
-    if args.workload == "adapt30":
+    if args.workload in ("adapt30", "adapt24"):
         if rank == 0:
             run_adapt(args)
         return
