@@ -12,7 +12,9 @@
 //
 // psi and lambda are first copied side by side (entry r = {psi[r], lambda[r]}),
 // so each rank of a pair costs one 16-byte (real) or 32-byte (complex) gather
-// from one L2 sector instead of two gathers from two sectors.
+// from one L2 sector instead of two gathers from two sectors. The pair records
+// are read once, with the streaming (evict-first) cache hint, so that they do
+// not push the gathered entries out of L2.
 //
 // Work split: operator j's pairs are cut into chunks of kPoolChunk; a block
 // sums one chunk (thread-strided, then a fixed shuffle/shared-memory tree) and
@@ -95,7 +97,7 @@ __global__ void __launch_bounds__(kPoolThreads) k_pool_grad(const uint2* __restr
 #pragma unroll
       for (int u = 0; u < kPoolUnroll; ++u) {
         const int64_t p = base + int64_t(u) * kPoolThreads;
-        pr[u] = p < p1 ? __ldg(rp + p) : make_uint2(0u, 0u);
+        pr[u] = p < p1 ? __ldcs(rp + p) : make_uint2(0u, 0u);  // read once: evict first from L2
       }
       PsiLam<T> a[kPoolUnroll], b[kPoolUnroll];
 #pragma unroll
