@@ -57,7 +57,8 @@ struct GateRec {
 // the entry range of its list for each of the kStrWarps warps (a fixed share of
 // the Ib range each).
 constexpr int kStrWarps = 8;
-constexpr int kStrMinDb = 512;  // smaller beta string sets: a warp per output alpha string
+constexpr int kStrMinDb = 512;    // smaller beta string sets: a warp per output alpha string
+constexpr int kStrWideDb = 2048;  // larger ones: beta strings read through L1, four blocks per SM
 struct StrPlan {
   int32_t Da, Db, NB, pad;
   const uint32_t* ka;      // [Da] alpha strings as qubit masks, increasing
@@ -153,7 +154,10 @@ __host__ __device__ inline uint32_t align_up(uint32_t v, uint32_t a) { return (v
 
 // String-driven H psi: shared memory and blocks of its two forms (a block per
 // output alpha string when Db >= kStrMinDb, else a warp per output alpha string).
+// The block form stages the beta strings next to the two rows unless
+// Db >= kStrWideDb, where leaving them in L1 lets four blocks share an SM.
 __host__ __device__ inline size_t str_smem_bytes(int Db, size_t amp) {
+  if (Db >= kStrWideDb) return size_t(Db) * 2 * amp;
   return Db >= kStrMinDb ? size_t(Db) * (2 * amp + 4)
                          : align_up(uint32_t(Db) * 4u, 16u) + size_t(kStrWarps) * 2 * size_t(Db) * amp;
 }

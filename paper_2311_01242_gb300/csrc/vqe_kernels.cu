@@ -1033,7 +1033,8 @@ __device__ __forceinline__ void str_groups(const StrPlan& sp, int g0, int g1, in
 // bucket with a source alpha string Ja, the source row psi[Ja, :] is staged in
 // shared memory; then every warp walks its share (a fixed Ib range) of each
 // group's beta pair list. Needs blockDim.x == 32 * kStrWarps and 2 * Db
-// amplitudes + Db words of shared memory.
+// amplitudes (+ Db words of beta strings when Db < kStrWideDb; above, they are
+// read from global memory through L1) of shared memory.
 template <bool REAL>
 __device__ __forceinline__ void hpsi_str_row(const StrPlan& sp, int ia, const GroupRec* __restrict__ groups,
                                              const uint32_t* __restrict__ emask,
@@ -1046,10 +1047,12 @@ __device__ __forceinline__ void hpsi_str_row(const StrPlan& sp, int ia, const Gr
   const int Db = sp.Db, NB = sp.NB;
   T* psi_s = reinterpret_cast<T*>(smem);
   T* lam_s = psi_s + Db;
-  uint32_t* kb_s = reinterpret_cast<uint32_t*>(lam_s + Db);
+  const bool wide = Db >= kStrWideDb;
+  uint32_t* kb_stage = reinterpret_cast<uint32_t*>(lam_s + Db);
+  const uint32_t* kb_s = wide ? sp.kb : kb_stage;
   for (int j = tid; j < Db; j += bs) {
     lam_s[j] = A::zero();
-    kb_s[j] = __ldg(sp.kb + j);
+    if (!wide) kb_stage[j] = __ldg(sp.kb + j);
   }
   for (int b = 0; b < NB; ++b) {
     const int ja = __ldg(sp.ja + int64_t(ia) * NB + b);
@@ -1103,8 +1106,10 @@ __device__ __forceinline__ void hpsi_str_warps(const StrPlan& sp, int ia0, const
   for (int j = lane; j < Db; j += 32) out[j] = lam_s[j];
 }
 
-template <bool REAL>
-__global__ void __launch_bounds__(kStrWarps * 32, 3)
+// WIDE: the block form for Db >= kStrWideDb (smaller shared-memory footprint,
+// four blocks per SM); the other instance runs three.
+template <bool REAL, bool WIDE>
+__global__ void __launch_bounds__(kStrWarps * 32, WIDE ? 4 : 3)
 k_hpsi_str(const StrPlan sp, const GroupRec* __restrict__ groups, const uint32_t* __restrict__ emask,
            const typename Amp<REAL>::C* __restrict__ vals, const typename Amp<REAL>::T* __restrict__ psi_am,
            typename Amp<REAL>::T* __restrict__ lam_am) {
@@ -1407,8 +1412,10 @@ __global__ void k_ell_fill(const uint32_t* __restrict__ sector, int64_t D, const
 cudaError_t set_str_smem_limit(size_t smem) {
   const int b = int(smem);
   const cudaFuncAttribute a = cudaFuncAttributeMaxDynamicSharedMemorySize;
-  cudaError_t e = cudaFuncSetAttribute(k_hpsi_str<true>, a, b);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_hpsi_str<false>, a, b);
+  cudaError_t e = cudaFuncSetAttribute(k_hpsi_str<true, false>, a, b);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_hpsi_str<false, false>, a, b);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_hpsi_str<true, true>, a, b);
+  if (e == cudaSuccess) e = cudaFuncSetAttribute(k_hpsi_str<false, true>, a, b);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_hpsi_str, a, b);
   return e;
 }
@@ -1491,8 +1498,12 @@ cudaError_t stream_hpsi(const InstDesc& d, const StreamPlan& sp, const StreamBuf
     T* lam_am = static_cast<T*>(b.lam_am);
     const size_t smem = str_smem_bytes(sp.str.Db, sizeof(T));
     k_perm_gather<REAL><<<grid, kStreamThreads, 0, stream>>>(sp.str.perm, d.D, psi, psi_am);
-    k_hpsi_str<REAL><<<str_blocks(sp.str.Da, sp.str.Db), kStrWarps * 32, smem, stream>>>(sp.str, d.groups, d.emask,
-                                                                                         tv, psi_am, lam_am);
+    if (sp.str.Db >= kStrWideDb)
+      k_hpsi_str<REAL, true><<<str_blocks(sp.str.Da, sp.str.Db), kStrWarps * 32, smem, stream>>>(
+          sp.str, d.groups, d.emask, tv, psi_am, lam_am);
+    else
+      k_hpsi_str<REAL, false><<<str_blocks(sp.str.Da, sp.str.Db), kStrWarps * 32, smem, stream>>>(
+          sp.str, d.groups, d.emask, tv, psi_am, lam_am);
     k_perm_scatter<REAL><<<grid, kStreamThreads, 0, stream>>>(sp.str.perm, d.D, lam_am, lam);
     k_dot<REAL><<<grid, kStreamThreads, 0, stream>>>(psi, lam, d.D, b.epart);
   } else if (sp.use_ell) {
