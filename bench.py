@@ -402,6 +402,24 @@ def measured_hbm_gbs():
         return 6800.0, "fallback"
 
 
+def pool_profile_traffic(n_pairs):
+    """DRAM bytes of one k_pool_grad launch over n_pairs, scaled from the committed
+    ncu summary (5.33 GB for 137.4M pairs) if it was taken on the current source."""
+    import re
+    path = os.path.join(ROOT, "profiles", "k_pool_grad_adapt30.md")
+    src = os.path.join(ROOT, "paper_2311_01242_gb300", "csrc", "vqe_pool.cu")
+    try:
+        text = open(path).read()
+        with open(src, "rb") as f:
+            cur = hashlib.sha256(f.read()).hexdigest()[:16]
+    except OSError:
+        return None
+    sha = re.search(r"sha256 \(first 16 hex\): `([0-9a-f]+)`", text)
+    if not sha or sha.group(1) != cur:
+        return None
+    return 5.33e9 * n_pairs / 137417280
+
+
 def run_adapt(args):
     """ADAPT-VQE screening at 30 qubits: psi = U(theta)|HF> of the 512-angle
     state, lambda = H psi, and the gradient of every one of the 3,500 pool
@@ -460,7 +478,7 @@ def run_adapt(args):
                        "l2": "flushed between timed steps (512 MB write)", "create_seconds": t_create,
                        "forward_and_hpsi_ms": ms_fwd_h, "screening_kernel_ms": ms_screen},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
-                         "frac": achieved / peak, "traffic": None, "peak_source": src,
+                         "frac": achieved / peak, "traffic": pool_profile_traffic(n_pairs), "peak_source": src,
                          "kernel": "k_pool_grad + k_pool_finalize"},
             "gpu_launches_per_step": 2 * len(exc) + 8}
     print(json.dumps(line), flush=True)
