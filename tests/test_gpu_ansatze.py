@@ -142,3 +142,28 @@ def test_hcb_24_orbitals_full_size():
             return float(vq.energy(H, A, t, workspace=ws))
         gs = (e_at(np.pi / 4) - e_at(-np.pi / 4)) - w_ * (e_at(np.pi / 2) - e_at(-np.pi / 2))
         assert abs(gs - g[k]) <= 1e-9, (k, gs, g[k])
+
+
+def test_hcb_pool_screening_matches_oracle():
+    """ADAPT screening in the boson form: every pair excitation of the 11-orbital
+    pool against 2 Re <H psi| (b+_a b_i - b+_i b_a) |psi> from the oracle."""
+    w = synth.puccd_scan(1)
+    p = w.problems[0]
+    pool = synth.hcb_pair_pool(11, 4)
+    cur = pool[[3, 17, 25]]
+    th = np.array([0.3, -0.2, 0.15])
+    model = oracle.HcbModel(p, 4)
+    psi = oracle.hcb_state(11, 15, cur, th)
+    hpsi = model.apply(psi)
+    g_o = np.array([2.0 * np.vdot(hpsi, oracle.hcb_generator(psi, int(i), int(a))).real for i, a in pool])
+    H = vq.Hamiltonian.from_problem_hcb(p)
+    A = vq.Ansatz(11, 15, cur, hcb=True)
+    P = vq.Ansatz(11, 15, pool, hcb=True)
+    for flags in (0, vq.VQE_FLAG_FORCE_COMPLEX):
+        old = vq.set_flags(flags)
+        try:
+            e, g = vq.pool_gradients(H, A, P, th)
+        finally:
+            vq.set_flags(old)
+        assert abs(float(e) - np.vdot(psi, hpsi).real) <= E_TOL
+        assert np.abs(g.cpu().numpy() - g_o).max() <= G_TOL
