@@ -362,10 +362,35 @@ struct StreamBatch {
   }
 };
 
+// vqe_batch_energy_grad_host replays its copies and launches from a CUDA graph
+// once a call has been seen with the same host buffers, workspace, flags and
+// tuning; one graph per batch (a new key replaces it).
+struct HostGraph {
+  const double* theta = nullptr;
+  int64_t ld_theta = 0;
+  double* energies = nullptr;
+  double* grads = nullptr;
+  int64_t ld_grad = 0;
+  void* ws = nullptr;
+  size_t ws_bytes = 0;
+  int flags = 0, device = -1;
+  uint64_t tuning = 0;
+  cudaGraphExec_t exec = nullptr;
+  bool same(const HostGraph& o) const {
+    return theta == o.theta && ld_theta == o.ld_theta && energies == o.energies && grads == o.grads &&
+           ld_grad == o.ld_grad && ws == o.ws && ws_bytes == o.ws_bytes && flags == o.flags &&
+           device == o.device && tuning == o.tuning;
+  }
+};
+
 struct vqe_batch_s {
   int n_inst = 0;
   int32_t max_params = 0;
   StreamBatch sb;
+  HostGraph hg;
+  uint64_t tuning_version = 0;
+  cudaStream_t capture_stream = nullptr;  // private stream the host-call graph is captured on
+  std::mutex hg_mu;
   std::vector<vqe_hamiltonian_t> hams;
   std::vector<vqe_ansatz_t> ans;
   std::vector<InstDesc> descs;          // host copies, device pointers inside
@@ -375,6 +400,8 @@ struct vqe_batch_s {
   InstDesc* d_res[2] = {nullptr, nullptr};
   size_t res_smem[2] = {0, 0};
   ~vqe_batch_s() {
+    if (hg.exec) cudaGraphExecDestroy(hg.exec);
+    if (capture_stream) cudaStreamDestroy(capture_stream);
     dfree(d_res[0]);
     dfree(d_res[1]);
   }
@@ -1989,18 +2016,67 @@ int vqe_batch_energy_grad_host(vqe_batch_t b, const double* theta_host, int64_t 
     d_g = reinterpret_cast<double*>(base + off);
     off += align256(size_t(b->n_inst) * size_t(Mx) * 8);
   }
-  cudaError_t ce = cudaMemcpy2DAsync(d_theta, size_t(Mx) * 8, theta_host, size_t(ld_theta) * 8,
-                                     size_t(b->max_params) * 8, size_t(b->n_inst), cudaMemcpyHostToDevice,
-                                     stream);
-  if (ce != cudaSuccess) return cuda_fail(ce, "theta upload");
-  rc = batch_run(b, d_theta, Mx, d_e, d_g, Mx, base + off, ws_bytes - off, stream);
-  if (rc) return rc;
-  ce = cudaMemcpyAsync(energies_host, d_e, size_t(b->n_inst) * 8, cudaMemcpyDeviceToHost, stream);
-  if (ce != cudaSuccess) return cuda_fail(ce, "energy download");
-  if (with_grad) {
-    ce = cudaMemcpy2DAsync(grads_host, size_t(ld_grad) * 8, d_g, size_t(Mx) * 8, size_t(b->max_params) * 8,
-                           size_t(b->n_inst), cudaMemcpyDeviceToHost, stream);
-    if (ce != cudaSuccess) return cuda_fail(ce, "gradient download");
+  // upload, evaluate, download, all asynchronous on s
+  auto issue = [&](cudaStream_t s) -> int {
+    cudaError_t ce = cudaMemcpy2DAsync(d_theta, size_t(Mx) * 8, theta_host, size_t(ld_theta) * 8,
+                                       size_t(b->max_params) * 8, size_t(b->n_inst), cudaMemcpyHostToDevice, s);
+    if (ce != cudaSuccess) return cuda_fail(ce, "theta upload");
+    const int r = batch_run(b, d_theta, Mx, d_e, d_g, Mx, base + off, ws_bytes - off, s);
+    if (r) return r;
+    ce = cudaMemcpyAsync(energies_host, d_e, size_t(b->n_inst) * 8, cudaMemcpyDeviceToHost, s);
+    if (ce != cudaSuccess) return cuda_fail(ce, "energy download");
+    if (with_grad) {
+      ce = cudaMemcpy2DAsync(grads_host, size_t(ld_grad) * 8, d_g, size_t(Mx) * 8, size_t(b->max_params) * 8,
+                             size_t(b->n_inst), cudaMemcpyDeviceToHost, s);
+      if (ce != cudaSuccess) return cuda_fail(ce, "gradient download");
+    }
+    return VQE_OK;
+  };
+  cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
+  if (cudaStreamIsCapturing(stream, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
+    cudaGetLastError();
+    return issue(stream);  // inside the caller's own capture: no synchronisation
+  }
+  HostGraph key;
+  key.theta = theta_host;
+  key.ld_theta = ld_theta;
+  key.energies = energies_host;
+  key.grads = grads_host;
+  key.ld_grad = ld_grad;
+  key.ws = ws;
+  key.ws_bytes = ws_bytes;
+  key.flags = g_flags;
+  key.tuning = b->tuning_version;
+  cudaGetDevice(&key.device);
+  std::lock_guard<std::mutex> lk(b->hg_mu);
+  cudaError_t ce;
+  if (b->hg.exec && b->hg.same(key)) {
+    ce = cudaGraphLaunch(b->hg.exec, stream);
+    if (ce != cudaSuccess) return cuda_fail(ce, "graph launch");
+  } else {
+    // first call with these buffers: run directly, then capture the same
+    // sequence (nothing executes during capture) for the next calls
+    if ((rc = issue(stream))) return rc;
+    if (b->hg.exec) {
+      cudaGraphExecDestroy(b->hg.exec);
+      b->hg.exec = nullptr;
+    }
+    if (!b->capture_stream) cudaStreamCreateWithFlags(&b->capture_stream, cudaStreamNonBlocking);
+    cudaGraph_t graph = nullptr;
+    if (b->capture_stream &&
+        cudaStreamBeginCapture(b->capture_stream, cudaStreamCaptureModeThreadLocal) == cudaSuccess) {
+      const std::string saved = g_err;
+      const int rc2 = issue(b->capture_stream);
+      const cudaError_t ce2 = cudaStreamEndCapture(b->capture_stream, &graph);
+      cudaGraphExec_t exec = nullptr;
+      if (rc2 == VQE_OK && ce2 == cudaSuccess && graph && cudaGraphInstantiate(&exec, graph, 0) == cudaSuccess) {
+        key.exec = exec;
+        b->hg = key;
+      }
+      if (graph) cudaGraphDestroy(graph);
+      g_err = saved;  // a failed capture only means no graph: the call itself succeeded
+    }
+    cudaGetLastError();
   }
   ce = cudaStreamSynchronize(stream);
   if (ce != cudaSuccess) return cuda_fail(ce, "stream synchronize");
@@ -2013,6 +2089,7 @@ int vqe_batch_set_tuning(vqe_batch_t b, int stream_threads, int sweep_threads) {
     return fail(VQE_ERR_INVALID_ARG, "stream_threads: a multiple of 32 in [64, 512], or 0 to keep");
   if (sweep_threads != 0 && (sweep_threads < 32 || sweep_threads > vqe::kResidentThreads || sweep_threads % 32))
     return fail(VQE_ERR_INVALID_ARG, "sweep_threads: a multiple of 32 in [32, 512], or 0 to keep");
+  ++b->tuning_version;  // launch shapes are captured in the host-call graph
   if (stream_threads) b->sb.threads = stream_threads;
   if (sweep_threads) {
     for (int mode = 0; mode < 2; ++mode) {

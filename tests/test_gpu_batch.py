@@ -83,3 +83,41 @@ def test_graph_replay_and_tuning_do_not_change_results(mixed, tmp_path):
     assert _same(e3, g3, e_ref, g_ref, ms)
     choice2, _ = vb.autotune(B, theta, cache_path=cache)  # served from the cache
     assert choice2 == choice
+
+
+def test_host_entry_replays_graph_with_new_inputs(mixed):
+    """vqe_batch_energy_grad_host with pinned buffers replays a captured graph
+    from the second call on; new angles written into the same buffers, a flag
+    change and a tuning change must all show up in the results (mixed batch:
+    resident and streamed instances)."""
+    insts, hams, ans, B, theta = mixed
+    n, M = len(insts), B.max_params
+    th_h = torch.empty(n, M, dtype=torch.float64).pin_memory()
+    e_h = torch.empty(n, dtype=torch.float64).pin_memory()
+    g_h = torch.empty(n, M, dtype=torch.float64).pin_memory()
+    ws = vq.alloc_workspace(B.host_workspace_bytes(True))
+    rng = np.random.default_rng(501)
+    for step in range(4):
+        th = theta.cpu() * (1.0 + 0.5 * step) + torch.as_tensor(rng.normal(0, 0.01, size=(n, M))) * (theta.cpu() != 0)
+        th_h.copy_(th)
+        B.energy_grad_host(th_h.numpy(), e_h.numpy(), g_h.numpy(), ws)
+        e_d, g_d = B.energy_grad(th.cuda().contiguous())
+        assert torch.equal(e_h, e_d.cpu()), step
+        assert torch.equal(g_h, g_d.cpu()[:, :M]), step
+    old = vq.set_flags(vq.VQE_FLAG_FP64_SWEEPS)
+    try:
+        B.energy_grad_host(th_h.numpy(), e_h.numpy(), g_h.numpy(), ws)
+        e_d, g_d = B.energy_grad(th_h.cuda())
+        assert torch.equal(e_h, e_d.cpu()) and torch.equal(g_h, g_d.cpu()[:, :M])
+    finally:
+        vq.set_flags(old)
+    B.energy_grad_host(th_h.numpy(), e_h.numpy(), g_h.numpy(), ws)
+    vb_threads = 128
+    assert vq.api._lib().vqe_batch_set_tuning(B.handle, vb_threads, 96) == 0
+    try:
+        e2 = e_h.clone()
+        B.energy_grad_host(th_h.numpy(), e_h.numpy(), g_h.numpy(), ws)
+        B.energy_grad_host(th_h.numpy(), e_h.numpy(), g_h.numpy(), ws)
+        assert torch.equal(e_h, e2)
+    finally:
+        vq.api._lib().vqe_batch_set_tuning(B.handle, 256, 128)
