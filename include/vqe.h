@@ -321,7 +321,14 @@ int vqe_batch_energy_grad(vqe_batch_t b, const double* theta_dev, int64_t ld_the
  * Same as vqe_batch_energy_grad with HOST arrays: copies theta host->device,
  * runs, copies energies and gradients device->host, and synchronises the
  * stream before returning. Uses the workspace for the staged copies too
- * (vqe_batch_host_workspace_bytes).
+ * (vqe_batch_host_workspace_bytes). The first call with a given set of host
+ * buffers, workspace, flags and tuning runs the copies and launches directly
+ * and captures them in a CUDA graph (on a private stream; nothing runs twice);
+ * later calls with the same set replay that graph, reading the buffers'
+ * current contents. Pageable host memory cannot be captured: such calls always
+ * run directly. Called while `stream` is being captured, it only enqueues the
+ * work (no synchronisation). One graph per batch; not for concurrent use of
+ * one batch handle from several threads with different buffers.
  */
 size_t vqe_batch_host_workspace_bytes(vqe_batch_t b, int with_grad);
 int vqe_batch_energy_grad_host(vqe_batch_t b, const double* theta_host, int64_t ld_theta,
