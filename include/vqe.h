@@ -327,8 +327,8 @@ int vqe_batch_energy_grad(vqe_batch_t b, const double* theta_dev, int64_t ld_the
  * later calls with the same set replay that graph, reading the buffers'
  * current contents. Pageable host memory cannot be captured: such calls always
  * run directly. Called while `stream` is being captured, it only enqueues the
- * work (no synchronisation). One graph per batch; not for concurrent use of
- * one batch handle from several threads with different buffers.
+ * work (no synchronisation). One graph per batch (a new set of buffers
+ * replaces it); calls on one batch handle from several threads are serialised.
  */
 size_t vqe_batch_host_workspace_bytes(vqe_batch_t b, int with_grad);
 int vqe_batch_energy_grad_host(vqe_batch_t b, const double* theta_host, int64_t ld_theta,
