@@ -2017,17 +2017,25 @@ int vqe_batch_energy_grad_host(vqe_batch_t b, const double* theta_host, int64_t 
     off += align256(size_t(b->n_inst) * size_t(Mx) * 8);
   }
   // upload, evaluate, download, all asynchronous on s
+  // (rows packed back to back on both sides: one plain copy instead of a
+  // strided one, which the copy engine would run row by row)
+  const size_t rows_bytes = size_t(b->n_inst) * size_t(Mx) * 8;
+  const bool packed_theta = b->max_params == Mx && ld_theta == Mx;
+  const bool packed_grad = b->max_params == Mx && ld_grad == Mx;
   auto issue = [&](cudaStream_t s) -> int {
-    cudaError_t ce = cudaMemcpy2DAsync(d_theta, size_t(Mx) * 8, theta_host, size_t(ld_theta) * 8,
-                                       size_t(b->max_params) * 8, size_t(b->n_inst), cudaMemcpyHostToDevice, s);
+    cudaError_t ce =
+        packed_theta ? cudaMemcpyAsync(d_theta, theta_host, rows_bytes, cudaMemcpyHostToDevice, s)
+                       : cudaMemcpy2DAsync(d_theta, size_t(Mx) * 8, theta_host, size_t(ld_theta) * 8,
+                                           size_t(b->max_params) * 8, size_t(b->n_inst), cudaMemcpyHostToDevice, s);
     if (ce != cudaSuccess) return cuda_fail(ce, "theta upload");
     const int r = batch_run(b, d_theta, Mx, d_e, d_g, Mx, base + off, ws_bytes - off, s);
     if (r) return r;
     ce = cudaMemcpyAsync(energies_host, d_e, size_t(b->n_inst) * 8, cudaMemcpyDeviceToHost, s);
     if (ce != cudaSuccess) return cuda_fail(ce, "energy download");
     if (with_grad) {
-      ce = cudaMemcpy2DAsync(grads_host, size_t(ld_grad) * 8, d_g, size_t(Mx) * 8, size_t(b->max_params) * 8,
-                             size_t(b->n_inst), cudaMemcpyDeviceToHost, s);
+      ce = packed_grad ? cudaMemcpyAsync(grads_host, d_g, rows_bytes, cudaMemcpyDeviceToHost, s)
+                         : cudaMemcpy2DAsync(grads_host, size_t(ld_grad) * 8, d_g, size_t(Mx) * 8,
+                                             size_t(b->max_params) * 8, size_t(b->n_inst), cudaMemcpyDeviceToHost, s);
       if (ce != cudaSuccess) return cuda_fail(ce, "gradient download");
     }
     return VQE_OK;
