@@ -31,16 +31,17 @@ def _check(rc):
 
 
 def _ptr(a):
+    """Address of a tensor's or array's data as an int (ctypes passes it as void*)."""
     if a is None:
         return None
     if isinstance(a, torch.Tensor):
-        return ctypes.c_void_p(a.data_ptr())
-    return a.ctypes.data_as(ctypes.c_void_p)
+        return a.data_ptr()
+    return a.ctypes.data
 
 
 def _stream(stream=None):
     s = stream if stream is not None else torch.cuda.current_stream()
-    return ctypes.c_void_p(s.cuda_stream)
+    return s.cuda_stream
 
 
 def set_flags(flags: int) -> int:
@@ -341,11 +342,33 @@ class Batch:
             grads_host.shape[1] if grads_host is not None else 0, _ptr(workspace), workspace.numel(),
             _stream(stream)))
 
+    def host_call(self, theta_host, energies_host, grads_host, workspace, stream=None):
+        """energy_grad_host on fixed host arrays, marshalled once: the returned
+        callable runs one evaluation per call (for optimizer loops that rewrite
+        theta_host in place and read the results from the same arrays)."""
+        return HostCall(self, theta_host, energies_host, grads_host, workspace, stream)
+
     def __del__(self):
         b = getattr(self, "handle", None)
         if b is not None and b.value:
             self._lib.vqe_destroy_batch(b)
             self.handle = None
+
+
+class HostCall:
+    """A prepared vqe_batch_energy_grad_host call (Batch.host_call)."""
+
+    def __init__(self, batch, theta_host, energies_host, grads_host, workspace, stream=None):
+        self._keep = (batch, theta_host, energies_host, grads_host, workspace)
+        self._fn = batch._lib.vqe_batch_energy_grad_host
+        self._args = (batch.handle.value, _ptr(theta_host), theta_host.shape[1], _ptr(energies_host),
+                      _ptr(grads_host), grads_host.shape[1] if grads_host is not None else 0, _ptr(workspace),
+                      workspace.numel(), _stream(stream))
+
+    def __call__(self):
+        rc = self._fn(*self._args)
+        if rc:
+            _check(rc)
 
 
 def _handle_arrays(hams, ansatze):
