@@ -1057,8 +1057,25 @@ __device__ __forceinline__ void hpsi_str_row(const StrPlan& sp, int ia, const Gr
   for (int b = 0; b < NB; ++b) {
     const int ja = __ldg(sp.ja + int64_t(ia) * NB + b);
     if (ja < 0) continue;  // same for the whole block
-    __syncthreads();       // the previous source row is no longer read
     const T* row = psi_am + int64_t(ja) * Db;
+    {
+      // A bucket holding a single group that leaves the beta string unchanged
+      // (an alpha-alpha double, most buckets at 24-30 qubits): every output
+      // beta string takes one term from the same position of the source row, so
+      // it is read straight from global memory, without staging or a pair list.
+      // Each output still gets its terms in bucket order: the same bits.
+      const int g0 = __ldg(sp.boff + b);
+      if (__ldg(sp.boff + b + 1) - g0 == 1) {
+        const GroupRec g = load_group(groups + __ldg(sp.bgrp + g0));
+        if ((g.x & 0xAAAAAAAAu) == 0) {
+          __syncthreads();  // outputs were last updated under the list path's thread mapping
+          const uint32_t ka = __ldg(sp.ka + ja);
+          for (int j = tid; j < Db; j += bs) A::mac(lam_s[j], group_coef<REAL>(g, emask, vals, ka | kb_s[j]), row[j]);
+          continue;
+        }
+      }
+    }
+    __syncthreads();       // the previous source row is no longer read
     for (int j = tid; j < Db; j += bs) psi_s[j] = row[j];
     __syncthreads();
     str_groups<REAL>(sp, __ldg(sp.boff + b), __ldg(sp.boff + b + 1), w, w + 1, __ldg(sp.ka + ja), groups, emask,
@@ -1094,8 +1111,21 @@ __device__ __forceinline__ void hpsi_str_warps(const StrPlan& sp, int ia0, const
   for (int b = 0; b < NB; ++b) {
     const int ja = __ldg(sp.ja + int64_t(ia) * NB + b);
     if (ja < 0) continue;  // same for the whole warp
-    __syncwarp();
     const T* row = psi_am + int64_t(ja) * Db;
+    {
+      // single beta-diagonal group: read the source row directly (as in the block form)
+      const int g0 = __ldg(sp.boff + b);
+      if (__ldg(sp.boff + b + 1) - g0 == 1) {
+        const GroupRec g = load_group(groups + __ldg(sp.bgrp + g0));
+        if ((g.x & 0xAAAAAAAAu) == 0) {
+          __syncwarp();
+          const uint32_t ka = __ldg(sp.ka + ja);
+          for (int j = lane; j < Db; j += 32) A::mac(lam_s[j], group_coef<REAL>(g, emask, vals, ka | kb_s[j]), row[j]);
+          continue;
+        }
+      }
+    }
+    __syncwarp();
     for (int j = lane; j < Db; j += 32) psi_s[j] = row[j];
     __syncwarp();
     str_groups<REAL>(sp, __ldg(sp.boff + b), __ldg(sp.boff + b + 1), 0, kStrWarps, __ldg(sp.ka + ja), groups, emask,
