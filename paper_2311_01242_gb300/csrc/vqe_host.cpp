@@ -2041,10 +2041,13 @@ int vqe_batch_energy_grad_host(vqe_batch_t b, const double* theta_host, int64_t 
     return VQE_OK;
   };
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
-  if (cudaStreamIsCapturing(stream, &cap) != cudaSuccess || cap != cudaStreamCaptureStatusNone) {
-    cudaGetLastError();
-    return issue(stream);  // inside the caller's own capture: no synchronisation
+  if (cudaStreamIsCapturing(stream, &cap) != cudaSuccess) {
+    cudaGetLastError();  // status unknown: plain copies and launches, then synchronise
+    if ((rc = issue(stream))) return rc;
+    const cudaError_t se = cudaStreamSynchronize(stream);
+    return se == cudaSuccess ? VQE_OK : cuda_fail(se, "stream synchronize");
   }
+  if (cap != cudaStreamCaptureStatusNone) return issue(stream);  // inside the caller's capture: no sync
   HostGraph key;
   key.theta = theta_host;
   key.ld_theta = ld_theta;
