@@ -83,6 +83,26 @@ void parallel_for(int64_t n, F f) {
   for (auto& t : ts) t.join();
 }
 
+// Run f(i) for every i in [0, n) on up to hardware_concurrency threads, each
+// thread taking the next unclaimed index (for items of uneven, large cost).
+template <typename F>
+void parallel_items(int64_t n, F f) {
+  int nt = int(std::thread::hardware_concurrency());
+  if (nt < 1) nt = 1;
+  if (nt > 32) nt = 32;
+  if (n <= 1 || nt == 1) {
+    for (int64_t i = 0; i < n; ++i) f(i);
+    return;
+  }
+  std::atomic<int64_t> next{0};
+  std::vector<std::thread> ts;
+  for (int t = 0; t < nt && t < n; ++t)
+    ts.emplace_back([&]() {
+      for (int64_t i = next++; i < n; i = next++) f(i);
+    });
+  for (auto& t : ts) t.join();
+}
+
 // ------------------------------------------------------------------ Pauli algebra
 // A Pauli string P(x, z) = i^{|x&z|} X^x Z^z. Product rule:
 // P(x1,z1) P(x2,z2) = i^{|x1&z1| + |x2&z2| + 2|z1&x2| - |x&z|} P(x, z), x = x1^x2, z = z1^z2.
@@ -1519,13 +1539,13 @@ static int finish_ansatz(std::unique_ptr<vqe_ansatz_s> A, const std::vector<uint
   // pair lists: lower states (occupied i,j; empty a,b) of each gate
   A->pair_off.assign(size_t(n_exc) + 1, 0);
   std::vector<std::vector<uint32_t>> per(n_exc);
-  parallel_for(n_exc, [&](int64_t lo, int64_t hi) {
-    for (int64_t m = lo; m < hi; ++m) enumerate(occv[size_t(m)], A->gates[m].flip, per[m]);
-  });
+  parallel_items(n_exc, [&](int64_t m) { enumerate(occv[size_t(m)], A->gates[m].flip, per[m]); });
   for (int m = 0; m < n_exc; ++m) A->pair_off[m + 1] = A->pair_off[m] + int64_t(per[m].size());
   A->pairs.resize(size_t(A->pair_off[n_exc]));
-  for (int m = 0; m < n_exc; ++m)
+  parallel_items(n_exc, [&](int64_t m) {
     std::copy(per[m].begin(), per[m].end(), A->pairs.begin() + A->pair_off[m]);
+    std::vector<uint32_t>().swap(per[m]);
+  });
   // Rank tables of the sorted sector. A state k splits into a high part h =
   // k >> L and a low part v = k & (2^L - 1); sorted order compares h first, so
   // rank(k) = #{sector states with a smaller high part} + #{low parts below v
@@ -1567,14 +1587,12 @@ static int finish_ansatz(std::unique_ptr<vqe_ansatz_s> A, const std::vector<uint
     for (size_t r = 0; r < A->sector.size(); ++r)
       if (rank(A->sector[r]) != uint32_t(r)) return fail(VQE_ERR_UNSUPPORTED, "sector rank mismatch");
     A->rpairs.resize(A->pairs.size());
-    parallel_for(n_exc, [&](int64_t lo, int64_t hi) {
-      for (int64_t m = lo; m < hi; ++m) {
-        const GateRec& g = A->gates[size_t(m)];
-        for (int64_t p = A->pair_off[m]; p < A->pair_off[m + 1]; ++p) {
-          const uint32_t k = A->pairs[size_t(p)];
-          const uint32_t sb = uint32_t((pc32(k & g.par) & 1) ^ (g.sign0 < 0 ? 1 : 0));
-          A->rpairs[size_t(p)] = make_uint2(rank(k) | (sb << 31), rank(k ^ g.flip));
-        }
+    parallel_items(n_exc, [&](int64_t m) {
+      const GateRec& g = A->gates[size_t(m)];
+      for (int64_t p = A->pair_off[m]; p < A->pair_off[m + 1]; ++p) {
+        const uint32_t k = A->pairs[size_t(p)];
+        const uint32_t sb = uint32_t((pc32(k & g.par) & 1) ^ (g.sign0 < 0 ? 1 : 0));
+        A->rpairs[size_t(p)] = make_uint2(rank(k) | (sb << 31), rank(k ^ g.flip));
       }
     });
   }
