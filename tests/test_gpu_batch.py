@@ -124,3 +124,25 @@ def test_host_entry_replays_graph_with_new_inputs(mixed):
         assert torch.equal(e_h, e2)
     finally:
         vq.api._lib().vqe_batch_set_tuning(B.handle, 256, 128)
+
+
+def test_prepared_host_call_matches_host_entry(mixed):
+    """Batch.host_call marshals the host arrays once; each call reads the current
+    contents of theta and fills the same result arrays."""
+    insts, hams, ans, B, theta = mixed
+    n, M = len(insts), B.max_params
+    th_h = torch.empty(n, M, dtype=torch.float64).pin_memory()
+    e_h = torch.empty(n, dtype=torch.float64).pin_memory()
+    g_h = torch.empty(n, M, dtype=torch.float64).pin_memory()
+    ws = vq.alloc_workspace(B.host_workspace_bytes(True))
+    call = B.host_call(th_h.numpy(), e_h.numpy(), g_h.numpy(), ws)
+    e_ref = np.zeros(n)
+    g_ref = np.zeros((n, M))
+    ws2 = vq.alloc_workspace(B.host_workspace_bytes(True))
+    for scale in (1.0, 0.5, 2.0):
+        th_h.copy_(theta.cpu() * scale)
+        call()
+        B.energy_grad_host(np.ascontiguousarray(th_h.numpy()), e_ref, g_ref, ws2)
+        assert np.array_equal(e_h.numpy(), e_ref), scale
+        for i, a in enumerate(ans):
+            assert np.array_equal(g_h.numpy()[i, :a.n_params], g_ref[i, :a.n_params]), (scale, i)
