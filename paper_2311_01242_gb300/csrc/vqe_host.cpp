@@ -317,10 +317,8 @@ struct vqe_ansatz_s {
   int lo_bits = 0;                    // rank(k) = rank_hi[k >> lo_bits] + rank_lo[k & (2^lo_bits - 1)]
   std::vector<uint32_t> rank_hi, rank_lo;
   std::vector<uint2> rpairs;          // (rank(k) | sign << 31, rank(k ^ flip)) per pair
-  std::vector<int64_t> slot_off;      // [M+1] pool screening: gate m's partial slots
-  int64_t n_pool_chunks = 0;          // pool screening work list length (= partial slots)
-  int64_t* d_slot_off = nullptr;
-  vqe::PoolChunk* d_pool_chunks = nullptr;
+  std::vector<int64_t> chunk_off;     // [M+1] pool screening: chunks of kPoolChunk pairs before gate m
+  int64_t* d_chunk_off = nullptr;
   uint32_t* d_rank_hi = nullptr;
   uint32_t* d_rank_lo = nullptr;
   uint2* d_rpairs = nullptr;
@@ -335,8 +333,7 @@ struct vqe_ansatz_s {
   ~vqe_ansatz_s() {
     dfree(d_gates);
     dfree(d_pair_off);
-    dfree(d_slot_off);
-    dfree(d_pool_chunks);
+    dfree(d_chunk_off);
     dfree(d_pairs);
     dfree(d_sector);
     dfree(d_rank_hi);
@@ -1602,59 +1599,14 @@ static int finish_ansatz(std::unique_ptr<vqe_ansatz_s> A, const std::vector<uint
   A->nb_rows.resize(size_t(n_exc) + 1);
   for (int m = 0; m < n_exc; ++m) A->nb_rows[m] = vqe::stream_grid(A->pair_off[m + 1] - A->pair_off[m]);
   A->nb_rows[n_exc] = vqe::stream_grid(int64_t(A->sector.size()));
-  // Pool screening work list (used when this handle serves as an operator pool):
-  // each gate's pairs, sorted by the rank of k, cut where that rank crosses a
-  // multiple of kPoolWindow and into chunks of at most kPoolChunk, listed window
-  // by window; a gate's partial slots are consecutive, in window order.
-  std::vector<vqe::PoolChunk> pool_chunks;
-  {
-    const int64_t D = int64_t(A->sector.size());
-    const int64_t wsize = std::max<int64_t>(vqe::kPoolWindow, (D + 4095) / 4096);  // at most 4096 windows
-    const int64_t nw = std::max<int64_t>(1, (D + wsize - 1) / wsize);
-    std::vector<std::vector<int64_t>> cut(static_cast<size_t>(n_exc));
-    parallel_items(n_exc, [&](int64_t m) {
-      std::vector<int64_t>& c = cut[size_t(m)];
-      c.resize(size_t(nw) + 1);
-      const int64_t b = A->pair_off[m], e = A->pair_off[m + 1];
-      for (int64_t w = 0; w <= nw; ++w) {
-        const uint32_t lim = uint32_t(std::min<int64_t>(w * wsize, D));
-        int64_t lo = b, hi = e;  // first pair with rank(k) >= lim
-        while (lo < hi) {
-          const int64_t mid = (lo + hi) / 2;
-          if ((A->rpairs[size_t(mid)].x & 0x7fffffffu) < lim)
-            lo = mid + 1;
-          else
-            hi = mid;
-        }
-        c[size_t(w)] = w == nw ? e : lo;
-      }
-    });
-    A->slot_off.assign(size_t(n_exc) + 1, 0);
-    for (int m = 0; m < n_exc; ++m) {
-      int64_t k = 0;
-      for (int64_t w = 0; w < nw; ++w)
-        k += (cut[size_t(m)][size_t(w + 1)] - cut[size_t(m)][size_t(w)] + vqe::kPoolChunk - 1) / vqe::kPoolChunk;
-      A->slot_off[m + 1] = A->slot_off[m] + k;
-    }
-    if (A->slot_off[n_exc] >= (int64_t(1) << 31)) return fail(VQE_ERR_UNSUPPORTED, "too many pool screening chunks");
-    std::vector<int64_t> next(A->slot_off.begin(), A->slot_off.end() - 1);
-    pool_chunks.reserve(size_t(A->slot_off[n_exc]));
-    for (int64_t w = 0; w < nw; ++w)
-      for (int m = 0; m < n_exc; ++m)
-        for (int64_t p = cut[size_t(m)][size_t(w)]; p < cut[size_t(m)][size_t(w + 1)]; p += vqe::kPoolChunk) {
-          vqe::PoolChunk ch;
-          ch.p0 = p;
-          ch.len = int32_t(std::min<int64_t>(vqe::kPoolChunk, cut[size_t(m)][size_t(w + 1)] - p));
-          ch.slot = int32_t(next[size_t(m)]++);
-          pool_chunks.push_back(ch);
-        }
-    A->n_pool_chunks = int64_t(pool_chunks.size());
-  }
+  A->chunk_off.assign(size_t(n_exc) + 1, 0);
+  for (int m = 0; m < n_exc; ++m)
+    A->chunk_off[m + 1] =
+        A->chunk_off[m] + (A->pair_off[m + 1] - A->pair_off[m] + vqe::kPoolChunk - 1) / vqe::kPoolChunk;
   int rc;
   if ((rc = upload(A->gates, &A->d_gates))) return rc;
   if ((rc = upload(A->pair_off, &A->d_pair_off))) return rc;
-  if ((rc = upload(A->slot_off, &A->d_slot_off))) return rc;
-  if (!pool_chunks.empty() && (rc = upload(pool_chunks, &A->d_pool_chunks))) return rc;
+  if ((rc = upload(A->chunk_off, &A->d_chunk_off))) return rc;
   if ((rc = upload(A->pairs, &A->d_pairs))) return rc;
   if ((rc = upload(A->sector, &A->d_sector))) return rc;
   if ((rc = upload(A->rank_hi, &A->d_rank_hi))) return rc;
@@ -1778,7 +1730,7 @@ size_t vqe_pool_workspace_bytes(vqe_hamiltonian_t h, vqe_ansatz_t a, vqe_ansatz_
   int rc = VQE_OK;
   if (!get_ell(h, a, &rc)) return 0;
   const bool real = use_real();
-  return ws_layout(a, !real, false).total + align256(size_t(std::max<int64_t>(pool->n_pool_chunks, 1)) * 8) +
+  return ws_layout(a, !real, false).total + align256(size_t(std::max<int64_t>(pool->chunk_off.back(), 1)) * 8) +
          align256(std::max<size_t>(a->sector.size(), 1) * (real ? 16 : 32));
 }
 
@@ -1796,7 +1748,7 @@ int vqe_pool_gradients(vqe_hamiltonian_t h, vqe_ansatz_t a, vqe_ansatz_t pool, c
   if (!e) return rc;
   const bool real = use_real();
   const WsLayout L = ws_layout(a, !real, false);
-  const int64_t n_chunks = pool->n_pool_chunks;
+  const int64_t n_chunks = pool->chunk_off.back();
   const size_t part_bytes = align256(size_t(std::max<int64_t>(n_chunks, 1)) * 8);
   const size_t need = L.total + part_bytes + align256(std::max<size_t>(a->sector.size(), 1) * (real ? 16 : 32));
   if ((rc = check_ws(ws, ws_bytes, need))) return rc;
@@ -1807,7 +1759,7 @@ int vqe_pool_gradients(vqe_hamiltonian_t h, vqe_ansatz_t a, vqe_ansatz_t pool, c
   if (ce != cudaSuccess) return cuda_fail(ce, "pool screening forward / H psi launch");
   double* part = reinterpret_cast<double*>(static_cast<char*>(ws) + L.total);
   void* pl = static_cast<char*>(ws) + L.total + part_bytes;
-  ce = vqe::pool_gradients(pool->d_rpairs, pool->d_pool_chunks, n_chunks, pool->d_slot_off, pool->M, real, b.psi,
+  ce = vqe::pool_gradients(pool->d_rpairs, pool->d_pair_off, pool->d_chunk_off, pool->M, n_chunks, real, b.psi,
                            b.lam, int64_t(a->sector.size()), pl, part, pool_grad, st);
   if (ce != cudaSuccess) return cuda_fail(ce, "pool screening launch");
   return VQE_OK;

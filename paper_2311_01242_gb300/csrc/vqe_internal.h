@@ -18,15 +18,6 @@ constexpr int kResidentThreads = 512;
 constexpr int kStreamThreads = 256;
 constexpr int kMaxPartials = 1024;          // per-gate reduction partials (streaming)
 constexpr int kPoolChunk = 4096;            // pairs per partial sum of the pool screening
-constexpr int64_t kPoolWindow = 65536;      // sector ranks per window of the pool screening order (at least)
-
-// One unit of the pool screening: pairs [p0, p0 + len) of one gate, whose sum
-// goes to partial slot `slot` (a gate's slots are consecutive, in window order).
-struct alignas(16) PoolChunk {
-  int64_t p0;
-  int32_t len, slot;
-};
-static_assert(sizeof(PoolChunk) == 16, "read as one int4");
 
 // One X-mask group of the Hamiltonian. The group adds f(src) * psi[src] to
 // lambda[src ^ x]; u is the pattern of src on the group's pattern qubits
@@ -263,13 +254,12 @@ cudaError_t ell_device_fill(const uint32_t* sector, int64_t D, const GroupRec* g
                             cudaStream_t stream);
 
 // ADAPT pool screening (vqe_pool.cu): grad[m] = 2 Re <lam| T_m - T_m^dagger |psi>
-// over the M operators of a pool handle. chunks[n_chunks]: the work list, in
-// processing order; slot_off[M+1]: operator m's partials are slots
-// [slot_off[m], slot_off[m+1]) of part (n_chunks doubles, one per chunk);
+// over the M operators of a pool handle; chunk_off[m] = sum over operators
+// before m of ceil(pairs / kPoolChunk); part holds n_chunks = chunk_off[M] doubles;
 // pl (16-byte aligned) receives psi and lam side by side, D * 2 amplitudes.
-cudaError_t pool_gradients(const uint2* rpairs, const PoolChunk* chunks, int64_t n_chunks, const int64_t* slot_off,
-                           int M, bool real, const void* psi, const void* lam, int64_t D, void* pl, double* part,
-                           double* grad, cudaStream_t stream);
+cudaError_t pool_gradients(const uint2* rpairs, const int64_t* pair_off, const int64_t* chunk_off, int M,
+                           int64_t n_chunks, bool real, const void* psi, const void* lam, int64_t D, void* pl,
+                           double* part, double* grad, cudaStream_t stream);
 
 // Host helpers for the allocation-free entry point (vqe_static.cu).
 int prepare_noalloc(vqe_hamiltonian_s* h, vqe_ansatz_s* a, bool with_grad, InstDesc* d, StreamPlan* sp,

@@ -16,13 +16,10 @@
 // are read once, with the streaming (evict-first) cache hint, so that they do
 // not push the gathered entries out of L2.
 //
-// Work split: operator j's pairs (sorted by the rank of k) are cut where the
-// rank crosses a window boundary (kPoolWindow ranks) and into chunks of at most
-// kPoolChunk; the work list runs window by window, so the blocks in flight
-// gather psi and lambda around the same ranks (the k side stays in L2). A block
-// sums one chunk (thread-strided, then a fixed shuffle/shared-memory tree) into
-// the chunk's own partial slot; the finaliser adds operator j's slots in window
-// order. The result does not depend on the grid size or on scheduling.
+// Work split: operator j's pairs are cut into chunks of kPoolChunk; a block
+// sums one chunk (thread-strided, then a fixed shuffle/shared-memory tree) and
+// writes one partial; the finaliser adds operator j's partials in chunk order.
+// The result does not depend on the grid size or on scheduling.
 #include <cuda_runtime.h>
 
 #include "vqe_internal.h"
@@ -45,6 +42,19 @@ __device__ __forceinline__ double pair_term(double lb, double pa, double la, dou
 }
 __device__ __forceinline__ double pair_term(double2 lb, double2 pa, double2 la, double2 pb) {
   return fma(lb.x, pa.x, fma(lb.y, pa.y, -fma(la.x, pb.x, la.y * pb.y)));
+}
+
+// index m with chunk_off[m] <= c < chunk_off[m + 1] (chunk_off nondecreasing)
+__device__ __forceinline__ int owner_of(const int64_t* __restrict__ chunk_off, int M, int64_t c) {
+  int lo = 0, hi = M;  // invariant: chunk_off[lo] <= c < chunk_off[hi]
+  while (hi - lo > 1) {
+    const int mid = (lo + hi) >> 1;
+    if (__ldg(chunk_off + mid) <= c)
+      lo = mid;
+    else
+      hi = mid;
+  }
+  return lo;
 }
 
 // psi and lambda of one sector entry, side by side
@@ -70,15 +80,17 @@ __global__ void k_interleave(const T* __restrict__ psi, const T* __restrict__ la
 
 template <typename T>
 __global__ void __launch_bounds__(kPoolThreads) k_pool_grad(const uint2* __restrict__ rp,
-                                                            const PoolChunk* __restrict__ chunks, int64_t n_chunks,
+                                                            const int64_t* __restrict__ pair_off,
+                                                            const int64_t* __restrict__ chunk_off, int M,
                                                             const PsiLam<T>* __restrict__ pl,
                                                             double* __restrict__ part) {
   __shared__ double red[kPoolThreads / 32];
+  const int64_t n_chunks = __ldg(chunk_off + M);
   for (int64_t c = blockIdx.x; c < n_chunks; c += gridDim.x) {
-    const int4 ch = __ldg(reinterpret_cast<const int4*>(chunks + c));  // {p0 lo, p0 hi, len, slot}
-    const int64_t p0 = int64_t((uint64_t(uint32_t(ch.y)) << 32) | uint32_t(ch.x));
-    const int64_t p1 = p0 + ch.z;
-    const int slot = ch.w;
+    const int m = owner_of(chunk_off, M, c);
+    const int64_t p0 = __ldg(pair_off + m) + (c - __ldg(chunk_off + m)) * int64_t(kPoolChunk);
+    const int64_t p_end = __ldg(pair_off + m + 1);
+    const int64_t p1 = p0 + kPoolChunk < p_end ? p0 + kPoolChunk : p_end;
     double acc = 0.0;
     for (int64_t base = p0 + threadIdx.x; base < p1; base += int64_t(kPoolThreads) * kPoolUnroll) {
       uint2 pr[kPoolUnroll];
@@ -107,18 +119,18 @@ __global__ void __launch_bounds__(kPoolThreads) k_pool_grad(const uint2* __restr
       double s = 0.0;
 #pragma unroll
       for (int w = 0; w < kPoolThreads / 32; ++w) s += red[w];
-      part[slot] = s;
+      part[c] = s;
     }
     __syncthreads();
   }
 }
 
-// g[m] = 2 * (sum of operator m's partial slots in order); one warp per operator
-__global__ void k_pool_finalize(const double* __restrict__ part, const int64_t* __restrict__ slot_off, int M,
+// g[m] = 2 * (sum of operator m's chunk partials in chunk order); one warp per operator
+__global__ void k_pool_finalize(const double* __restrict__ part, const int64_t* __restrict__ chunk_off, int M,
                                 double* __restrict__ g) {
   const int m = blockIdx.x;
   if (m >= M) return;
-  const int64_t c0 = __ldg(slot_off + m), c1 = __ldg(slot_off + m + 1);
+  const int64_t c0 = __ldg(chunk_off + m), c1 = __ldg(chunk_off + m + 1);
   double s = 0.0;
   for (int64_t c = c0 + threadIdx.x; c < c1; c += 32) s += part[c];
 #pragma unroll
@@ -128,9 +140,9 @@ __global__ void k_pool_finalize(const double* __restrict__ part, const int64_t* 
 
 }  // namespace
 
-cudaError_t pool_gradients(const uint2* rpairs, const PoolChunk* chunks, int64_t n_chunks, const int64_t* slot_off,
-                           int M, bool real, const void* psi, const void* lam, int64_t D, void* pl, double* part,
-                           double* grad, cudaStream_t stream) {
+cudaError_t pool_gradients(const uint2* rpairs, const int64_t* pair_off, const int64_t* chunk_off, int M,
+                           int64_t n_chunks, bool real, const void* psi, const void* lam, int64_t D, void* pl,
+                           double* part, double* grad, cudaStream_t stream) {
   if (M <= 0) return cudaSuccess;
   if (n_chunks > 0) {
     int dev = 0, sms = 0;
@@ -146,15 +158,15 @@ cudaError_t pool_gradients(const uint2* rpairs, const PoolChunk* chunks, int64_t
       auto* v = static_cast<PsiLam<double>*>(pl);
       k_interleave<double><<<igrid, 256, 0, stream>>>(static_cast<const double*>(psi),
                                                       static_cast<const double*>(lam), D, v);
-      k_pool_grad<double><<<grid, kPoolThreads, 0, stream>>>(rpairs, chunks, n_chunks, v, part);
+      k_pool_grad<double><<<grid, kPoolThreads, 0, stream>>>(rpairs, pair_off, chunk_off, M, v, part);
     } else {
       auto* v = static_cast<PsiLam<double2>*>(pl);
       k_interleave<double2><<<igrid, 256, 0, stream>>>(static_cast<const double2*>(psi),
                                                        static_cast<const double2*>(lam), D, v);
-      k_pool_grad<double2><<<grid, kPoolThreads, 0, stream>>>(rpairs, chunks, n_chunks, v, part);
+      k_pool_grad<double2><<<grid, kPoolThreads, 0, stream>>>(rpairs, pair_off, chunk_off, M, v, part);
     }
   }
-  k_pool_finalize<<<unsigned(M), 32, 0, stream>>>(part, slot_off, M, grad);
+  k_pool_finalize<<<unsigned(M), 32, 0, stream>>>(part, chunk_off, M, grad);
   return cudaGetLastError();
 }
 
