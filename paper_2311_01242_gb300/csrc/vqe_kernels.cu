@@ -987,11 +987,12 @@ k_gate_adj(const uint2* __restrict__ rp, int64_t P, const double2* __restrict__ 
 // Groups gi in [g0, g1) of one bucket against a staged source row: for each
 // group in order, lanes walk list entries [e0, e1) (this warp's share, or the
 // whole list) and add f_g(src) psi_s[Jb] into lam_s[Ib]. The next group's
-// record and range are loaded while the current group runs; four list entries
-// per lane are in flight. Entries of one list have distinct Ib, and __syncwarp
-// separates the groups, so each output is updated by one lane at a time, in
-// group order.
-template <bool REAL>
+// record and range are loaded while the current group runs; U list entries per
+// lane are in flight (8 with real amplitudes in the wide block form and in the
+// warp form, else 4: the best measured for each). Entries of one list have
+// distinct Ib, and __syncwarp separates the groups, so each output is updated
+// by one lane at a time, in group order (U does not change the order).
+template <bool REAL, int U>
 __device__ __forceinline__ void str_groups(const StrPlan& sp, int g0, int g1, int w_lo, int w_hi, uint32_t ka,
                                            const GroupRec* __restrict__ groups, const uint32_t* __restrict__ emask,
                                            const typename Amp<REAL>::C* __restrict__ vals, const uint32_t* kb_s,
@@ -1010,12 +1011,12 @@ __device__ __forceinline__ void str_groups(const StrPlan& sp, int g0, int g1, in
       e0n = __ldg(sp.bsplit + int64_t(gi + 1) * (kStrWarps + 1) + w_lo);
       e1n = __ldg(sp.bsplit + int64_t(gi + 1) * (kStrWarps + 1) + w_hi);
     }
-    for (int e = e0 + lane; e < e1; e += 4 * 32) {
-      uint32_t ent[4];
+    for (int e = e0 + lane; e < e1; e += U * 32) {
+      uint32_t ent[U];
 #pragma unroll
-      for (int u = 0; u < 4; ++u) ent[u] = (e + 32 * u < e1) ? __ldg(sp.lists + e + 32 * u) : 0xFFFFFFFFu;
+      for (int u = 0; u < U; ++u) ent[u] = (e + 32 * u < e1) ? __ldg(sp.lists + e + 32 * u) : 0xFFFFFFFFu;
 #pragma unroll
-      for (int u = 0; u < 4; ++u) {
+      for (int u = 0; u < U; ++u) {
         if (ent[u] == 0xFFFFFFFFu) break;
         const uint32_t ib = ent[u] & 0xFFFFu, jb = ent[u] >> 16;
         A::mac(lam_s[ib], group_coef<REAL>(g, emask, vals, ka | kb_s[jb]), psi_s[jb]);
@@ -1035,7 +1036,7 @@ __device__ __forceinline__ void str_groups(const StrPlan& sp, int g0, int g1, in
 // group's beta pair list. Needs blockDim.x == 32 * kStrWarps and 2 * Db
 // amplitudes (+ Db words of beta strings when Db < kStrWideDb; above, they are
 // read from global memory through L1) of shared memory.
-template <bool REAL>
+template <bool REAL, bool WIDE>
 __device__ __forceinline__ void hpsi_str_row(const StrPlan& sp, int ia, const GroupRec* __restrict__ groups,
                                              const uint32_t* __restrict__ emask,
                                              const typename Amp<REAL>::C* __restrict__ vals,
@@ -1047,12 +1048,11 @@ __device__ __forceinline__ void hpsi_str_row(const StrPlan& sp, int ia, const Gr
   const int Db = sp.Db, NB = sp.NB;
   T* psi_s = reinterpret_cast<T*>(smem);
   T* lam_s = psi_s + Db;
-  const bool wide = Db >= kStrWideDb;
   uint32_t* kb_stage = reinterpret_cast<uint32_t*>(lam_s + Db);
-  const uint32_t* kb_s = wide ? sp.kb : kb_stage;
+  const uint32_t* kb_s = WIDE ? sp.kb : kb_stage;
   for (int j = tid; j < Db; j += bs) {
     lam_s[j] = A::zero();
-    if (!wide) kb_stage[j] = __ldg(sp.kb + j);
+    if (!WIDE) kb_stage[j] = __ldg(sp.kb + j);
   }
   for (int b = 0; b < NB; ++b) {
     const int ja = __ldg(sp.ja + int64_t(ia) * NB + b);
@@ -1078,7 +1078,7 @@ __device__ __forceinline__ void hpsi_str_row(const StrPlan& sp, int ia, const Gr
     __syncthreads();       // the previous source row is no longer read
     for (int j = tid; j < Db; j += bs) psi_s[j] = row[j];
     __syncthreads();
-    str_groups<REAL>(sp, __ldg(sp.boff + b), __ldg(sp.boff + b + 1), w, w + 1, __ldg(sp.ka + ja), groups, emask,
+    str_groups<REAL, (WIDE && REAL) ? 8 : 4>(sp, __ldg(sp.boff + b), __ldg(sp.boff + b + 1), w, w + 1, __ldg(sp.ka + ja), groups, emask,
                      vals, kb_s, psi_s, lam_s, lane);
   }
   __syncthreads();
@@ -1128,7 +1128,7 @@ __device__ __forceinline__ void hpsi_str_warps(const StrPlan& sp, int ia0, const
     __syncwarp();
     for (int j = lane; j < Db; j += 32) psi_s[j] = row[j];
     __syncwarp();
-    str_groups<REAL>(sp, __ldg(sp.boff + b), __ldg(sp.boff + b + 1), 0, kStrWarps, __ldg(sp.ka + ja), groups, emask,
+    str_groups<REAL, REAL ? 8 : 4>(sp, __ldg(sp.boff + b), __ldg(sp.boff + b + 1), 0, kStrWarps, __ldg(sp.ka + ja), groups, emask,
                      vals, kb_s, psi_s, lam_s, lane);
   }
   __syncwarp();
@@ -1145,7 +1145,7 @@ k_hpsi_str(const StrPlan sp, const GroupRec* __restrict__ groups, const uint32_t
            typename Amp<REAL>::T* __restrict__ lam_am) {
   extern __shared__ __align__(16) unsigned char smem[];
   if (sp.Db >= kStrMinDb)
-    hpsi_str_row<REAL>(sp, int(blockIdx.x), groups, emask, vals, psi_am, lam_am, smem);
+    hpsi_str_row<REAL, WIDE>(sp, int(blockIdx.x), groups, emask, vals, psi_am, lam_am, smem);
   else
     hpsi_str_warps<REAL>(sp, int(blockIdx.x) * kStrWarps, groups, emask, vals, psi_am, lam_am, smem);
 }
@@ -1316,7 +1316,10 @@ __global__ void __launch_bounds__(kStrWarps * 32, 2) kb_hpsi_str(BatchDev b, Bat
   const double* psi_am = reinterpret_cast<const double*>(b.ws + b.am_off[i]);
   double* lam_am = reinterpret_cast<double*>(b.ws + b.am_off[i]) + d->D;
   if (sp.Db >= kStrMinDb)
-    hpsi_str_row<true>(sp, blk, d->groups, d->emask, d->vals, psi_am, lam_am, smem);
+    if (sp.Db >= kStrWideDb)
+      hpsi_str_row<true, true>(sp, blk, d->groups, d->emask, d->vals, psi_am, lam_am, smem);
+    else
+      hpsi_str_row<true, false>(sp, blk, d->groups, d->emask, d->vals, psi_am, lam_am, smem);
   else
     hpsi_str_warps<true>(sp, blk * kStrWarps, d->groups, d->emask, d->vals, psi_am, lam_am, smem);
 }
