@@ -5,9 +5,10 @@ Each round screens the whole pool with one vqe_pool_gradients call (forward
 sweep, H psi and every pool operator's gradient on the device), appends the
 operator of largest |g_j| (lowest index on ties) at angle 0, and re-optimises
 all angles with BFGS on the host from the previous optimum, each evaluation
-one vqe_energy_grad call. The paper takes the pool gradients as the
-convergence measure without fixing a rule; here the loop stops when their
-2-norm falls below grad_tol, or after max_ops operators.
+one vqe_batch_energy_grad_host call on a one-instance batch (angles in, energy
+and gradient out through pinned host arrays; graph-replayed). The paper takes
+the pool gradients as the convergence measure without fixing a rule; here the
+loop stops when their 2-norm falls below grad_tol, or after max_ops operators.
 """
 from dataclasses import dataclass, field
 from typing import List
@@ -46,15 +47,23 @@ def adapt_vqe(H, n_qubits, hf_bits, pool_excitations, grad_tol=1e-3, max_ops=Non
             return AdaptResult(float(e), chosen, theta, history, evals)
         chosen.append(j)
         A = api.Ansatz(n_qubits, hf_bits, pool_exc[chosen])
-        ws = api.alloc_workspace(api.workspace_bytes(H, A, api.VQE_WS_GRAD), device)
-        th_dev = torch.empty(A.n_params, dtype=torch.float64, device=device)
+        # one-instance batch evaluated from pinned host arrays: each BFGS
+        # evaluation is one library call (copies, launch and synchronisation)
+        B = api.Batch([H], [A])
+        m = A.n_params
+        th_h = torch.zeros(1, m, dtype=torch.float64).pin_memory()
+        e_h = torch.zeros(1, dtype=torch.float64).pin_memory()
+        g_h = torch.zeros(1, m, dtype=torch.float64).pin_memory()
+        ws = api.alloc_workspace(B.host_workspace_bytes(True), device)
+        th_np, e_np, g_np = th_h.numpy(), e_h.numpy(), g_h.numpy()
+        call = B.host_call(th_np, e_np, g_np, ws)
 
         def fun(t):
             nonlocal evals
             evals += 1
-            th_dev.copy_(torch.from_numpy(np.ascontiguousarray(t, dtype=np.float64)))
-            ev, gv = api.energy_grad(H, A, th_dev, workspace=ws)
-            return float(ev), gv.cpu().numpy()
+            th_np[0, :] = t
+            call()
+            return float(e_np[0]), g_np[0].copy()
 
         res = so.minimize(fun, np.append(theta, 0.0), jac=True, method="BFGS",
                           options={"gtol": gtol, "maxiter": maxiter})
