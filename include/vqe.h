@@ -285,8 +285,10 @@ int vqe_apply_hamiltonian(vqe_hamiltonian_t h, vqe_ansatz_t a, const double* psi
  *     pool is empty).
  *   workspace: vqe_pool_workspace_bytes(h, a, pool) bytes, 256-byte aligned
  *     (the sector-compressed psi and lambda, a copy of both side by side, and
- *     one partial per 4096 pairs of the pool). Asynchronous on `stream`; allocates nothing, so it can be
- *     captured in a CUDA graph. Deterministic: fixed reduction order.
+ *     one partial sum per started 4096 pairs of each operator); a smaller or
+ *     misaligned workspace returns VQE_ERR_WORKSPACE before any launch.
+ * Asynchronous on `stream`; allocates nothing, so it can be captured in a CUDA
+ * graph. Deterministic: fixed reduction order, independent of the grid size.
  */
 size_t vqe_pool_workspace_bytes(vqe_hamiltonian_t h, vqe_ansatz_t a, vqe_ansatz_t pool);
 int vqe_pool_gradients(vqe_hamiltonian_t h, vqe_ansatz_t a, vqe_ansatz_t pool,
