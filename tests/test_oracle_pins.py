@@ -178,9 +178,10 @@ def _generator_dense(exc, n):
 
 
 @pytest.mark.parametrize("exc", [(0, 2, -1, -1), (1, 5, -1, -1), (0, 1, 2, 3), (0, 3, 4, 5),
-                                 (1, 2, 3, 4), (0, 2, 4, 5)])
+                                 (1, 2, 3, 4), (0, 2, 4, 5), (4, 1, -1, -1), (3, 5, 0, 2), (2, 3, 0, 1)])
 def test_gate_matches_expm(exc):
-    """The pair rotation equals scipy.linalg.expm(theta (T - T^dagger)) on random states."""
+    """The pair rotation equals scipy.linalg.expm(theta (T - T^dagger)) on random states,
+    including generalised excitations that move electrons to lower orbitals (k-UpCCGSD)."""
     n = 6
     rng = np.random.default_rng(9)
     A = _generator_dense(exc, n)
