@@ -167,3 +167,19 @@ def test_hcb_pool_screening_matches_oracle():
             vq.set_flags(old)
         assert abs(float(e) - np.vdot(psi, hpsi).real) <= E_TOL
         assert np.abs(g.cpu().numpy() - g_o).max() <= G_TOL
+
+
+def test_downward_generalised_excitations_match_oracle():
+    """Generalised excitations that move electrons to lower orbitals, and
+    repeats, in one ansatz (the gates after the first layer start from states
+    where those orbitals are occupied)."""
+    p = synth.random_problem(np.random.default_rng(408), 4, 4, 3)
+    exc = np.array([(0, 4, -1, -1), (1, 7, -1, -1), (0, 1, 4, 5), (4, 0, -1, -1), (7, 3, -1, -1),
+                    (4, 5, 2, 3), (2, 6, 0, 1), (0, 4, -1, -1)], dtype=np.int32)
+    th = np.random.default_rng(409).normal(0, 0.5, size=len(exc))
+    e_o, g_o = oracle.gradient_direct(oracle.EnergyModel.from_problem(p), 15, exc, th)
+    H = vq.Hamiltonian.from_problem(p)
+    A = vq.Ansatz(8, 15, exc)
+    for flags in PATHS:
+        e, g = _eg(H, A, th, flags)
+        assert abs(e - e_o) <= E_TOL and np.abs(g - g_o).max() <= G_TOL, flags
