@@ -155,3 +155,18 @@ def test_fold_frozen_rejects_overlap_and_range(lib):
         api.fold_frozen(h, e, 0.0, [0], [0, 1])
     with pytest.raises(api.VQEError):
         api.fold_frozen(h, e, 0.0, [5], [0, 1])
+
+
+def test_frozen_core_then_boson_mapping_matches_oracle(lib):
+    """The paper's CH3F pipeline in small: freeze the core (Eq. 3), then map the
+    active space to pUCCD's boson form. Library host mappings against the oracle's
+    fold and its seniority-zero block of the folded problem."""
+    prob = synth.random_problem(np.random.default_rng(124), 6, 8, 3)
+    frozen, active = [0], [1, 2, 3, 4, 5]
+    h2, e2, c2 = api.fold_frozen(prob.h, prob.eri, prob.c0, frozen, active)
+    xs, zs, cs = api.hcb_hamiltonian(len(active), h2, e2, c2)
+    red = oracle.fold_frozen(prob, frozen, active)
+    block, bos = oracle.hcb_hamiltonian_matrix(red, 3)
+    dense = oracle.pauli_sum_dense(xs, zs, cs, len(active))
+    idx = bos.astype(np.int64)
+    assert np.abs(dense[np.ix_(idx, idx)] - block.toarray()).max() < 1e-12
