@@ -9,6 +9,9 @@
  *   - U(theta) = U_M ... U_1, U_k = exp(theta_k (T_k - T_k^dagger)), one
  *     rotation per single or double excitation of the UCCSD ansatz (Sec. 2.1.2);
  *   - |HF> is the Hartree-Fock reference bitstring of Eq. 1.
+ * Around that evaluation it also provides ADAPT-VQE's pool screening (Sec.
+ * 2.1.1), pUCCD's hard-core boson form and generalised excitation lists
+ * (Sec. 2.1.2), and the frozen-core folding of Eq. 3 (Sec. 2.1.3).
  *
  * Conventions shared by every call:
  *   - Bit q of a basis index is qubit q; qubit q is spin orbital q (spatial
