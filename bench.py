@@ -35,6 +35,9 @@ FP64_DFMA_PER_CLK_SM = 2
 N_SMS = 152
 SM_MAX_MHZ = 2070.0
 FP64_PEAK_TFLOPS = FP64_DFMA_PER_CLK_SM * N_SMS * SM_MAX_MHZ * 1e6 * 2 / 1e12
+# 64-bit integer high multiplies (__umul64hi) sustained per clock per SM, measured
+# by an integer throughput probe on this GB300 (the fixed-point kernels' multiply)
+INT_MUL64_PER_CLK_SM = 6.7
 PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_resident_config1.md")
 KERNEL_SRC = os.path.join(ROOT, "paper_2311_01242_gb300", "csrc", "vqe_kernels.cu")
 
@@ -60,6 +63,9 @@ def parse():
                          "form, 11 orbitals x 64 geometries in one launch; puccd24: one 24-orbital pUCCD "
                          "instance (12 pairs, 2.7M boson states)")
     ap.add_argument("--held-out", type=int, default=24, help="warmstart: held-out scan points compared")
+    ap.add_argument("--skip", nargs="*", default=[], choices=["config3", "config2", "warmstart", "complex"],
+                    help="default line: leave these per-config entries out")
+    ap.add_argument("--no-per-config", action="store_true", help="default line: headline only")
     ap.add_argument("--pool-ops", type=int, default=None,
                     help="adapt30/adapt24: screen only the first N pool operators (a small profiling case)")
     return ap.parse_args()
@@ -92,7 +98,8 @@ class ClockSampler:
         for line in self.proc.stdout:
             self.lines.append((time.time(), line.strip()))
 
-    def stop(self):
+    def stop(self, t_begin=None, t_end=None):
+        """Summary of the samples taken in [t_begin, t_end] (time.time(); all if None)."""
         if self.proc is None:
             return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"], "samples": 0}
         time.sleep(0.05)
@@ -103,7 +110,11 @@ class ClockSampler:
             self.proc.kill()
         sm, smax, reasons = [], [], set()
         names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
-        for _, line in self.lines:
+        lines = [(t, ln) for t, ln in self.lines
+                 if (t_begin is None or t >= t_begin) and (t_end is None or t <= t_end)]
+        if not lines:  # a region shorter than the sampling interval: the nearest samples
+            lines = self.lines[-2:]
+        for _, line in lines:
             parts = [p.strip() for p in line.split(",")]
             if len(parts) < 9:
                 continue
@@ -528,13 +539,15 @@ def run_adapt_loop(args):
     print(json.dumps(line), flush=True)
 
 
-def run_warmstart(args):
+def warmstart_summary(args):
     """16 qubits, 8 electrons, 512-point scan r in [0.7, 4.0], 360 UCCSD angles:
     plain VQE with continuation on every 4th point trains the network; at
     held-out points, BFGS runs from the HF start, from the nearest earlier
     training point's angles (continuation), and from the network prediction
-    (HF when the prediction's energy is not below HF). Reports evaluations and
-    seconds until E <= E_exact + 1 mHa (exact: GPU Lanczos in the sector)."""
+    (HF when the prediction's energy is not below HF). Per arm: evaluations and
+    seconds until E <= E_exact + 1 mHa (exact: GPU Lanczos in the sector), or
+    the best converged energy + 1 mHa where no start reaches that; a run that
+    never reaches the target counts with every evaluation and second it spent."""
     import numpy as np
     import torch
 
@@ -544,6 +557,7 @@ def run_warmstart(args):
 
     torch.cuda.set_device(0)
     vq.load()
+    t_all = time.perf_counter()
     w = synth.config4()
     scan = w.scan
     rs = scan.rs
@@ -583,28 +597,359 @@ def run_warmstart(args):
         reached_exact += int(res["reached_exact"])
         for name in arms:
             r = res[name]
+            # the network arm also pays its prediction: two energy evaluations and the forward pass
             extra_e, extra_t = (2, t_pred) if name == "mlp" else (0, 0.0)
-            arms[name].append((None if r["evals"] is None else r["evals"] + extra_e,
-                               None if r["seconds"] is None else r["seconds"] + extra_t))
+            hit = r["evals"] is not None
+            arms[name].append((hit, (r["evals"] if hit else r["evals_total"]) + extra_e,
+                               (r["seconds"] if hit else r["seconds_total"]) + extra_t))
     summary = {}
     for name, v in arms.items():
-        ev = [a for a, _ in v if a is not None]
-        sec = [b for _, b in v if b is not None]
-        summary[name] = {"mean_evals": float(np.mean(ev)) if ev else None,
-                         "median_evals": float(np.median(ev)) if ev else None,
-                         "mean_seconds": float(np.mean(sec)) if sec else None,
-                         "reached": len(ev), "points": len(v)}
-    line = {"metric": "time to 1 mHa vs plain (learned warm start)", "value": summary["mlp"]["mean_seconds"],
-            "unit": "s", "higher_is_better": False, "n_gpus": 1, "dtype": "f64 (VQE), bf16/f32 (network)",
-            "data": "synthetic",
-            "config": {"workload": "16 qubits, 8 electrons, 512-point scan r in [0.7,4.0], 360 UCCSD angles",
-                       "train_points": len(train), "held_out_points": len(held), "target": "E_exact + 1 mHa "
-                       "(or best converged + 1 mHa where UCCSD cannot reach it)"},
+        ev = [e for _, e, _ in v]
+        sec = [s for _, _, s in v]
+        summary[name] = {"mean_evals": float(np.mean(ev)), "median_evals": float(np.median(ev)),
+                         "mean_seconds": float(np.mean(sec)), "reached": int(sum(h for h, _, _ in v)),
+                         "points": len(v)}
+    return {"metric": "time to 1 mHa vs plain (learned warm start)", "value": summary["mlp"]["mean_seconds"],
+            "unit": "s", "higher_is_better": False, "dtype": "f64 (VQE), bf16/f32 (network)",
+            "workload": "16 qubits, 8 electrons, 512-point scan r in [0.7,4.0], 360 UCCSD angles",
+            "train_points": len(train), "held_out_points": len(held),
+            "target": "E_exact + 1 mHa (or best converged + 1 mHa where no start reaches it)",
+            "averaging": "every held-out point in every arm; a run that never reaches the target counts "
+                         "with all its evaluations and its whole wall time",
             "arms": summary, "fallbacks_to_hf": fallbacks, "held_out_reaching_exact": reached_exact,
             "training": {"vqe_seconds": t_data, "vqe_evals": int(np.sum(evals)), "fit_seconds": t_fit,
-                         "fit_steps": 3000, "final_loss": float(hist[-1]), "create_seconds": t_create}}
+                         "fit_steps": 3000, "final_loss": float(hist[-1]), "create_seconds": t_create},
+            "wall_s": time.perf_counter() - t_all}
+
+
+def run_warmstart(args):
+    s = warmstart_summary(args)
+    line = {"metric": s["metric"], "value": s["value"], "unit": "s", "higher_is_better": False, "n_gpus": 1,
+            "dtype": s["dtype"], "data": "synthetic",
+            "config": {"workload": s["workload"], "train_points": s["train_points"],
+                       "held_out_points": s["held_out_points"], "target": s["target"]},
+            "arms": s["arms"], "fallbacks_to_hf": s["fallbacks_to_hf"],
+            "held_out_reaching_exact": s["held_out_reaching_exact"], "training": s["training"]}
     print(json.dumps(line), flush=True)
 
+
+# ------------------------------------------------------------------ per-config entries of the default line
+def _measure(fn, steps, warmup, gpu_index):
+    """CUDA-event time of fn() per step on torch's current stream (the library
+    launches there), after max(3, warmup) untimed calls, with a 512 MB write
+    (> the 129 MB L2) before each timed step; SM clocks are sampled during the
+    timed region only. Returns (timing dict, clocks dict)."""
+    import torch
+    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
+    warm = max(3, warmup)
+    for _ in range(warm):
+        fn()
+    torch.cuda.synchronize()
+    stream = torch.cuda.current_stream()
+    starts = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    ends = [torch.cuda.Event(enable_timing=True) for _ in range(steps)]
+    sampler = ClockSampler(gpu_index)
+    sampler.start()
+    t0 = time.time()
+    for i in range(steps):
+        flush.fill_(float(i))
+        starts[i].record(stream)
+        fn()
+        ends[i].record(stream)
+    torch.cuda.synchronize()
+    t1 = time.time()
+    clocks = sampler.stop(t0, t1)
+    per = [s.elapsed_time(e) for s, e in zip(starts, ends)]
+    return ({"ms_per_step": sum(per) / steps, "ms_median": statistics.median(per), "ms_min": min(per),
+             "steps": steps, "warmup": warm}, clocks)
+
+
+def _e2e(call, steps, h2d, d2h, unit, units_per_call):
+    """Wall-clock rate of a prepared host-buffer C-ABI call (copies from pinned
+    host memory, launches, copies back, stream synchronised inside each call)."""
+    for _ in range(3):
+        call()
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        call()
+    dt = time.perf_counter() - t0
+    return {"value": units_per_call * steps / dt, "unit": unit, "h2d_bytes_per_step": int(h2d),
+            "d2h_bytes_per_step": int(d2h), "steps": steps, "ms_per_call": 1e3 * dt / steps}
+
+
+def _profile_field(path, src_files, field):
+    """A numeric field of a committed ncu summary, if the summary names the
+    current sha256 of the kernel sources it was taken on; else None."""
+    import re
+    try:
+        text = open(os.path.join(ROOT, "profiles", path)).read()
+        h = hashlib.sha256()
+        for f in src_files:
+            with open(os.path.join(ROOT, "paper_2311_01242_gb300", "csrc", f), "rb") as fh:
+                h.update(fh.read())
+    except OSError:
+        return None
+    sha = re.search(r"sources sha256 \(first 16 hex\): `([0-9a-f]+)`", text)
+    m = re.search(re.escape(field) + r": ([0-9.eE+-]+)", text)
+    if not sha or not m or sha.group(1) != h.hexdigest()[:16]:
+        return None
+    return float(m.group(1))
+
+
+def _oracle_rows_and_gate(xs, zs, cs, n, n_alpha, n_beta, exc, n_rows, gate_n=None, seed=0):
+    """Seconds per output row of H psi (oracle.pauli_sum_row over every term,
+    averaged over n_rows sampled sector rows) and per gate pass
+    (oracle.apply_gate on a full 2^gate_n vector); the oracle as it stands."""
+    import numpy as np
+    import oracle
+    sec = oracle.sector_basis(n, n_alpha, n_beta)
+    rng = np.random.default_rng(seed)
+    vals = rng.normal(size=len(sec))
+
+    def amp(idx):
+        pos = np.minimum(np.searchsorted(sec, idx), len(sec) - 1)
+        return np.where(sec[pos] == idx, vals[pos], 0.0)
+
+    rows = rng.choice(len(sec), size=min(n_rows, len(sec)), replace=False)
+    t0 = time.perf_counter()
+    for r in rows:
+        oracle.pauli_sum_row(xs, zs, cs, int(sec[r]), amp)
+    t_row = (time.perf_counter() - t0) / len(rows)
+    gn = gate_n or n
+    psi = rng.normal(size=1 << gn) + 0j
+    t0 = time.perf_counter()
+    oracle.apply_gate(psi, exc, 0.1)
+    t_gate = time.perf_counter() - t0
+    return t_row, t_gate, len(sec)
+
+
+def _adjoint_seconds(t_row, t_gate, D, M):
+    """One energy + adjoint gradient from the oracle's primitives: a forward
+    sweep (M gate passes), H psi (D rows) and a reverse sweep that un-applies
+    every gate to two vectors and applies one generator (counted as 3 gate
+    passes per gate)."""
+    return M * t_gate + D * t_row + 3 * M * t_gate
+
+
+def cpu_baseline_config3(w, exc):
+    import oracle
+    import synth
+    p = w.problems[0]
+    t0 = time.perf_counter()
+    xs, zs, cs = oracle.jordan_wigner(p, w.drop_tol)
+    t_jw = time.perf_counter() - t0
+    # a 30-qubit oracle gate pass needs ~60 GB of host arrays; its cost is linear in
+    # 2^n, so a 24-qubit pass of a double excitation is timed and scaled by 2^6
+    t_row, t_gate24, D = _oracle_rows_and_gate(xs, zs, cs, 30, 5, 5, [0, 1, 20, 21], 60, gate_n=24)
+    t_gate = t_gate24 * 64
+    secs = _adjoint_seconds(t_row, t_gate, D, len(exc))
+    return {"value": 1.0 / secs, "unit": "evals/s", "cores": 1, "kind": "oracle", "extrapolated": True,
+            "sample": f"oracle.pauli_sum_row on 60 sampled rows of the 30-qubit sector ({len(xs)} terms; "
+                      f"{t_row * 1e3:.2f} ms/row) and one oracle.apply_gate pass over a full 2^24 vector "
+                      f"({t_gate24:.2f} s, x64 for 2^30), extrapolated to 4 x 512 gate passes + {D} rows "
+                      f"= {secs:.3g} s per energy+gradient; single process; the oracle's Jordan-Wigner "
+                      f"mapping ({t_jw:.1f} s) untimed"}
+
+
+def cpu_baseline_config2(insts, ns_all, ms_all):
+    import numpy as np
+    import oracle
+    per_n = {}
+    total = 0.0
+    for n in (14, 16, 18, 20):
+        j = int(np.nonzero(ns_all == n)[0][0])
+        p, exc, _ = insts[j]
+        xs, zs, cs = oracle.jordan_wigner(p)
+        na, nb = (p.n_elec + 1) // 2, p.n_elec // 2
+        t_row, t_gate, D = _oracle_rows_and_gate(xs, zs, cs, n, na, nb, exc[0], 40)
+        per_n[n] = (t_row, t_gate, D)
+    for i in range(len(insts)):
+        n = int(ns_all[i])
+        t_row, t_gate, D = per_n[n]
+        total += _adjoint_seconds(t_row, t_gate, D, len(insts[i][1]))
+    return {"value": len(insts) / total, "unit": "instance-evals/s", "cores": 1, "kind": "oracle",
+            "extrapolated": True,
+            "sample": "per qubit count (one instance each of 14/16/18/20 qubits): oracle.pauli_sum_row on 40 "
+                      "sampled sector rows and one oracle.apply_gate pass over the full 2^n vector ("
+                      + ", ".join(f"{n}q {v[0] * 1e3:.2f} ms/row, {v[1] * 1e3:.1f} ms/gate" for n, v in per_n.items())
+                      + f"), extrapolated per instance to 4M gate passes + D rows and summed over the 256 "
+                        f"instances = {total:.3g} s per batch; single process"}
+
+
+def entry_config3(args, gpu_index):
+    """30 qubits (config 3): one energy + adjoint gradient per step."""
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_2311_01242_gb300 as vq
+
+    steps, warmup = min(args.steps, 20), max(3, min(args.warmup, 5))
+    w = synth.config3()
+    p, exc, th = w.problems[0], w.excitations[0], w.thetas[0]
+    t0 = time.perf_counter()
+    H = vq.Hamiltonian.from_problem(p, w.drop_tol)
+    A = vq.Ansatz(30, synth.hf_bitstring(10), exc)
+    ws = vq.alloc_workspace(vq.workspace_bytes(H, A, vq.VQE_WS_GRAD))
+    t_create = time.perf_counter() - t0
+    theta = torch.as_tensor(th).cuda()
+    e_buf = torch.empty(1, dtype=torch.float64, device="cuda")
+    g_buf = torch.empty(len(exc), dtype=torch.float64, device="cuda")
+    tm, clocks = _measure(lambda: vq.energy_grad(H, A, theta, workspace=ws, out=(e_buf, g_buf)), steps, warmup,
+                          gpu_index)
+    e_real = float(e_buf[0])
+    flops, state_bytes = vq.work_estimate(H, A, True)
+    counts = vq.work_counts(H, A)
+    ms = tm["ms_per_step"]
+    # complex128 amplitudes and full complex coefficients (the same kernels' complex form)
+    old = vq.set_flags(vq.VQE_FLAG_FORCE_COMPLEX)
+    try:
+        wsc = vq.alloc_workspace(vq.workspace_bytes(H, A, vq.VQE_WS_GRAD | vq.VQE_WS_COMPLEX))
+        e_c = torch.empty(1, dtype=torch.float64, device="cuda")
+        g_c = torch.empty(len(exc), dtype=torch.float64, device="cuda")
+        tc, clocks_c = _measure(lambda: vq.energy_grad(H, A, theta, workspace=wsc, out=(e_c, g_c)), min(steps, 5),
+                                3, gpu_index)
+        d_e = abs(float(e_c[0]) - e_real)
+        d_g = float((g_c - g_buf).abs().max())
+        del wsc
+    finally:
+        vq.set_flags(old)
+    # end to end through the host-buffer C entry point (a one-instance batch runs
+    # the single-instance launches)
+    B = vq.Batch([H], [A])
+    th_h = torch.as_tensor(th, dtype=torch.float64).reshape(1, -1).pin_memory()
+    e_h = torch.empty(1, dtype=torch.float64).pin_memory()
+    g_h = torch.empty(1, len(exc), dtype=torch.float64).pin_memory()
+    wsh = vq.alloc_workspace(B.host_workspace_bytes(True))
+    th_np, e_np, g_np = th_h.numpy(), e_h.numpy(), g_h.numpy()
+    e2e = _e2e(B.host_call(th_np, e_np, g_np, wsh), min(steps, 10), th_np.nbytes, e_np.nbytes + g_np.nbytes,
+               "evals/s", 1)
+    assert abs(float(e_np[0]) - e_real) <= 1e-12, "host-buffer and device calls disagree"
+    del wsh, B
+    peak_hbm, hbm_src = measured_hbm_gbs()
+    hpsi_dram = _profile_field("k_hpsi_str_config3.md", ["vqe_kernels.cu"], "dram_bytes_per_launch")
+    achieved = flops / (ms / 1e3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS, "kernel": "k_hpsi_str (wide block form) + k_gate_fwd/k_gate_adj",
+            "traffic": hpsi_dram,
+            "dram_bytes_per_step": hpsi_dram,
+            "hbm_gbs": None if hpsi_dram is None else hpsi_dram / (ms / 1e3) / 1e9,
+            "hbm_frac": None if hpsi_dram is None else hpsi_dram / (ms / 1e3) / 1e9 / peak_hbm,
+            "hbm_peak": peak_hbm, "hbm_peak_source": hbm_src,
+            "state_bytes_per_step": state_bytes, "state_gbs": state_bytes / (ms / 1e3) / 1e9,
+            "fp64_flops_per_step": flops, "hpsi_entries": counts["n_entries"], "amplitude_pairs": counts["n_pairs"],
+            "binding": "FP64 pipe and instruction issue of the string-driven H psi (sector-compressed psi and "
+                       "lambda, 72 MB each, stay in L2; DRAM carries the list entries and tables)"}
+    cpu = cpu_baseline_config3(w, exc)
+    return {"workload": "30 qubits, 10 electrons, 512 UCCSD angles (9.0M sector amplitudes), energy + adjoint "
+                        "gradient", "metric": "energy+adjoint-grad evals/s", "value": 1e3 / ms, "unit": "evals/s",
+            **tm, "dtype": "f64 (real amplitudes)", "create_seconds": t_create, "clocks": clocks, "roofline": roof,
+            "e2e": e2e, "cpu_baseline": cpu,
+            "complex128": {"value": 1e3 / tc["ms_per_step"], "unit": "evals/s", **tc, "clocks": clocks_c,
+                           "abs_diff_energy_vs_real": d_e, "max_abs_diff_grad_vs_real": d_g},
+            "l2": "flushed between timed steps (512 MB write)"}
+
+
+def entry_config2(args, gpu_index):
+    """256 uneven instances (config 2): one CUDA-graph replay of the batch per step."""
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_2311_01242_gb300 as vq
+    from paper_2311_01242_gb300 import batch as vb
+
+    steps, warmup = min(args.steps, 20), max(3, min(args.warmup, 5))
+    t0 = time.perf_counter()
+    insts = [synth.config2_instance(j) for j in range(256)]
+    hams = [vq.Hamiltonian.from_problem(p) for p, _, _ in insts]
+    ans = [vq.Ansatz(p.n_qubits, synth.hf_bitstring(p.n_elec), e) for p, e, _ in insts]
+    B = vq.Batch(hams, ans)
+    theta = torch.zeros(256, B.max_params, dtype=torch.float64)
+    for i, (_, _, t) in enumerate(insts):
+        theta[i, :len(t)] = torch.as_tensor(t)
+    theta_d = theta.cuda()
+    choice, timings = vb.autotune(B, theta_d, reps=2)
+    gb = vb.GraphBatch(B)
+    gb(theta_d)
+    t_create = time.perf_counter() - t0
+    tm, clocks = _measure(lambda: gb(), steps, warmup, gpu_index)
+    ms = tm["ms_per_step"]
+    flops = state_bytes = 0.0
+    n_entries = n_pairs = 0
+    for h, a in zip(hams, ans):
+        f, b = vq.work_estimate(h, a, True)
+        c = vq.work_counts(h, a)
+        flops += f
+        state_bytes += b
+        n_entries += c["n_entries"]
+        n_pairs += c["n_pairs"]
+    th_h = theta.clone().pin_memory()
+    e_h = torch.empty(256, dtype=torch.float64).pin_memory()
+    g_h = torch.empty(256, B.max_params, dtype=torch.float64).pin_memory()
+    wsh = vq.alloc_workspace(B.host_workspace_bytes(True))
+    th_np, e_np, g_np = th_h.numpy(), e_h.numpy(), g_h.numpy()
+    e2e = _e2e(B.host_call(th_np, e_np, g_np, wsh), min(steps, 10), th_np.nbytes, e_np.nbytes + g_np.nbytes,
+               "instance-evals/s", 256)
+    e_dev, _ = gb()
+    assert np.abs(e_np - e_dev.cpu().numpy()).max() <= 1e-12, "host-buffer and graph replay disagree"
+    del wsh
+    peak_hbm, hbm_src = measured_hbm_gbs()
+    dram = _profile_field("k_batch_config2.md", ["vqe_kernels.cu", "vqe_batch.cu"], "dram_bytes_per_launch")
+    achieved = flops / (ms / 1e3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS, "kernel": "batched kernels of one graph replay",
+            "traffic": dram, "dram_bytes_per_step": dram,
+            "hbm_gbs": None if dram is None else dram / (ms / 1e3) / 1e9,
+            "hbm_frac": None if dram is None else dram / (ms / 1e3) / 1e9 / peak_hbm,
+            "hbm_peak": peak_hbm, "hbm_peak_source": hbm_src,
+            "state_bytes_per_step": state_bytes, "state_gbs": state_bytes / (ms / 1e3) / 1e9,
+            "fp64_flops_per_step": flops, "hpsi_entries": n_entries, "amplitude_pairs": n_pairs}
+    ns_all, ms_all = synth.configs.config2_sizes()
+    cpu = cpu_baseline_config2(insts, ns_all, ms_all)
+    return {"workload": "256 instances, n in {14,16,18,20}, n/2 electrons, 64-256 UCCSD angles each, energy + "
+                        "adjoint gradient of every instance per step (one CUDA-graph replay)",
+            "metric": "energy+adjoint-grad instance-evals/s", "value": 256e3 / ms, "unit": "instance-evals/s",
+            **tm, "dtype": "f64 (real amplitudes)", "create_seconds": t_create, "autotune": {"choice": choice},
+            "clocks": clocks, "roofline": roof, "e2e": e2e, "cpu_baseline": cpu,
+            "l2": "flushed between timed steps (512 MB write)"}
+
+
+def entry_config1_complex(B, theta, n_inst, M, steps, warmup, gpu_index):
+    """The 12-qubit scan with complex128 amplitudes (VQE_FLAG_FORCE_COMPLEX)."""
+    import torch
+    import paper_2311_01242_gb300 as vq
+    old = vq.set_flags(vq.VQE_FLAG_FORCE_COMPLEX)
+    try:
+        e = torch.empty(n_inst, dtype=torch.float64, device="cuda")
+        g = torch.empty(n_inst, M, dtype=torch.float64, device="cuda")
+        ws = vq.alloc_workspace(B.workspace_bytes(True))
+        tm, clocks = _measure(lambda: B.energy_grad(theta, e, g, ws), steps, warmup, gpu_index)
+    finally:
+        vq.set_flags(old)
+    return {"workload": WORKLOAD + " (complex128 amplitudes and coefficients)", "value": n_inst * 1e3 / tm["ms_per_step"],
+            "unit": UNIT, **tm, "clocks": clocks, "energies": e, "kernel": "k_resident (complex, one CTA per instance)"}
+
+
+def per_config(args, gpu_index, extra=None):
+    """The configurations besides the headline: each entry is timed on its own
+    (CUDA events, L2 flushed, clocks sampled), with its roofline, an end-to-end
+    figure through the host-buffer C entry point and the oracle's rate."""
+    out = dict(extra or {})
+    for name, fn in (("config3", lambda: entry_config3(args, gpu_index)),
+                     ("config2", lambda: entry_config2(args, gpu_index)),
+                     ("warmstart", lambda: warmstart_summary(args))):
+        if name in args.skip:
+            continue
+        t0 = time.perf_counter()
+        try:
+            out[name] = fn()
+        except Exception as ex:  # keep the headline line even if one entry fails
+            out[name] = {"error": f"{type(ex).__name__}: {ex}"}
+        out[name]["entry_wall_s"] = time.perf_counter() - t0
+        import torch
+        torch.cuda.empty_cache()
+    return out
 
 
 def main():
@@ -715,6 +1060,13 @@ def main():
     achieved = flops_per_launch / (ms_per_step / 1000.0) / 1e12
     traffic = profiled_traffic(n_inst)
     probe = vq.probe_fp64()  # untimed: confirms the per-SM FP64 rate behind the peak
+    # the resource the kernel actually uses: 64-bit integer multiplies (fixed-point
+    # sweeps: 2 per lane forward, 3 per lane in reverse, two lanes per pair; H psi:
+    # one per connected entry) against the probed __umul64hi rate, and issue slots
+    wc = vq.work_counts(hams[0], A)
+    muls = n_inst * (10 * wc["n_pairs"] + wc["n_entries"])
+    mul_peak = INT_MUL64_PER_CLK_SM * N_SMS * SM_MAX_MHZ * 1e6
+    issue_pct = _profile_field("k_resident_config1.md", ["vqe_kernels.cu"], "issue_active_pct")
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": max(3, args.warmup), "ms_per_step": ms_per_step, "higher_is_better": True,
@@ -732,13 +1084,32 @@ def main():
                              "the gate sweeps and H psi run it on the integer pipe in 64-bit fixed point, the energy sum in FP64",
                      "probe": {"dfma_per_clock_per_sm": probe["dfma_per_clock_per_sm"],
                                "dependent_dfma_clocks": probe["dependent_dfma_clocks"],
-                               "sm_count": probe["sm_count"]}},
+                               "sm_count": probe["sm_count"]},
+                     "int_mul64_per_launch": muls,
+                     "int_mul64_frac": muls / (ms_per_step / 1000.0) / mul_peak,
+                     "int_mul64_peak_per_s": mul_peak,
+                     "issue_active_pct": issue_pct,
+                     "hbm_gbs": None if traffic is None else traffic / (ms_per_step / 1000.0) / 1e9,
+                     "hbm_frac": None if traffic is None else
+                     traffic / (ms_per_step / 1000.0) / 1e9 / measured_hbm_gbs()[0],
+                     "binding": "dependent latency of each instance's gate chain (fixed-point multiplies, "
+                                "shared-memory loads and one barrier per gate); FP64-equivalent flops, integer "
+                                "multiplies and DRAM bytes are all far below their peaks"},
         "clocks": clocks,
         "e2e": {"value": e2e_value, "unit": UNIT, "h2d_bytes_per_step": int(th_np.nbytes),
                 "d2h_bytes_per_step": int(e_np.nbytes + g_np.nbytes), "steps": K2},
         "gpu_launches": K,
         "wall_s_timed_region": t_wall,
     }
+    if rank == 0 and world == 1 and not args.no_per_config:
+        extra = {}
+        if "complex" not in args.skip:
+            c1 = entry_config1_complex(B, theta, n_inst, M, K, args.warmup, gpu_index_for(local_rank))
+            c1["max_abs_diff_energy_vs_real"] = float((c1.pop("energies") - energies).abs().max())
+            extra["config1_complex128"] = c1
+        del wsh, ws
+        torch.cuda.empty_cache()
+        line["per_config"] = per_config(args, gpu_index_for(local_rank), extra)
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         line["cpu_baseline"] = cpu_baseline()
     if rank == 0:

@@ -26,10 +26,15 @@
  *
  * Memory ownership: create calls copy their host inputs and own device copies
  * of the derived tables until the matching destroy call. theta, energies,
- * gradients and the workspace are caller-owned device memory; the compute
- * calls never allocate, so they can be enqueued on any stream. Every compute
- * call is asynchronous on the given stream (a cudaStream_t; NULL is the legacy
- * default stream) except where noted.
+ * gradients and the workspace are caller-owned device memory. One allocation
+ * happens outside the create calls: the first use of a (Hamiltonian, sector)
+ * pair (vqe_workspace_bytes, vqe_work_counts, vqe_create_batch, or the first
+ * compute call with that pair) builds the pair's connectivity or string tables,
+ * synchronously, and the pair keeps them until the Hamiltonian is destroyed.
+ * After that the compute calls allocate nothing, so make that first call
+ * before any stream capture. Every compute call is asynchronous on the given
+ * stream (a cudaStream_t; NULL is the legacy default stream) except where
+ * noted.
  *
  * Errors: every int-returning call returns VQE_OK (0) or a VQE_ERR_* code and
  * sets a thread-local message readable with vqe_last_error(). Invalid
@@ -272,6 +277,22 @@ int vqe_apply_hamiltonian(vqe_hamiltonian_t h, vqe_ansatz_t a, const double* psi
                           size_t workspace_bytes, vqe_stream_t stream);
 
 /*
+ * lambda = H psi on the ansatz's sector with REAL amplitudes compressed to the
+ * sector: psi_dev and lam_dev hold D = sector_dim (vqe_ansatz_info) device
+ * doubles, entry r the amplitude of the r-th sector state in increasing order
+ * of basis index; energy_dev[0] receives <psi|lambda>. This runs the same
+ * real-amplitude H psi kernels as vqe_energy and vqe_energy_grad (string-driven
+ * for spin sectors, connectivity rows or a scan of all groups otherwise), which
+ * keep the real part of each folded coefficient c * i^{|x&z|}; for the real
+ * Hamiltonians of Eq. 2 that is the whole of H. psi_dev and lam_dev must not
+ * overlap. workspace: vqe_workspace_bytes(h, a, VQE_WS_ENERGY) bytes,
+ * 256-byte aligned. Asynchronous on `stream`.
+ */
+int vqe_apply_hamiltonian_sector(vqe_hamiltonian_t h, vqe_ansatz_t a, const double* psi_dev,
+                                 double* lam_dev, double* energy_dev, void* workspace,
+                                 size_t workspace_bytes, vqe_stream_t stream);
+
+/*
  * ADAPT-VQE operator screening (Sec. 2.1.1, ADAPT-VQE: the ansatz grows one pool
  * operator at a time, chosen and stopped by the energy gradients with respect
  * to the pool). For psi = U(theta)|HF> of ansatz a and lambda = H psi, writes
@@ -300,10 +321,19 @@ int vqe_pool_gradients(vqe_hamiltonian_t h, vqe_ansatz_t a, vqe_ansatz_t pool,
 
 /*
  * A batch of independent instances (the paper runs hundreds of independent
- * simulation jobs over geometries and molecules, abstract and Sec. 4),
- * evaluated by one launch for instances that fit shared memory, and by
- * per-instance streaming passes otherwise. hams/ansatze: n_inst handles (they may repeat) that must
- * outlive the batch. Synchronous; allocates the batch's device descriptors.
+ * simulation jobs over geometries and molecules, abstract and Sec. 4).
+ * Instances whose sector and tables fit shared memory run in one resident
+ * launch (a CTA pair each). All other instances run in ONE persistent launch:
+ * a device work queue of tasks (per instance: HF init, each gate's rotation on
+ * a range of pairs, H psi on a range of output strings or rows, the energy's
+ * partial sums, each gate's adjoint step and gradient partials), taken in a
+ * fixed list-scheduled order by a grid sized to the device, where a task waits
+ * (bounded in time, see vqe_batch_set_wait) only for the earlier tasks of its
+ * own instance; a small finalising launch then sums the partials. Instances
+ * with a gate or sector of more than 262,144 pairs or states are evaluated
+ * after it, one by one. Results equal vqe_energy_grad's on each instance bit
+ * for bit. hams/ansatze: n_inst handles (they may repeat) that must outlive
+ * the batch. Synchronous; allocates the batch's device descriptors and queues.
  */
 int vqe_create_batch(int n_inst, const vqe_hamiltonian_t* hams,
                      const vqe_ansatz_t* ansatze, vqe_batch_t* out);
@@ -341,13 +371,39 @@ int vqe_batch_energy_grad_host(vqe_batch_t b, const double* theta_host, int64_t 
                                void* workspace, size_t workspace_bytes, vqe_stream_t stream);
 
 /*
- * Launch shape of a batch (used by the autotuner): threads per block of the
- * gate-major streaming kernels (multiple of 32 in [64, 512]) and threads that
- * run the gate sweeps of shared-memory-resident instances (multiple of 32 in
- * [32, 512]); 0 keeps the current value. Synchronous. Results do not depend on
- * either value.
+ * Launch shape of a batch (used by the autotuner): CTAs per SM of the
+ * persistent launch (1..16; 0 = as many as fit), amplitude pairs per gate task
+ * of the persistent launch (a multiple of 256; 0 keeps the current value,
+ * initially 1024), and threads that run the gate sweeps of shared-memory-
+ * resident instances (a multiple of 32 in [32, 512]; 0 keeps the current
+ * value). Rebuilds the task queues; synchronous. Results do not depend on any
+ * of them. vqe_batch_get_tuning reports the current values, the persistent
+ * grid and the task count of the gradient queue (any output may be NULL).
  */
-int vqe_batch_set_tuning(vqe_batch_t b, int stream_threads, int sweep_threads);
+int vqe_batch_set_tuning(vqe_batch_t b, int ctas_per_sm, int gate_chunk, int sweep_threads);
+int vqe_batch_get_tuning(vqe_batch_t b, int* ctas_per_sm, int* gate_chunk, int* grid, int64_t* n_tasks);
+
+/*
+ * Bounded waits of the persistent launch. A CTA whose task depends on
+ * unfinished tasks of the same instance polls that instance's progress counter
+ * for at most budget_ns nanoseconds (default 2e9; 1e3 .. 6e11 accepted), then
+ * writes its task's index + 1 into the status word in the workspace, takes no
+ * more tasks and returns; the other CTAs stop at their next task or wait, and
+ * every energy and gradient of the persistent instances is written as NaN.
+ * vqe_batch_energy_grad_host then returns VQE_ERR_TIMEOUT; after the device
+ * call, vqe_batch_status does. probe_task >= 0 makes that task of the queue
+ * wait for a count that no task reaches, so its wait runs out (a check of the
+ * timeout path that stops no GPU); -1 for normal operation.
+ */
+int vqe_batch_set_wait(vqe_batch_t b, int64_t budget_ns, int32_t probe_task);
+
+/*
+ * Status of the last persistent launch that used `workspace` (the batch's
+ * workspace as passed to vqe_batch_energy_grad): synchronises `stream`, reads
+ * the status word, and returns VQE_OK or VQE_ERR_TIMEOUT (the message names the
+ * task and instance whose wait ran out).
+ */
+int vqe_batch_status(vqe_batch_t b, const void* workspace, size_t workspace_bytes, vqe_stream_t stream);
 
 void vqe_destroy_batch(vqe_batch_t b);
 
@@ -422,11 +478,19 @@ int vqe_mlp_adam(int64_t n, float* params, const float* grads, float* m, float* 
  * The caller passes theta, the energy and the gradient as for vqe_energy_grad;
  * the scratch comes from one static device array of VQE_NOALLOC_SCRATCH_BYTES
  * that every GPU loading this library keeps until the process exits.
- * Limit: instances whose streaming workspace (four sector-sized vectors of
- * 8-byte real amplitudes, the cos/sin table and 8 KiB of partials per
- * parameter) exceeds that size are rejected with VQE_ERR_INVALID_ARG and a
- * message; for example 20 qubits with 10 electrons (63,504 sector states) and
- * 512 parameters fits, 26 qubits with 13 electrons (2.9M states) does not.
+ * H psi uses the string or connectivity tables of the (h, sector) pair when an
+ * earlier call already built them (vqe_workspace_bytes, vqe_energy_grad or a
+ * batch; the results then equal vqe_energy_grad's), else a scan of all X-mask
+ * groups per output; the call itself builds nothing.
+ * Limit: instances whose scratch exceeds that size are rejected with
+ * VQE_ERR_INVALID_ARG and a message. The scratch is two sector-sized vectors
+ * (8-byte real amplitudes, 16-byte complex ones), two more for the string
+ * tables (left out, with those tables, when they would not fit), the cos/sin
+ * table and 8 KiB of partials per parameter: for example 20 qubits with 10
+ * electrons (63,504 sector states) and 512 parameters fits on every path, 24
+ * qubits with 10 electrons (627,264 states) and 512 parameters fits with real
+ * amplitudes without the string tables, 26 qubits with 13 electrons (2.9M
+ * states) does not fit.
  * The first call on each device looks up the array's device address (with the
  * device current); make that first call before any stream capture. All calls
  * share the array and it keeps the last call's contents; each call writes every
@@ -444,6 +508,17 @@ int vqe_energy_grad_noalloc(vqe_hamiltonian_t h, vqe_ansatz_t a, const double* t
  */
 int vqe_work_estimate(vqe_hamiltonian_t h, vqe_ansatz_t a, int with_grad,
                       double* fp64_flops, double* state_bytes);
+
+/*
+ * The exact counts behind vqe_work_estimate: amplitude pairs over all gates of
+ * the ansatz (*n_pairs), connected (output, X-mask group) entries of H psi on
+ * the ansatz's sector (*n_entries), and the folded-table additions beyond the
+ * first term of each entry (*extra_adds). Any output may be NULL. Host only;
+ * like vqe_workspace_bytes, the first call for a (Hamiltonian, sector) pair
+ * builds that pair's connectivity or string tables (synchronous, allocates).
+ */
+int vqe_work_counts(vqe_hamiltonian_t h, vqe_ansatz_t a, int64_t* n_pairs, int64_t* n_entries,
+                    double* extra_adds);
 
 /*
  * Device probe (synchronous, allocates and frees a small buffer): the rate of

@@ -17,9 +17,9 @@ _BUILD_DIR = os.path.join(_HERE, "_build")
 LIB_PATH = os.path.join(_BUILD_DIR, "libvqe.so")
 HEADER = os.path.join(_ROOT, "include", "vqe.h")
 
-SOURCES = ["vqe_kernels.cu", "vqe_host.cpp", "vqe_static.cu", "vqe_mlp.cu", "vqe_probe.cu", "vqe_aux.cu",
-           "vqe_pool.cu"]
-DEPS = SOURCES + ["vqe_internal.h"]
+SOURCES = ["vqe_kernels.cu", "vqe_batch.cu", "vqe_host.cpp", "vqe_static.cu", "vqe_mlp.cu", "vqe_probe.cu",
+           "vqe_aux.cu", "vqe_pool.cu"]
+DEPS = SOURCES + ["vqe_internal.h", "vqe_device.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ARCH + ["-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC"]
 
@@ -112,6 +112,7 @@ PROTOTYPES = {
     "vqe_energy_grad": (ctypes.c_int, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_sz, c_vp]),
     "vqe_state": (ctypes.c_int, [c_vp, c_vp, c_vp, c_vp, c_vp, c_sz, c_vp]),
     "vqe_apply_hamiltonian": (ctypes.c_int, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_sz, c_vp]),
+    "vqe_apply_hamiltonian_sector": (ctypes.c_int, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_sz, c_vp]),
     "vqe_pool_workspace_bytes": (c_sz, [c_vp, c_vp, c_vp]),
     "vqe_pool_gradients": (ctypes.c_int, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_sz, c_vp]),
     "vqe_create_batch": (ctypes.c_int, [ctypes.c_int, c_vp, c_vp, P(c_vp)]),
@@ -120,12 +121,16 @@ PROTOTYPES = {
     "vqe_batch_energy_grad": (ctypes.c_int, [c_vp, c_vp, c_i64, c_vp, c_vp, c_i64, c_vp, c_sz, c_vp]),
     "vqe_batch_host_workspace_bytes": (c_sz, [c_vp, ctypes.c_int]),
     "vqe_batch_energy_grad_host": (ctypes.c_int, [c_vp, c_vp, c_i64, c_vp, c_vp, c_i64, c_vp, c_sz, c_vp]),
-    "vqe_batch_set_tuning": (ctypes.c_int, [c_vp, ctypes.c_int, ctypes.c_int]),
+    "vqe_batch_set_tuning": (ctypes.c_int, [c_vp, ctypes.c_int, ctypes.c_int, ctypes.c_int]),
+    "vqe_batch_get_tuning": (ctypes.c_int, [c_vp, P(ctypes.c_int), P(ctypes.c_int), P(ctypes.c_int), P(c_i64)]),
+    "vqe_batch_set_wait": (ctypes.c_int, [c_vp, c_i64, c_i32]),
+    "vqe_batch_status": (ctypes.c_int, [c_vp, c_vp, c_sz, c_vp]),
     "vqe_destroy_batch": (None, [c_vp]),
     "vqe_batched_workspace_bytes": (c_sz, [ctypes.c_int, c_vp, c_vp, ctypes.c_int]),
     "vqe_energy_batched": (ctypes.c_int, [ctypes.c_int, c_vp, c_vp, c_vp, c_vp, c_vp, c_sz, c_vp]),
     "vqe_energy_grad_batched": (ctypes.c_int, [ctypes.c_int, c_vp, c_vp, c_vp, c_vp, c_vp, c_vp, c_sz, c_vp]),
     "vqe_work_estimate": (ctypes.c_int, [c_vp, c_vp, ctypes.c_int, P(c_dbl), P(c_dbl)]),
+    "vqe_work_counts": (ctypes.c_int, [c_vp, c_vp, P(c_i64), P(c_i64), P(c_dbl)]),
     "vqe_energy_grad_noalloc": (ctypes.c_int, [c_vp, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "vqe_probe_fp64": (ctypes.c_int, [P(c_dbl), P(c_dbl), P(c_dbl), P(ctypes.c_int), P(ctypes.c_int), P(c_sz),
                                       P(ctypes.c_int)]),

@@ -266,6 +266,20 @@ def apply_hamiltonian(h, a, psi, workspace=None, stream=None):
     return lam, e[0]
 
 
+def apply_hamiltonian_sector(h, a, psi, workspace=None, stream=None):
+    """(lambda, <psi|lambda>) for a real float64 CUDA vector psi compressed to the
+    ansatz's sector (vqe_apply_hamiltonian_sector): the real-amplitude H psi
+    kernels of the energy and gradient calls."""
+    assert psi.dtype == torch.float64 and psi.is_cuda and psi.is_contiguous()
+    if workspace is None:
+        workspace = alloc_workspace(workspace_bytes(h, a, VQE_WS_ENERGY), psi.device)
+    lam = torch.empty_like(psi)
+    e = torch.empty(1, dtype=torch.float64, device=psi.device)
+    _check(_lib().vqe_apply_hamiltonian_sector(h.handle, a.handle, _ptr(psi), _ptr(lam), _ptr(e), _ptr(workspace),
+                                               workspace.numel(), _stream(stream)))
+    return lam, e[0]
+
+
 def pool_workspace_bytes(h, a, pool):
     nb = _lib().vqe_pool_workspace_bytes(h.handle, a.handle, pool.handle)
     if nb == 0:
@@ -295,6 +309,13 @@ def work_estimate(h, a, with_grad=True):
     b = ctypes.c_double()
     _check(_lib().vqe_work_estimate(h.handle, a.handle, int(bool(with_grad)), ctypes.byref(f), ctypes.byref(b)))
     return f.value, b.value
+
+
+def work_counts(h, a):
+    """vqe_work_counts: {"n_pairs", "n_entries", "extra_adds"} of the pair (h, a)."""
+    p, e, x = ctypes.c_int64(), ctypes.c_int64(), ctypes.c_double()
+    _check(_lib().vqe_work_counts(h.handle, a.handle, ctypes.byref(p), ctypes.byref(e), ctypes.byref(x)))
+    return {"n_pairs": p.value, "n_entries": e.value, "extra_adds": x.value}
 
 
 class Batch:
@@ -341,6 +362,26 @@ class Batch:
             self.handle, _ptr(theta_host), theta_host.shape[1], _ptr(energies_host), _ptr(grads_host),
             grads_host.shape[1] if grads_host is not None else 0, _ptr(workspace), workspace.numel(),
             _stream(stream)))
+
+    def set_tuning(self, ctas_per_sm=0, gate_chunk=0, sweep_threads=0):
+        """vqe_batch_set_tuning (0 keeps a value; ctas_per_sm 0 = as many as fit)."""
+        _check(self._lib.vqe_batch_set_tuning(self.handle, int(ctas_per_sm), int(gate_chunk), int(sweep_threads)))
+
+    def tuning(self):
+        """{"ctas_per_sm", "gate_chunk", "grid", "n_tasks"} of the persistent launch."""
+        c, g, gr = ctypes.c_int(), ctypes.c_int(), ctypes.c_int()
+        nt = ctypes.c_int64()
+        _check(self._lib.vqe_batch_get_tuning(self.handle, ctypes.byref(c), ctypes.byref(g), ctypes.byref(gr),
+                                              ctypes.byref(nt)))
+        return {"ctas_per_sm": c.value, "gate_chunk": g.value, "grid": gr.value, "n_tasks": nt.value}
+
+    def set_wait(self, budget_ns=2_000_000_000, probe_task=-1):
+        """vqe_batch_set_wait: the persistent launch's wait bound (and the timeout probe)."""
+        _check(self._lib.vqe_batch_set_wait(self.handle, int(budget_ns), int(probe_task)))
+
+    def status(self, workspace, stream=None):
+        """vqe_batch_status of the last persistent launch on `workspace` (raises VQEError on a timeout)."""
+        _check(self._lib.vqe_batch_status(self.handle, _ptr(workspace), workspace.numel(), _stream(stream)))
 
     def host_call(self, theta_host, energies_host, grads_host, workspace, stream=None):
         """energy_grad_host on fixed host arrays, marshalled once: the returned

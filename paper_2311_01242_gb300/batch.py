@@ -2,12 +2,14 @@
 
 A batch of independent instances (geometries, molecules of uneven size) is
 evaluated by libvqe in one resident launch for the instances that fit shared
-memory and, for the others, by gate-major streaming launches that cover every
-instance at once (one launch per gate index, one for H psi). GraphBatch
-captures that whole launch sequence once and replays it with new angles
+memory and, for the others, in one persistent launch that works through a
+device queue of per-instance tasks (gate rotations on ranges of pairs, H psi on
+ranges of output strings, reductions), plus a small finalising launch.
+GraphBatch captures that launch sequence once and replays it with new angles
 written in place into the captured theta buffer. autotune() times the batch's
-launch shapes and keeps the fastest, cached in a JSON file keyed by the
-batch's sizes; results never depend on the launch shape.
+launch shapes (persistent CTAs per SM, amplitude pairs per gate task, resident
+sweep width) and keeps the fastest, cached in a JSON file keyed by the batch's
+sizes; results never depend on the launch shape.
 """
 import hashlib
 import json
@@ -67,9 +69,9 @@ def _time(batch, theta, energies, grads, ws, reps):
     return start.elapsed_time(end) / reps
 
 
-def autotune(batch, theta, stream_threads=(128, 256, 512), sweep_threads=(64, 128, 256), reps=5,
+def autotune(batch, theta, ctas_per_sm=(1, 2), gate_chunk=(512, 1024, 2048), sweep_threads=(128,), reps=5,
              cache_path=None):
-    """Pick (stream_threads, sweep_threads) by timing; returns (choice, timings in ms)."""
+    """Pick (ctas_per_sm, gate_chunk, sweep_threads) by timing; returns (choice, timings in ms)."""
     lib = api._lib()
     sig = signature(batch.hams, batch.ansatze)
     cache = {}
@@ -77,23 +79,24 @@ def autotune(batch, theta, stream_threads=(128, 256, 512), sweep_threads=(64, 12
         with open(cache_path) as f:
             cache = json.load(f)
     if sig in cache:
-        st, sw = cache[sig]["choice"]
-        api._check(lib.vqe_batch_set_tuning(batch.handle, st, sw))
-        return (st, sw), cache[sig]["timings"]
+        choice = tuple(cache[sig]["choice"])
+        api._check(lib.vqe_batch_set_tuning(batch.handle, *choice))
+        return choice, cache[sig]["timings"]
     energies = torch.empty(batch.n_inst, dtype=torch.float64, device=theta.device)
     grads = torch.empty(batch.n_inst, theta.shape[1], dtype=torch.float64, device=theta.device)
     ws = api.alloc_workspace(batch.workspace_bytes(True), theta.device)
     timings = {}
-    for st in stream_threads:
-        for sw in sweep_threads:
-            api._check(lib.vqe_batch_set_tuning(batch.handle, st, sw))
-            timings[f"{st},{sw}"] = _time(batch, theta, energies, grads, ws, reps)
+    for c in ctas_per_sm:
+        for g in gate_chunk:
+            for sw in sweep_threads:
+                api._check(lib.vqe_batch_set_tuning(batch.handle, c, g, sw))
+                timings[f"{c},{g},{sw}"] = _time(batch, theta, energies, grads, ws, reps)
     best = min(timings, key=timings.get)
-    st, sw = (int(v) for v in best.split(","))
-    api._check(lib.vqe_batch_set_tuning(batch.handle, st, sw))
+    choice = tuple(int(v) for v in best.split(","))
+    api._check(lib.vqe_batch_set_tuning(batch.handle, *choice))
     if cache_path:
-        cache[sig] = {"choice": [st, sw], "timings": timings}
+        cache[sig] = {"choice": list(choice), "timings": timings}
         os.makedirs(os.path.dirname(os.path.abspath(cache_path)), exist_ok=True)
         with open(cache_path, "w") as f:
             json.dump(cache, f, indent=1)
-    return (st, sw), timings
+    return choice, timings

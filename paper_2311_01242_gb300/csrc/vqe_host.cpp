@@ -10,6 +10,7 @@
 #include <map>
 #include <memory>
 #include <mutex>
+#include <queue>
 #include <string>
 #include <thread>
 #include <tuple>
@@ -277,6 +278,7 @@ struct vqe_hamiltonian_s {
     uint32_t* d_ell = nullptr;
     uint16_t* d_ell16 = nullptr;      // device-built 16-bit table (large sectors)
     uint32_t* d_ellp = nullptr;       // packed entries for the resident kernel (small sectors)
+    bool ellp_fast = false;           // d_ellp holds single-slot entries (flag bit 31)
     int64_t nnz = 0;                  // connected (output, group) pairs
     double extra_adds = 0;            // sum over nnz of (entries - 1)
     // spin sectors: alpha/beta string tables of the string-driven H psi
@@ -343,42 +345,41 @@ struct vqe_ansatz_s {
   }
 };
 
-// Gate-major streaming of the batch's instances that do not fit shared memory
-// (real-amplitude path): device-side plan built once at batch creation.
+// Persistent evaluation of the batch's instances that do not fit shared memory
+// (real-amplitude path): per-slot workspace offsets and two task queues (with
+// and without the gradient), built at batch creation and again when the
+// tuning changes.
+struct PersistQueue {
+  std::vector<vqe::PTask> tasks;  // queue order
+  std::vector<vqe::PFinal> finals;
+  int n_grad_rows = 0;
+  vqe::PTask* d_tasks = nullptr;
+  vqe::PFinal* d_finals = nullptr;
+  ~PersistQueue() {
+    dfree(d_tasks);
+    dfree(d_finals);
+  }
+};
+
 struct StreamBatch {
-  std::vector<int> slots;                 // batch index of each streamed slot
-  std::vector<InstDesc> descs;
-  std::vector<int64_t> psi_off, lam_off, am_off, ebase, gbase;
-  vqe::BatchSegs str_segs{};               // total 0: H psi by connectivity rows
-  size_t str_smem = 0;
-  int32_t* d_str_inst = nullptr;
-  int64_t* d_str_pref = nullptr;
-  int64_t* d_am_off = nullptr;
-  int Mmax = 0;
-  std::vector<vqe::BatchSegs> gate_segs;  // per gate index, device pointers inside
-  vqe::BatchSegs out_segs{};
-  int64_t n_gm = 0;
-  size_t cs_off = 0, ebuf_off = 0, gbuf_off = 0, total_energy = 0, total_grad = 0;
-  int threads = 256;
+  std::vector<int> slots;                 // batch index of each persistent slot
+  std::vector<int> big;                   // batch indices evaluated one by one (too large for a slot)
+  std::vector<InstDesc> descs;            // per slot
+  std::vector<vqe::PSlot> pslots;
   InstDesc* d_desc = nullptr;
-  int64_t *d_psi_off = nullptr, *d_lam_off = nullptr, *d_ebase = nullptr, *d_gbase = nullptr;
-  int32_t *d_seg_inst = nullptr, *d_out_inst = nullptr, *d_gm_inst = nullptr, *d_gm_gate = nullptr;
-  int64_t *d_seg_pref = nullptr, *d_out_pref = nullptr;
+  vqe::PSlot* d_slots = nullptr;
+  std::unique_ptr<PersistQueue> q[2];     // 0: energy only, 1: with gradient
+  size_t counters_off = 0, persist_bytes = 0, big_bytes = 0;
+  size_t smem = 0;
+  int grid = 0;
+  int ctas_per_sm = 0;                    // 0: as many as fit
+  int gate_chunk = 1024;                  // pairs per FWD/ADJ task (multiple of 256)
+  long long budget_ns = 2000000000ll;
+  int probe_task = -1;
+  int last_queue = 1;                     // queue of the last launch (for status messages)
   ~StreamBatch() {
     dfree(d_desc);
-    dfree(d_psi_off);
-    dfree(d_lam_off);
-    dfree(d_ebase);
-    dfree(d_gbase);
-    dfree(d_seg_inst);
-    dfree(d_out_inst);
-    dfree(d_gm_inst);
-    dfree(d_gm_gate);
-    dfree(d_seg_pref);
-    dfree(d_out_pref);
-    dfree(d_str_inst);
-    dfree(d_str_pref);
-    dfree(d_am_off);
+    dfree(d_slots);
   }
 };
 
@@ -753,8 +754,12 @@ const vqe_hamiltonian_s::Ell* get_ell(vqe_hamiltonian_t h, vqe_ansatz_t a, int* 
         return nullptr;
       }
       if (W > 0 && D <= 32767 && G <= 8191) {
-        // packed entries for the resident kernel: source rank, source pattern, group
+        // packed entries for the resident kernel: source rank, source pattern,
+        // group; with G <= 4095, single-term groups carry their signed table slot
+        // instead (no group record or mask to read in the kernel)
         const uint32_t lo_mask = (1u << a->lo_bits) - 1u;
+        const bool fast = G <= 4095;
+        e.ellp_fast = fast;
         std::vector<uint32_t> packed(ell.size(), vqe::kEllPad);
         parallel_for(D, [&](int64_t lo, int64_t hi) {
           for (int64_t r = lo; r < hi; ++r) {
@@ -767,7 +772,11 @@ const vqe_hamiltonian_s::Ell* get_ell(vqe_hamiltonian_t h, vqe_ansatz_t a, int* 
               uint32_t u = 0;
               for (int b = 0; b < gr.ubits; ++b) u |= ((src >> ((gr.upos >> (8 * b)) & 31u)) & 1u) << b;
               const uint32_t rs = a->rank_hi[src >> a->lo_bits] + a->rank_lo[src & lo_mask];
-              packed[size_t(j) * size_t(D) + size_t(r)] = rs | (u << 15) | (g << 19);
+              const uint32_t slot = uint32_t(gr.vbeg) + u;
+              uint32_t v = rs | (u << 15) | (g << 19);
+              if (fast && gr.kind == 0 && gr.eend == gr.ebeg + 1 && slot < 32768u)
+                v = rs | (uint32_t(pc32(src & h->emask[gr.ebeg]) & 1) << 15) | (slot << 16) | 0x80000000u;
+              packed[size_t(j) * size_t(D) + size_t(r)] = v;
             }
           }
         });
@@ -818,6 +827,7 @@ InstDesc make_desc(vqe_hamiltonian_t h, vqe_ansatz_t a, const vqe_hamiltonian_s:
   d.hf_rank = int32_t(a->rank_hi[a->hf >> a->lo_bits] + a->rank_lo[a->hf & ((1u << a->lo_bits) - 1u)]);
   d.str = e->use_str ? e->d_str : nullptr;
   d.ellp = e->d_ellp;
+  d.ellp_fast = e->ellp_fast ? 1 : 0;
   d.hbound = h->d_bound;
   d.gates = a->d_gates;
   d.pair_off = a->d_pair_off;
@@ -985,24 +995,54 @@ int run_single(vqe_hamiltonian_t h, vqe_ansatz_t a, const double* theta, double*
 
 namespace vqe {
 
-// Descriptor, streaming plan and scratch layout for vqe_energy_grad_noalloc:
-// scan-mode H psi (no connectivity table is built or used), real amplitudes
-// unless complex arithmetic is forced. Allocates no device memory.
-int prepare_noalloc(vqe_hamiltonian_s* h, vqe_ansatz_s* a, bool with_grad, InstDesc* d, StreamPlan* sp,
-                    bool* real, size_t off[5], size_t* need) {
+// Descriptor, streaming plan and scratch layout for vqe_energy_grad_noalloc.
+// H psi uses the (Hamiltonian, sector) pair's string or connectivity tables
+// when an earlier call already built them, else a scan of all groups with an
+// integer sector test; nothing is built or allocated here. Only the buffers the
+// chosen path touches get scratch: the alpha-major copies only for the
+// string-driven H psi. Real amplitudes unless complex arithmetic is forced.
+int prepare_noalloc(vqe_hamiltonian_s* h, vqe_ansatz_s* a, bool with_grad, size_t limit, InstDesc* d,
+                    StreamPlan* sp, bool* real, size_t off[7], size_t* need) {
   const int rc = check_pair(h, a);
   if (rc) return rc;
   *real = use_real();
-  const vqe_hamiltonian_s::Ell none;
-  *d = make_desc(h, a, &none, 0);
-  *sp = plan(a, &none);
-  const WsLayout L = ws_layout(a, !*real, with_grad);
-  off[0] = L.psi;
-  off[1] = L.lam;
-  off[2] = L.cs;
-  off[3] = L.epart;
-  off[4] = L.gpart;
-  *need = L.total;
+  static const vqe_hamiltonian_s::Ell none;
+  const vqe_hamiltonian_s::Ell* e = &none;
+  {
+    std::lock_guard<std::mutex> lock(h->mu);
+    auto it = h->ells.find(a->key());
+    if (it != h->ells.end()) e = &it->second;  // entries are never erased while h lives
+  }
+  *d = make_desc(h, a, e, 0);
+  *sp = plan(a, e);
+  // the string-driven H psi needs two more sector-sized vectors; when they do
+  // not fit, the connectivity rows (if built) or the group scan serve instead
+  const size_t amp = *real ? 8 : 16;
+  const size_t vec0 = align256(std::max<size_t>(a->sector.size(), 1) * amp);
+  const size_t fixed = align256(size_t(std::max(a->M, 1)) * 16) + align256(size_t(vqe::kMaxPartials) * 8) +
+                       (with_grad ? align256(size_t(std::max(a->M, 1)) * vqe::kMaxPartials * 8) : 0);
+  if (sp->use_str && 4 * vec0 + fixed > limit) sp->use_str = false;
+  const size_t vec = align256(std::max<size_t>(a->sector.size(), 1) * amp);
+  size_t o = 0;
+  off[0] = o;  // psi
+  o += vec;
+  off[1] = o;  // lambda
+  o += vec;
+  if (sp->use_str) {
+    off[2] = o;  // alpha-major psi
+    o += vec;
+    off[3] = o;  // alpha-major lambda
+    o += vec;
+  } else {
+    off[2] = off[3] = 0;
+  }
+  off[4] = o;  // cos/sin
+  o += align256(size_t(std::max(a->M, 1)) * 16);
+  off[5] = o;  // energy partials
+  o += align256(size_t(vqe::kMaxPartials) * 8);
+  off[6] = o;  // gradient partials
+  if (with_grad) o += align256(size_t(std::max(a->M, 1)) * vqe::kMaxPartials * 8);
+  *need = o;
   return VQE_OK;
 }
 
@@ -1721,6 +1761,25 @@ int vqe_apply_hamiltonian(vqe_hamiltonian_t h, vqe_ansatz_t a, const double* psi
   return VQE_OK;
 }
 
+int vqe_apply_hamiltonian_sector(vqe_hamiltonian_t h, vqe_ansatz_t a, const double* psi, double* lam_out,
+                                 double* energy, void* ws, size_t ws_bytes, vqe_stream_t stream) {
+  int rc = check_pair(h, a);
+  if (rc) return rc;
+  if (!psi || !lam_out || !energy) return fail(VQE_ERR_INVALID_ARG, "NULL device pointer");
+  if (psi == lam_out) return fail(VQE_ERR_INVALID_ARG, "psi and lambda must not overlap");
+  const auto* e = get_ell(h, a, &rc);
+  if (!e) return rc;
+  const WsLayout L = ws_layout(a, false, false);
+  if ((rc = check_ws(ws, ws_bytes, L.total))) return rc;
+  InstDesc d = make_desc(h, a, e, 0);
+  vqe::StreamBuffers b = buffers(ws, L);
+  b.psi = const_cast<double*>(psi);  // read only: H psi writes lambda and the alpha-major copies
+  b.lam = lam_out;
+  cudaError_t ce = vqe::stream_apply_h_real(d, plan(a, e), b, energy, static_cast<cudaStream_t>(stream));
+  if (ce != cudaSuccess) return cuda_fail(ce, "apply_hamiltonian_sector launch");
+  return VQE_OK;
+}
+
 size_t vqe_pool_workspace_bytes(vqe_hamiltonian_t h, vqe_ansatz_t a, vqe_ansatz_t pool) {
   if (check_pair(h, a)) return 0;
   if (!pool) {
@@ -1765,126 +1824,287 @@ int vqe_pool_gradients(vqe_hamiltonian_t h, vqe_ansatz_t a, vqe_ansatz_t pool, c
   return VQE_OK;
 }
 
+// Largest instance a persistent slot takes: every per-gate pair list and the
+// sector fit one pass of 1024 blocks of 256 threads, so the slot's reductions
+// follow the single-instance kernels' partial sums exactly.
+constexpr int64_t kSlotMaxItems = int64_t(vqe::kMaxPartials) * vqe::kStreamThreads;
+
+static bool slot_fits(vqe_ansatz_t a) {
+  if (int64_t(a->sector.size()) > kSlotMaxItems) return false;
+  for (int m = 0; m < a->M; ++m)
+    if (a->pair_off[m + 1] - a->pair_off[m] > kSlotMaxItems) return false;
+  return true;
+}
+
+// Builds both task queues of the persistent launch for the current grid and
+// gate chunk. Each slot is a chain of levels (INIT, FWD 0..M-1, [GATHER], HPSI,
+// [SCATTER], DOT, then ADJ M-1..0 with the gradient); a task waits for every
+// task of the earlier levels of its slot. The queue order comes from a list
+// schedule of rough task costs over the grid's CTAs: whenever a CTA frees up,
+// it takes the ready task whose level has the longest remaining chain after it
+// (critical path first), so long instances start early and short ones fill in.
+static int build_queues(vqe_batch_s* B) {
+  StreamBatch& sb = B->sb;
+  const int n = int(sb.slots.size());
+  const int64_t gc = sb.gate_chunk;
+  for (int mode = 0; mode < 2; ++mode) {
+    const bool grad = mode == 1;
+    struct Lvl {
+      int slot;
+      int64_t t0, nt;  // first task (in `tasks`) and count
+      double cost, bottom;
+    };
+    std::vector<vqe::PTask> tasks;
+    std::vector<double> cost;
+    std::vector<Lvl> lv;
+    std::vector<int64_t> slot_lv0(n + 1, 0);
+    std::unique_ptr<PersistQueue> Q(new PersistQueue);
+    for (int s = 0; s < n; ++s) {
+      const int bi = sb.slots[s];
+      vqe_ansatz_t a = B->ans[bi];
+      const auto& d = sb.descs[s];
+      const int64_t D = int64_t(a->sector.size());
+      int rc2 = VQE_OK;
+      const auto* e = get_ell(B->hams[bi], a, &rc2);
+      if (!e) return rc2;
+      const bool str = d.str != nullptr;
+      int32_t done = 0;  // tasks of the slot in earlier levels
+      slot_lv0[s] = int64_t(lv.size());
+      auto level = [&](auto&& add) {
+        Lvl L{s, int64_t(tasks.size()), 0, 0.0, 0.0};
+        add();
+        L.nt = int64_t(tasks.size()) - L.t0;
+        if (L.nt == 0) return;
+        for (int64_t t = L.t0; t < L.t0 + L.nt; ++t) {
+          tasks[t].need = done;
+          L.cost = std::max(L.cost, cost[t]);
+        }
+        done += int32_t(L.nt);
+        lv.push_back(L);
+      };
+      auto task = [&](int kind, int m, int64_t lo, int64_t hi, int64_t aux, double c) {
+        vqe::PTask t;
+        t.slot = s;
+        t.kind = kind;
+        t.m = m;
+        t.need = 0;
+        t.lo = lo;
+        t.hi = hi;
+        t.aux = aux;
+        tasks.push_back(t);
+        cost.push_back(c);
+      };
+      // cost estimates in ns per CTA (only their proportions matter)
+      level([&] { task(vqe::PT_INIT, 0, 0, D, 0, 1000.0 + 0.5 * double(D)); });
+      for (int m = 0; m < a->M; ++m)
+        level([&] {
+          const int64_t P = a->pair_off[m + 1] - a->pair_off[m];
+          for (int64_t lo = 0; lo < P; lo += gc) {
+            const int64_t hi = std::min(P, lo + gc);
+            task(vqe::PT_FWD, m, lo, hi, 0, 1500.0 + 0.6 * double(hi - lo));
+          }
+        });
+      const int64_t ch = 16384;  // entries per GATHER / SCATTER task
+      if (str)
+        level([&] {
+          for (int64_t lo = 0; lo < D; lo += ch) task(vqe::PT_GATHER, 0, lo, std::min(D, lo + ch), 0, 1500.0 + 0.3 * double(std::min(ch, D - lo)));
+        });
+      level([&] {
+        const double per_entry = 1.6;  // measured order of magnitude of the string-driven H psi per CTA
+        if (str) {
+          const int Da = e->str.Da, Db = e->str.Db;
+          const int per = Db < vqe::kStrMinDb ? vqe::kStrWarps : 1;
+          for (int lo = 0; lo < Da; lo += per) {
+            const int hi = std::min(Da, lo + per);
+            task(vqe::PT_HPSI, 0, lo, hi, 0, 2000.0 + per_entry * double(e->nnz) * double(hi - lo) / double(Da));
+          }
+        } else {
+          for (int64_t lo = 0; lo < D; lo += vqe::kPersistThreads) {
+            const int64_t hi = std::min(D, lo + vqe::kPersistThreads);
+            task(vqe::PT_HPSI, 0, lo, hi, 0, 2000.0 + 3.0 * per_entry * double(e->nnz) * double(hi - lo) / double(D));
+          }
+        }
+      });
+      if (str)
+        level([&] {
+          for (int64_t lo = 0; lo < D; lo += ch) task(vqe::PT_SCATTER, 0, lo, std::min(D, lo + ch), 0, 1500.0 + 0.3 * double(std::min(ch, D - lo)));
+        });
+      const int64_t nbD = (std::max<int64_t>(D, 1) + vqe::kPersistThreads - 1) / vqe::kPersistThreads;
+      level([&] {
+        for (int64_t lo = 0; lo < nbD; lo += 16) task(vqe::PT_DOT, 0, lo, std::min(nbD, lo + 16), 0, 1500.0 + 150.0 * double(std::min<int64_t>(16, nbD - lo)));
+      });
+      if (grad) {
+        // gate m's partials start after those of gates 0..m-1
+        std::vector<int64_t> gbase(a->M + 1, 0);
+        for (int m = 0; m < a->M; ++m) {
+          const int64_t P = a->pair_off[m + 1] - a->pair_off[m];
+          gbase[m + 1] = gbase[m] + std::max<int64_t>(1, (P + vqe::kStreamThreads - 1) / vqe::kStreamThreads);
+        }
+        for (int m = a->M - 1; m >= 0; --m)
+          level([&] {
+            const int64_t P = a->pair_off[m + 1] - a->pair_off[m];
+            for (int64_t lo = 0; lo < P; lo += gc) {
+              const int64_t hi = std::min(P, lo + gc);
+              task(vqe::PT_ADJ, m, lo, hi, gbase[m], 2000.0 + 1.0 * double(hi - lo));
+            }
+          });
+      }
+    }
+    slot_lv0[n] = int64_t(lv.size());
+    // remaining chain after each level (inclusive)
+    for (int s = 0; s < n; ++s) {
+      double acc = 0.0;
+      for (int64_t l = slot_lv0[s + 1] - 1; l >= slot_lv0[s]; --l) {
+        acc += lv[l].cost;
+        lv[l].bottom = acc;
+      }
+    }
+    // list schedule over the grid's CTAs
+    std::vector<int64_t> level_of(tasks.size());
+    for (int64_t l = 0; l < int64_t(lv.size()); ++l)
+      for (int64_t t = lv[l].t0; t < lv[l].t0 + lv[l].nt; ++t) level_of[t] = l;
+    typedef std::pair<double, int64_t> PQ;  // (priority, -task) max-heap; (time, level) min-heap
+    std::priority_queue<std::pair<double, int64_t>> ready;
+    std::priority_queue<PQ, std::vector<PQ>, std::greater<PQ>> running;
+    std::vector<int64_t> left(lv.size());
+    for (int64_t l = 0; l < int64_t(lv.size()); ++l) left[l] = lv[l].nt;
+    auto push_level = [&](int64_t l) {
+      for (int64_t t = lv[l].t0; t < lv[l].t0 + lv[l].nt; ++t) ready.push(std::make_pair(lv[l].bottom, -t));
+    };
+    for (int s = 0; s < n; ++s)
+      if (slot_lv0[s] < slot_lv0[s + 1]) push_level(slot_lv0[s]);
+    int free_ctas = std::max(1, sb.grid);
+    double now = 0.0;
+    Q->tasks.reserve(tasks.size());
+    while (Q->tasks.size() < tasks.size()) {
+      while (free_ctas > 0 && !ready.empty()) {
+        const int64_t t = -ready.top().second;
+        ready.pop();
+        Q->tasks.push_back(tasks[t]);
+        running.push(std::make_pair(now + cost[t], level_of[t]));
+        --free_ctas;
+      }
+      if (running.empty()) break;  // cannot happen: every level follows a finished one
+      const PQ done = running.top();
+      running.pop();
+      now = done.first;
+      ++free_ctas;
+      const int64_t l = done.second;
+      if (--left[l] == 0 && l + 1 < int64_t(lv.size()) && lv[l + 1].slot == lv[l].slot) push_level(l + 1);
+    }
+    if (Q->tasks.size() != tasks.size()) return fail(VQE_ERR_INVALID_ARG, "persistent queue construction failed");
+    if (tasks.size() > size_t(INT32_MAX / 2)) return fail(VQE_ERR_UNSUPPORTED, "batch has too many tasks");
+    // finalising rows: gradients first, then energies
+    if (grad) {
+      for (int s = 0; s < n; ++s) {
+        vqe_ansatz_t a = B->ans[sb.slots[s]];
+        int64_t base = 0;
+        for (int m = 0; m < a->M; ++m) {
+          const int64_t P = a->pair_off[m + 1] - a->pair_off[m];
+          const int64_t nb = std::max<int64_t>(1, (P + vqe::kStreamThreads - 1) / vqe::kStreamThreads);
+          Q->finals.push_back(vqe::PFinal{sb.pslots[s].gp + base * 8, int32_t(nb), m, sb.descs[s].inst, 2.0});
+          base += nb;
+        }
+      }
+      Q->n_grad_rows = int(Q->finals.size());
+    }
+    for (int s = 0; s < n; ++s) {
+      const int64_t D = int64_t(B->ans[sb.slots[s]]->sector.size());
+      const int64_t nbD = (std::max<int64_t>(D, 1) + vqe::kPersistThreads - 1) / vqe::kPersistThreads;
+      Q->finals.push_back(vqe::PFinal{sb.pslots[s].ep, int32_t(nbD), -1, sb.descs[s].inst, 1.0});
+    }
+    int rc;
+    if ((rc = upload(Q->tasks, &Q->d_tasks))) return rc;
+    if ((rc = upload(Q->finals, &Q->d_finals))) return rc;
+    sb.q[mode] = std::move(Q);
+  }
+  return VQE_OK;
+}
+
+// The persistent kernel's dynamic shared-memory limit only ever grows (per
+// device), so that every batch created so far can still launch.
+static int ensure_persist_smem(size_t smem) {
+  static std::mutex mu;
+  static std::map<int, size_t> done;
+  int dev = 0;
+  cudaError_t e = cudaGetDevice(&dev);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaGetDevice");
+  std::lock_guard<std::mutex> lock(mu);
+  auto it = done.find(dev);
+  if (it != done.end() && it->second >= smem) return VQE_OK;
+  e = vqe::set_persist_smem_limit(smem);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute (persistent kernel)");
+  done[dev] = smem;
+  return VQE_OK;
+}
+
+// Grid of the persistent launch: the SM count times the CTAs that fit per SM
+// (or the tuned count, if smaller).
+static int persist_grid(const StreamBatch& sb, int* grid) {
+  int dev = 0, sms = 0, per_sm = 0;
+  int rc = ensure_persist_smem(sb.smem);
+  if (rc) return rc;
+  cudaError_t ce = cudaGetDevice(&dev);
+  if (ce == cudaSuccess) ce = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+  if (ce == cudaSuccess) ce = vqe::persist_occupancy(sb.smem, &per_sm);
+  if (ce != cudaSuccess) return cuda_fail(ce, "persistent launch set-up");
+  if (per_sm < 1) return fail(VQE_ERR_UNSUPPORTED, "persistent kernel does not fit an SM");
+  if (sb.ctas_per_sm > 0) per_sm = std::min(per_sm, sb.ctas_per_sm);
+  *grid = sms * per_sm;
+  return VQE_OK;
+}
+
 static int build_stream_batch(vqe_batch_s* B) {
   StreamBatch& sb = B->sb;
   for (int i : B->streaming[0]) {
-    sb.slots.push_back(i);
-    sb.descs.push_back(B->descs[i]);
+    if (slot_fits(B->ans[i]))
+      sb.slots.push_back(i);
+    else
+      sb.big.push_back(i);
   }
+  for (int i : sb.big) sb.big_bytes = std::max(sb.big_bytes, ws_layout(B->ans[i], false, true).total);
   const int n = int(sb.slots.size());
   if (n == 0) return VQE_OK;
   size_t off = 0;
-  int64_t eb = 0, gb = 0;
   for (int s = 0; s < n; ++s) {
-    vqe_ansatz_t a = B->ans[sb.slots[s]];
-    const size_t vec = align256(std::max<size_t>(a->sector.size(), 1) * 8);
-    sb.psi_off.push_back(int64_t(off));
-    sb.lam_off.push_back(int64_t(off + vec));
-    sb.am_off.push_back(int64_t(off + 2 * vec));  // alpha-major psi, then lambda (D entries on)
-    off += 2 * vec + align256(2 * std::max<size_t>(a->sector.size(), 1) * 8);
-    sb.ebase.push_back(eb);
-    eb += int64_t(a->sector.size());
-    sb.gbase.push_back(gb);
-    gb += int64_t(a->pairs.size());
-    sb.Mmax = std::max(sb.Mmax, a->M);
-  }
-  sb.cs_off = off;
-  off += align256(size_t(n) * size_t(std::max(sb.Mmax, 1)) * 16);
-  sb.ebuf_off = off;
-  off += align256(size_t(std::max<int64_t>(eb, 1)) * 8);
-  sb.total_energy = off;
-  sb.gbuf_off = off;
-  sb.total_grad = off + align256(size_t(std::max<int64_t>(gb, 1)) * 8);
-  // per-gate segments: slots that have pairs for gate m, in slot order
-  std::vector<int32_t> seg_inst;
-  std::vector<int64_t> seg_pref;
-  std::vector<std::pair<size_t, size_t>> where(sb.Mmax);
-  std::vector<int64_t> totals(sb.Mmax, 0);
-  std::vector<int32_t> nsegs(sb.Mmax, 0);
-  for (int m = 0; m < sb.Mmax; ++m) {
-    const size_t i0 = seg_inst.size(), p0 = seg_pref.size();
-    int64_t acc = 0;
-    seg_pref.push_back(0);
-    for (int s = 0; s < n; ++s) {
-      vqe_ansatz_t a = B->ans[sb.slots[s]];
-      if (m >= a->M) continue;
-      const int64_t cnt = a->pair_off[m + 1] - a->pair_off[m];
-      if (cnt == 0) continue;
-      seg_inst.push_back(s);
-      acc += cnt;
-      seg_pref.push_back(acc);
+    const int i = sb.slots[s];
+    vqe_ansatz_t a = B->ans[i];
+    sb.descs.push_back(B->descs[i]);
+    const size_t D = std::max<size_t>(a->sector.size(), 1);
+    const size_t vec = align256(D * 8);
+    vqe::PSlot ps;
+    ps.psi = int64_t(off);
+    ps.lam = int64_t(off + vec);
+    off += 2 * vec;
+    if (B->descs[i].str) {
+      ps.psi_am = int64_t(off);
+      ps.lam_am = int64_t(off + vec);
+      off += 2 * vec;
+      int rc2 = VQE_OK;
+      const auto* e = get_ell(B->hams[i], a, &rc2);
+      if (!e) return rc2;
+      sb.smem = std::max(sb.smem, vqe::str_smem_bytes(e->str.Db, 8));
+    } else {
+      ps.psi_am = ps.lam_am = -1;
     }
-    where[m] = std::make_pair(i0, p0);
-    totals[m] = acc;
-    nsegs[m] = int32_t(seg_inst.size() - i0);
+    ps.cs = int64_t(off);
+    off += align256(size_t(std::max(a->M, 1)) * 16);
+    ps.ep = int64_t(off);
+    off += align256(((D + vqe::kPersistThreads - 1) / vqe::kPersistThreads) * 8);
+    ps.gp = int64_t(off);
+    int64_t nbg = 0;
+    for (int m = 0; m < a->M; ++m)
+      nbg += std::max<int64_t>(1, (a->pair_off[m + 1] - a->pair_off[m] + vqe::kStreamThreads - 1) / vqe::kStreamThreads);
+    off += align256(size_t(std::max<int64_t>(nbg, 1)) * 8);
+    sb.pslots.push_back(ps);
   }
-  std::vector<int32_t> out_inst(n);
-  std::vector<int64_t> out_pref(n + 1, 0);
-  for (int s = 0; s < n; ++s) {
-    out_inst[s] = s;
-    out_pref[s + 1] = out_pref[s] + int64_t(B->ans[sb.slots[s]]->sector.size());
-  }
-  std::vector<int32_t> gm_inst, gm_gate;
-  for (int s = 0; s < n; ++s)
-    for (int m = 0; m < B->ans[sb.slots[s]]->M; ++m) {
-      gm_inst.push_back(s);
-      gm_gate.push_back(m);
-    }
-  sb.n_gm = int64_t(gm_inst.size());
+  sb.counters_off = off;
+  sb.persist_bytes = off + align256(size_t(n + 2) * sizeof(int));
   int rc;
   if ((rc = upload(sb.descs, &sb.d_desc))) return rc;
-  if ((rc = upload(sb.psi_off, &sb.d_psi_off))) return rc;
-  if ((rc = upload(sb.lam_off, &sb.d_lam_off))) return rc;
-  if ((rc = upload(sb.ebase, &sb.d_ebase))) return rc;
-  if ((rc = upload(sb.gbase, &sb.d_gbase))) return rc;
-  if (seg_inst.empty()) seg_inst.push_back(0);
-  if ((rc = upload(seg_inst, &sb.d_seg_inst))) return rc;
-  if ((rc = upload(seg_pref, &sb.d_seg_pref))) return rc;
-  if ((rc = upload(out_inst, &sb.d_out_inst))) return rc;
-  if ((rc = upload(out_pref, &sb.d_out_pref))) return rc;
-  if (!gm_inst.empty()) {
-    if ((rc = upload(gm_inst, &sb.d_gm_inst))) return rc;
-    if ((rc = upload(gm_gate, &sb.d_gm_gate))) return rc;
-  }
-  sb.gate_segs.resize(sb.Mmax);
-  for (int m = 0; m < sb.Mmax; ++m) {
-    vqe::BatchSegs g;
-    g.inst = sb.d_seg_inst + where[m].first;
-    g.pref = sb.d_seg_pref + where[m].second;
-    g.nseg = nsegs[m];
-    g.total = totals[m];
-    sb.gate_segs[m] = g;
-  }
-  sb.out_segs.inst = sb.d_out_inst;
-  sb.out_segs.pref = sb.d_out_pref;
-  sb.out_segs.nseg = n;
-  sb.out_segs.total = out_pref[n];
-  if ((rc = upload(sb.am_off, &sb.d_am_off))) return rc;
-  // string-driven H psi when every streamed instance has a string plan
-  bool all_str = true;
-  std::vector<int32_t> str_inst(n);
-  std::vector<int64_t> str_pref(n + 1, 0);
-  for (int s = 0; s < n; ++s) {
-    int rc2 = VQE_OK;
-    const auto* e = get_ell(B->hams[sb.slots[s]], B->ans[sb.slots[s]], &rc2);
-    if (!e) return rc2;
-    if (!e->use_str) {
-      all_str = false;
-      break;
-    }
-    str_inst[s] = s;
-    str_pref[s + 1] = str_pref[s] + vqe::str_blocks(e->str.Da, e->str.Db);
-    sb.str_smem = std::max(sb.str_smem, vqe::str_smem_bytes(e->str.Db, 8));
-  }
-  if (all_str) {
-    if ((rc = upload(str_inst, &sb.d_str_inst))) return rc;
-    if ((rc = upload(str_pref, &sb.d_str_pref))) return rc;
-    sb.str_segs.inst = sb.d_str_inst;
-    sb.str_segs.pref = sb.d_str_pref;
-    sb.str_segs.nseg = n;
-    sb.str_segs.total = str_pref[n];
-  }
-  return VQE_OK;
+  if ((rc = upload(sb.pslots, &sb.d_slots))) return rc;
+  if ((rc = persist_grid(sb, &sb.grid))) return rc;
+  return build_queues(B);
 }
 
 int vqe_create_batch(int n_inst, const vqe_hamiltonian_t* hams, const vqe_ansatz_t* ans, vqe_batch_t* out) {
@@ -1927,13 +2147,41 @@ int vqe_create_batch(int n_inst, const vqe_hamiltonian_t* hams, const vqe_ansatz
 
 int32_t vqe_batch_max_params(vqe_batch_t b) { return b ? b->max_params : 0; }
 
+// Streamed instances run one by one (stream_energy_grad) in complex mode, under
+// VQE_FLAG_NO_STRINGS, and for instances too large for a persistent slot.
+static bool persistent_mode(vqe_batch_t b, bool real) {
+  return real && !(g_flags & VQE_FLAG_NO_STRINGS) && !b->sb.slots.empty();
+}
+
 size_t vqe_batch_workspace_bytes(vqe_batch_t b, int with_grad) {
   if (!b) return 0;
   const int mode = use_real() ? 0 : 1;
-  if (mode == 0) return b->sb.slots.empty() ? 0 : (with_grad ? b->sb.total_grad : b->sb.total_energy);
-  size_t need = 0;
-  for (int i : b->streaming[mode]) need = std::max(need, ws_layout(b->ans[i], mode == 1, with_grad != 0).total);
-  return need;
+  size_t one = 0;  // largest one-by-one instance
+  if (mode == 0 && persistent_mode(b, true)) {
+    for (int i : b->sb.big) one = std::max(one, ws_layout(b->ans[i], false, with_grad != 0).total);
+    return b->sb.persist_bytes + one;
+  }
+  for (int i : b->streaming[mode]) one = std::max(one, ws_layout(b->ans[i], mode == 1, with_grad != 0).total);
+  return one;
+}
+
+static int run_one_by_one(vqe_batch_t b, const std::vector<int>& which, bool real, const double* theta,
+                          int64_t ld_theta, double* energies, double* grads, int64_t ld_grad, char* ws,
+                          size_t ws_bytes, cudaStream_t stream) {
+  const bool with_grad = grads != nullptr;
+  for (int i : which) {
+    vqe_ansatz_t a = b->ans[i];
+    int rc2 = VQE_OK;
+    const auto* e = get_ell(b->hams[i], a, &rc2);
+    if (!e) return rc2;
+    const WsLayout L = ws_layout(a, !real, with_grad);
+    if ((rc2 = check_ws(ws, ws_bytes, L.total))) return rc2;
+    cudaError_t ce = vqe::stream_energy_grad(b->descs[i], plan(a, e), buffers(ws, L), real, with_grad,
+                                             theta + int64_t(i) * ld_theta, energies + i,
+                                             with_grad ? grads + int64_t(i) * ld_grad : nullptr, stream);
+    if (ce != cudaSuccess) return cuda_fail(ce, "batched streaming launch");
+  }
+  return VQE_OK;
 }
 
 static int batch_run(vqe_batch_t b, const double* theta, int64_t ld_theta, double* energies, double* grads,
@@ -1955,44 +2203,36 @@ static int batch_run(vqe_batch_t b, const double* theta, int64_t ld_theta, doubl
                                           use_fixed(real));
     if (ce != cudaSuccess) return cuda_fail(ce, "batched resident launch");
   }
-  if (real && !b->sb.slots.empty()) {
+  if (persistent_mode(b, real)) {
     const StreamBatch& sb = b->sb;
-    const size_t need = with_grad ? sb.total_grad : sb.total_energy;
+    const size_t need = vqe_batch_workspace_bytes(b, with_grad);
     if ((rc = check_ws(ws, ws_bytes, need))) return rc;
-    vqe::BatchDev bd;
-    bd.desc = sb.d_desc;
-    bd.psi_off = sb.d_psi_off;
-    bd.lam_off = sb.d_lam_off;
-    bd.ebase = sb.d_ebase;
-    bd.gbase = sb.d_gbase;
-    bd.ws = static_cast<char*>(ws);
-    bd.cs = reinterpret_cast<double2*>(static_cast<char*>(ws) + sb.cs_off);
-    bd.ebuf = reinterpret_cast<double*>(static_cast<char*>(ws) + sb.ebuf_off);
-    bd.gbuf = reinterpret_cast<double*>(static_cast<char*>(ws) + sb.gbuf_off);
-    bd.am_off = sb.d_am_off;
-    bd.n = int(sb.slots.size());
-    bd.Mmax = sb.Mmax;
-    vqe::BatchSegs str_segs = sb.str_segs;
-    if (g_flags & VQE_FLAG_NO_STRINGS) str_segs.total = 0;
-    cudaError_t ce = vqe::batch_stream_run(bd, sb.gate_segs.data(), sb.out_segs, str_segs, sb.str_smem,
-                                           sb.d_gm_inst, sb.d_gm_gate, sb.n_gm,
-                                           theta, ld_theta, energies, with_grad ? grads : nullptr, ld_grad,
-                                           sb.threads, stream);
-    if (ce != cudaSuccess) return cuda_fail(ce, "batched streaming launch");
+    const PersistQueue& Q = *sb.q[with_grad ? 1 : 0];
+    b->sb.last_queue = with_grad ? 1 : 0;
+    vqe::PersistDev pd;
+    pd.desc = sb.d_desc;
+    pd.slots = sb.d_slots;
+    pd.tasks = Q.d_tasks;
+    pd.n_tasks = int32_t(Q.tasks.size());
+    pd.n = int32_t(sb.slots.size());
+    pd.ws = static_cast<char*>(ws);
+    pd.counters = reinterpret_cast<int*>(static_cast<char*>(ws) + sb.counters_off);
+    pd.budget_ns = sb.budget_ns;
+    pd.probe_task = sb.probe_task;
+    pd.pad = 0;
+    if ((rc = ensure_persist_smem(sb.smem))) return rc;
+    cudaError_t ce = vqe::batch_persistent_run(pd, sb.grid, sb.smem, Q.d_finals, int(Q.finals.size()),
+                                               Q.n_grad_rows, theta, ld_theta, energies,
+                                               with_grad ? grads : nullptr, ld_grad, stream);
+    if (ce != cudaSuccess) return cuda_fail(ce, "persistent batch launch");
+    if (!sb.big.empty())
+      return run_one_by_one(b, sb.big, true, theta, ld_theta, energies, grads, ld_grad,
+                            static_cast<char*>(ws) + sb.persist_bytes, ws_bytes - sb.persist_bytes, stream);
   } else if (!b->streaming[mode].empty()) {
     const size_t need = vqe_batch_workspace_bytes(b, with_grad);
     if ((rc = check_ws(ws, ws_bytes, need))) return rc;
-    for (int i : b->streaming[mode]) {
-      vqe_ansatz_t a = b->ans[i];
-      int rc2 = VQE_OK;
-      const auto* e = get_ell(b->hams[i], a, &rc2);
-      if (!e) return rc2;
-      const WsLayout L = ws_layout(a, !real, with_grad);
-      cudaError_t ce = vqe::stream_energy_grad(b->descs[i], plan(a, e), buffers(ws, L), real, with_grad,
-                                               theta + int64_t(i) * ld_theta, energies + i,
-                                               with_grad ? grads + int64_t(i) * ld_grad : nullptr, stream);
-      if (ce != cudaSuccess) return cuda_fail(ce, "batched streaming launch");
-    }
+    return run_one_by_one(b, b->streaming[mode], real, theta, ld_theta, energies, grads, ld_grad,
+                          static_cast<char*>(ws), ws_bytes, stream);
   }
   return VQE_OK;
 }
@@ -2058,12 +2298,18 @@ int vqe_batch_energy_grad_host(vqe_batch_t b, const double* theta_host, int64_t 
     }
     return VQE_OK;
   };
+  // after the synchronisation: a wait of the persistent launch that ran out
+  // (status word in the batch's part of the workspace) returns VQE_ERR_TIMEOUT
+  auto persist_check = [&]() -> int {
+    if (!persistent_mode(b, use_real())) return VQE_OK;
+    return vqe_batch_status(b, base + off, ws_bytes - off, stream);
+  };
   cudaStreamCaptureStatus cap = cudaStreamCaptureStatusNone;
   if (cudaStreamIsCapturing(stream, &cap) != cudaSuccess) {
     cudaGetLastError();  // status unknown: plain copies and launches, then synchronise
     if ((rc = issue(stream))) return rc;
     const cudaError_t se = cudaStreamSynchronize(stream);
-    return se == cudaSuccess ? VQE_OK : cuda_fail(se, "stream synchronize");
+    return se == cudaSuccess ? persist_check() : cuda_fail(se, "stream synchronize");
   }
   if (cap != cudaStreamCaptureStatusNone) return issue(stream);  // inside the caller's capture: no sync
   HostGraph key;
@@ -2109,17 +2355,25 @@ int vqe_batch_energy_grad_host(vqe_batch_t b, const double* theta_host, int64_t 
   }
   ce = cudaStreamSynchronize(stream);
   if (ce != cudaSuccess) return cuda_fail(ce, "stream synchronize");
-  return VQE_OK;
+  return persist_check();
 }
 
-int vqe_batch_set_tuning(vqe_batch_t b, int stream_threads, int sweep_threads) {
+int vqe_batch_set_tuning(vqe_batch_t b, int ctas_per_sm, int gate_chunk, int sweep_threads) {
   if (!b) return fail(VQE_ERR_INVALID_ARG, "NULL batch");
-  if (stream_threads != 0 && (stream_threads < 64 || stream_threads > 512 || stream_threads % 32))
-    return fail(VQE_ERR_INVALID_ARG, "stream_threads: a multiple of 32 in [64, 512], or 0 to keep");
+  if (ctas_per_sm < 0 || ctas_per_sm > 16) return fail(VQE_ERR_INVALID_ARG, "ctas_per_sm: 1..16, or 0 for all that fit");
+  if (gate_chunk < 0 || gate_chunk % vqe::kStreamThreads || gate_chunk > (1 << 20))
+    return fail(VQE_ERR_INVALID_ARG, "gate_chunk: a multiple of 256 up to 2^20, or 0 to keep");
   if (sweep_threads != 0 && (sweep_threads < 32 || sweep_threads > vqe::kResidentThreads || sweep_threads % 32))
     return fail(VQE_ERR_INVALID_ARG, "sweep_threads: a multiple of 32 in [32, 512], or 0 to keep");
   ++b->tuning_version;  // launch shapes are captured in the host-call graph
-  if (stream_threads) b->sb.threads = stream_threads;
+  StreamBatch& sb = b->sb;
+  if (!sb.slots.empty() && (ctas_per_sm != sb.ctas_per_sm || (gate_chunk && gate_chunk != sb.gate_chunk))) {
+    sb.ctas_per_sm = ctas_per_sm;
+    if (gate_chunk) sb.gate_chunk = gate_chunk;
+    int rc = persist_grid(sb, &sb.grid);
+    if (rc == VQE_OK) rc = build_queues(b);
+    if (rc) return rc;
+  }
   if (sweep_threads) {
     for (int mode = 0; mode < 2; ++mode) {
       for (auto& d : b->res_descs[mode]) d.sweep_threads = sweep_threads;
@@ -2131,6 +2385,46 @@ int vqe_batch_set_tuning(vqe_batch_t b, int stream_threads, int sweep_threads) {
     }
   }
   return VQE_OK;
+}
+
+int vqe_batch_get_tuning(vqe_batch_t b, int* ctas_per_sm, int* gate_chunk, int* grid, int64_t* n_tasks) {
+  if (!b) return fail(VQE_ERR_INVALID_ARG, "NULL batch");
+  if (ctas_per_sm) *ctas_per_sm = b->sb.ctas_per_sm;
+  if (gate_chunk) *gate_chunk = b->sb.gate_chunk;
+  if (grid) *grid = b->sb.slots.empty() ? 0 : b->sb.grid;
+  if (n_tasks) *n_tasks = b->sb.q[1] ? int64_t(b->sb.q[1]->tasks.size()) : 0;
+  return VQE_OK;
+}
+
+int vqe_batch_set_wait(vqe_batch_t b, int64_t budget_ns, int32_t probe_task) {
+  if (!b) return fail(VQE_ERR_INVALID_ARG, "NULL batch");
+  if (budget_ns < 1000 || budget_ns > int64_t(600) * 1000000000ll)
+    return fail(VQE_ERR_INVALID_ARG, "budget_ns: 1e3 .. 6e11");
+  if (probe_task < -1) return fail(VQE_ERR_INVALID_ARG, "probe_task: a task index, or -1");
+  ++b->tuning_version;
+  b->sb.budget_ns = budget_ns;
+  b->sb.probe_task = probe_task;
+  return VQE_OK;
+}
+
+int vqe_batch_status(vqe_batch_t b, const void* ws, size_t ws_bytes, vqe_stream_t stream) {
+  if (!b) return fail(VQE_ERR_INVALID_ARG, "NULL batch");
+  const StreamBatch& sb = b->sb;
+  if (sb.slots.empty()) return VQE_OK;
+  if (!ws || ws_bytes < sb.persist_bytes) return fail(VQE_ERR_WORKSPACE, "workspace smaller than the batch's");
+  int status = 0;
+  cudaError_t ce = cudaMemcpyAsync(&status, static_cast<const char*>(ws) + sb.counters_off + (sb.slots.size() + 1) * sizeof(int),
+                                   sizeof(int), cudaMemcpyDeviceToHost, static_cast<cudaStream_t>(stream));
+  if (ce == cudaSuccess) ce = cudaStreamSynchronize(static_cast<cudaStream_t>(stream));
+  if (ce != cudaSuccess) return cuda_fail(ce, "status read");
+  if (status == 0) return VQE_OK;
+  const int t = status - 1;
+  const PersistQueue* Q = sb.q[sb.last_queue].get();
+  std::string what = "task " + std::to_string(t);
+  if (Q && t >= 0 && size_t(t) < Q->tasks.size())
+    what += " (instance " + std::to_string(sb.descs[Q->tasks[t].slot].inst) + ")";
+  return fail(VQE_ERR_TIMEOUT, "persistent batch: a wait of " + what + " ran out of its " +
+                                   std::to_string(sb.budget_ns) + " ns budget; outputs are NaN");
 }
 
 void vqe_destroy_batch(vqe_batch_t b) { delete b; }
@@ -2267,6 +2561,18 @@ int vqe_energy_grad_batched(int n_inst, const vqe_hamiltonian_t* hams, const vqe
   if (!grads_dev) return fail(VQE_ERR_INVALID_ARG, "NULL gradient array");
   return batched_run(n_inst, hams, ans, theta_dev, energies_dev, grads_dev, ws, ws_bytes,
                      static_cast<cudaStream_t>(stream));
+}
+
+int vqe_work_counts(vqe_hamiltonian_t h, vqe_ansatz_t a, int64_t* n_pairs, int64_t* n_entries,
+                    double* extra_adds) {
+  int rc = check_pair(h, a);
+  if (rc) return rc;
+  const auto* e = get_ell(h, a, &rc);
+  if (!e) return rc;
+  if (n_pairs) *n_pairs = int64_t(a->pairs.size());
+  if (n_entries) *n_entries = e->nnz;
+  if (extra_adds) *extra_adds = e->extra_adds;
+  return VQE_OK;
 }
 
 int vqe_work_estimate(vqe_hamiltonian_t h, vqe_ansatz_t a, int with_grad, double* flops, double* bytes) {

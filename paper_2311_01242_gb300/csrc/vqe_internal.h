@@ -75,7 +75,7 @@ struct InstDesc {
   // ansatz
   int32_t n, M;
   uint32_t hf;
-  int32_t pad0;
+  int32_t ellp_fast;         // 1: ellp entries with bit 31 set are single-slot entries (see below)
   int64_t D;                 // sector dimension
   const uint32_t* sector;    // [D] sorted basis indices of the sector
   const GateRec* gates;      // [M]
@@ -89,7 +89,10 @@ struct InstDesc {
   int32_t lo_bits, hf_rank;  // hf_rank = rank(hf)
   const StrPlan* str;        // device copy of the string plan, or null
   // resident kernel: [W][D] packed entries rank(src) | pattern(src) << 15 | group << 19
-  // (D <= 32767, G <= 8191), pad 0xFFFFFFFF
+  // (D <= 32767, G <= 8191), pad 0xFFFFFFFF. With ellp_fast (G <= 4095), an entry
+  // whose group has a single folded term (f = (-1)^s vals[slot], the double
+  // excitations of Jordan-Wigner chemistry) is instead
+  // rank(src) | s << 15 | slot << 16 | 1 << 31 (slot < 32768).
   const uint32_t* ellp;
   const double* hbound;      // device: sum of |vals| (bounds every row sum of |H|)
   // Hamiltonian
@@ -108,38 +111,49 @@ struct InstDesc {
   int32_t n_elec, n_alpha;   // sector (n_alpha < 0: electron number only)
 };
 
-// Gate-major batched streaming plan: one launch per gate index over every
-// instance that has that gate, one H psi launch over all instances. Work items
-// of a launch are the concatenation of per-instance segments; a thread finds
-// its segment by binary search over the segment prefix sums.
-struct BatchSegs {
-  const int32_t* inst;   // [nseg] instance slot of each segment
-  const int64_t* pref;   // [nseg + 1] exclusive prefix sums of segment sizes
-  int32_t nseg;
-  int64_t total;
+// Persistent batched evaluation (vqe_batch.cu): a device work queue of tasks,
+// each instance a chain of levels (see PTaskKind), run by one launch.
+constexpr int kPersistThreads = 256;  // == kStrWarps * 32, the string-driven H psi's block
+enum PTaskKind : int32_t { PT_INIT = 0, PT_FWD = 1, PT_GATHER = 2, PT_HPSI = 3, PT_SCATTER = 4, PT_DOT = 5, PT_ADJ = 6 };
+struct PTask {
+  int32_t slot;   // persistent slot (instance) of the task
+  int32_t kind;   // PTaskKind
+  int32_t m;      // gate (FWD, ADJ)
+  int32_t need;   // the slot's progress counter must reach this before the task runs
+  int64_t lo, hi; // pairs of gate m (FWD, ADJ), alpha-major entries (GATHER, SCATTER), output alpha
+                  // strings (HPSI, string form) or rows (HPSI, other sectors), 256-entry blocks (DOT)
+  int64_t aux;    // ADJ: index of gate m's first partial among the slot's gradient partials
+};
+struct PSlot {    // byte offsets in the workspace
+  int64_t psi, lam, psi_am, lam_am, cs, ep, gp;
+};
+struct PFinal {   // one output of the finalising launch
+  int64_t off;    // byte offset of its partials in the workspace
+  int32_t nb;     // partial count
+  int32_t m;      // gate, or -1 for the energy
+  int64_t inst;   // row in the caller's arrays
+  double scale;   // 2 for gradients, 1 for energies
+};
+struct PersistDev {
+  const InstDesc* desc;  // [n]
+  const PSlot* slots;    // [n]
+  const PTask* tasks;    // [n_tasks], the queue order
+  int32_t n_tasks, n;
+  char* ws;
+  int* counters;         // [n] progress, then the next-task counter, then the status word
+  long long budget_ns;   // bound of every wait
+  int32_t probe_task;    // >= 0: that task waits for a count nothing reaches (timeout check)
+  int32_t pad;
 };
 
-struct BatchDev {
-  const InstDesc* desc;    // [n] descriptors of the streamed instances
-  const int64_t* psi_off;  // [n] byte offsets of psi in the workspace
-  const int64_t* lam_off;  // [n] byte offsets of lambda
-  const int64_t* ebase;    // [n] first slot in the per-output energy buffer
-  const int64_t* gbase;    // [n] first slot in the per-pair gradient buffer
-  char* ws;                // workspace base
-  double2* cs;             // [n * Mmax] cos/sin
-  double* ebuf;            // [sum D] per-output psi*lambda
-  double* gbuf;            // [sum P] per-pair gradient contributions
-  const int64_t* am_off;   // [n] byte offsets of alpha-major psi, then lambda (string-driven H psi)
-  int32_t n, Mmax;
-};
-
-// str_segs.total > 0: every instance has a string plan and H psi runs
-// string-driven (str_blocks blocks per instance; str_smem bytes).
-cudaError_t batch_stream_run(const BatchDev& b, const BatchSegs* gate_segs, const BatchSegs& out_segs,
-                             const BatchSegs& str_segs, size_t str_smem,
-                             const int32_t* d_gm_inst, const int32_t* d_gm_gate, int64_t n_gm,
-                             const double* theta, int64_t ld_theta, double* energy, double* grad,
-                             int64_t ld_grad, int threads, cudaStream_t stream);
+// memset of the counters, the persistent launch (grid CTAs), and the finalising
+// launch over rows[0, n_rows) (gradient rows first: n_grad_rows of them, skipped
+// when grad is null).
+cudaError_t batch_persistent_run(const PersistDev& p, int grid, size_t smem, const PFinal* rows, int n_rows,
+                                 int n_grad_rows, const double* theta, int64_t ld_theta, double* energy, double* grad,
+                                 int64_t ld_grad, cudaStream_t stream);
+cudaError_t set_persist_smem_limit(size_t smem);
+cudaError_t persist_occupancy(size_t smem, int* blocks_per_sm);
 cudaError_t set_str_smem_limit(size_t smem);
 
 // Shared-memory layout of the resident kernel (byte offsets), computed the same
@@ -243,6 +257,9 @@ cudaError_t stream_state(const InstDesc& d, const StreamPlan& sp, const StreamBu
 cudaError_t stream_apply_h(const InstDesc& d, const StreamPlan& sp, const StreamBuffers& b,
                            const double* psi_in, double* lam_out, double* energy,
                            cudaStream_t stream);
+// lambda = H psi with real amplitudes compressed to the sector (b.psi in, b.lam out).
+cudaError_t stream_apply_h_real(const InstDesc& d, const StreamPlan& sp, const StreamBuffers& b, double* energy,
+                                cudaStream_t stream);
 
 // Device-built connectivity table (16-bit group indices) for large sectors:
 // len[r] = groups connected to output r; then rows filled in `order`.
@@ -262,8 +279,11 @@ cudaError_t pool_gradients(const uint2* rpairs, const int64_t* pair_off, const i
                            double* part, double* grad, cudaStream_t stream);
 
 // Host helpers for the allocation-free entry point (vqe_static.cu).
-int prepare_noalloc(vqe_hamiltonian_s* h, vqe_ansatz_s* a, bool with_grad, InstDesc* d, StreamPlan* sp,
-                    bool* real, size_t off[5], size_t* need);
+// off: psi, lambda, alpha-major psi, alpha-major lambda (0 when unused), cos/sin,
+// energy partials, gradient partials; *need: total bytes.
+// The string-driven H psi is used only if its scratch fits in `limit` bytes.
+int prepare_noalloc(vqe_hamiltonian_s* h, vqe_ansatz_s* a, bool with_grad, size_t limit, InstDesc* d,
+                    StreamPlan* sp, bool* real, size_t off[7], size_t* need);
 int set_error(int code, const char* msg);
 
 // Table refold from new coefficients (vqe_aux.cu): slot s of the value tables is

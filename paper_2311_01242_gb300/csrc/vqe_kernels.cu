@@ -20,415 +20,10 @@
 #include <cuda_runtime.h>
 
 #include "vqe_internal.h"
+#include "vqe_device.cuh"
 
 namespace vqe {
 namespace {
-
-__device__ __forceinline__ int parity32(uint32_t v) { return __popc(v) & 1; }
-
-// v with its sign bit flipped when s == 1 (integer pipe, no FP64 op).
-__device__ __forceinline__ double sflip(double v, int s) {
-  return __hiloint2double(__double2hiint(v) ^ (s << 31), __double2loint(v));
-}
-__device__ __forceinline__ double2 sflip(double2 v, int s) {
-  return make_double2(sflip(v.x, s), sflip(v.y, s));
-}
-
-// ---------------------------------------------------------------- fixed-point sweeps
-// The resident kernel's real sweeps can run in 64-bit fixed point on the
-// integer pipe: amplitudes of the unit-norm state as Q1.62 (value = v / 2^62),
-// cos and sin magnitudes as unsigned Q0.64 with their signs kept apart, so a
-// product is the high word of a 64 x 64 multiply. Rotations preserve the
-// 2-norm, so |value| <= 1 holds for every entry at every gate.
-__device__ __forceinline__ long long dbits(double v) { return __double_as_longlong(v); }
-__device__ __forceinline__ double llbits(long long v) { return __longlong_as_double(v); }
-// floor(a * b / 2^64) for signed a, unsigned b
-__device__ __forceinline__ long long mulhi_su(long long a, unsigned long long b) {
-  const unsigned long long h = __umul64hi(static_cast<unsigned long long>(a), b);
-  return static_cast<long long>(h - (a < 0 ? b : 0ull));
-}
-// v, negated when b == 1
-__device__ __forceinline__ long long neg_if(long long v, int b) {
-  const long long m = -static_cast<long long>(b);
-  return (v ^ m) - m;
-}
-// |x| * 2^64 rounded, for |x| <= 1 (1 itself saturates to 2^64 - 1)
-__device__ __forceinline__ unsigned long long fix_mag(double x) {
-  const double a = fabs(x) * 18446744073709551616.0;
-  return a >= 18446744073709551616.0 ? ~0ull : __double2ull_rn(a);
-}
-// 2^e as a double, for |e| < 1000
-__device__ __forceinline__ double pow2(int e) { return __longlong_as_double(static_cast<long long>(1023 + e) << 52); }
-// smallest e with b < 2^e for a finite b >= 0 (clamped to [-400, 400])
-__device__ __forceinline__ int bound_exp(double b) {
-  const int ex = int((__double_as_longlong(b) >> 52) & 0x7ff);
-  const int e = ex == 0 ? -400 : ex - 1022;
-  return e < -400 ? -400 : (e > 400 ? 400 : e);
-}
-
-__device__ __forceinline__ uint32_t pattern_of(uint32_t src, uint32_t upos, int ubits) {
-  uint32_t u = 0;
-#pragma unroll
-  for (int j = 0; j < kMaxPatternBits; ++j)
-    if (j < ubits) u |= ((src >> ((upos >> (8 * j)) & 31u)) & 1u) << j;
-  return u;
-}
-
-__device__ __forceinline__ GateRec load_gate(const GateRec* p) {
-  const int4 a = __ldg(reinterpret_cast<const int4*>(p));
-  GateRec r;
-  r.flip = uint32_t(a.x);
-  r.par = uint32_t(a.y);
-  r.sign0 = a.z;
-  r.pad = 0;
-  return r;
-}
-
-// ---------------------------------------------------------------- amplitude algebra
-template <bool REAL> struct Amp;
-
-template <> struct Amp<true> {
-  typedef double T;
-  typedef double C;  // coefficient type
-  static __device__ __forceinline__ T zero() { return 0.0; }
-  static __device__ __forceinline__ T unit() { return 1.0; }
-  static __device__ __forceinline__ C coef(const InstDesc& d, int64_t slot) { return __ldg(d.vals + slot); }
-  // acc += f * p
-  static __device__ __forceinline__ void mac(T& acc, C f, T p) { acc = fma(f, p, acc); }
-  // Re(conj(a) * b)
-  static __device__ __forceinline__ double redot(T a, T b) { return a * b; }
-  // (c a - ss b, ss a + c b); nss = -ss comes in precomputed (sign bit flipped
-  // in the integer pipe) so that no FP64 negation is issued
-  static __device__ __forceinline__ void rot(T& a, T& b, double c, double ss, double nss) {
-    const T a0 = a;
-    a = fma(nss, b, c * a0);
-    b = fma(ss, a0, c * b);
-  }
-  // lb pa - la pb
-  static __device__ __forceinline__ double cross(T lb, T pa, T la, T pb) {
-    return fma(lb, pa, -(la * pb));
-  }
-  static __device__ __forceinline__ double2 to_c(T a) { return make_double2(a, 0.0); }
-  static __device__ __forceinline__ T from_c(double2 a) { return a.x; }
-};
-
-template <> struct Amp<false> {
-  typedef double2 T;
-  typedef double2 C;
-  static __device__ __forceinline__ T zero() { return make_double2(0.0, 0.0); }
-  static __device__ __forceinline__ T unit() { return make_double2(1.0, 0.0); }
-  static __device__ __forceinline__ C coef(const InstDesc& d, int64_t slot) { return __ldg(d.cvals + slot); }
-  static __device__ __forceinline__ void mac(T& acc, C f, T p) {
-    acc.x = fma(f.x, p.x, fma(-f.y, p.y, acc.x));
-    acc.y = fma(f.x, p.y, fma(f.y, p.x, acc.y));
-  }
-  static __device__ __forceinline__ double redot(T a, T b) { return fma(a.x, b.x, a.y * b.y); }
-  static __device__ __forceinline__ void rot(T& a, T& b, double c, double ss, double nss) {
-    const T a0 = a;
-    a.x = fma(nss, b.x, c * a0.x);
-    a.y = fma(nss, b.y, c * a0.y);
-    b.x = fma(ss, a0.x, c * b.x);
-    b.y = fma(ss, a0.y, c * b.y);
-  }
-  static __device__ __forceinline__ double cross(T lb, T pa, T la, T pb) {
-    return fma(lb.x, pa.x, fma(lb.y, pa.y, -fma(la.x, pb.x, la.y * pb.y)));
-  }
-  static __device__ __forceinline__ double2 to_c(T a) { return a; }
-  static __device__ __forceinline__ T from_c(double2 a) { return a; }
-};
-
-__device__ __forceinline__ GroupRec load_group(const GroupRec* p) {
-  const int4* q = reinterpret_cast<const int4*>(p);
-  const int4 a = q[0];
-  const int4 b = q[1];
-  GroupRec g;
-  g.x = uint32_t(a.x);
-  g.upos = uint32_t(a.y);
-  g.ebeg = a.z;
-  g.eend = a.w;
-  g.vbeg = b.x;
-  g.ubits = b.y;
-  g.kind = b.z;
-  g.nq = b.w;
-  return g;
-}
-
-template <typename C>
-__device__ __forceinline__ void cadd(C& f, const C& v) {
-  if constexpr (sizeof(C) == sizeof(double)) {
-    f += v;
-  } else {
-    f.x += v.x;
-    f.y += v.y;
-  }
-}
-
-// Folded coefficient f_g(src) of a group (all three forms of GroupRec), from
-// tables in shared or global memory. Signs are applied in the integer pipe.
-// u is the pattern of src on the group's pattern qubits (pattern_of).
-template <bool REAL>
-__device__ __forceinline__ typename Amp<REAL>::C group_coef_u(const GroupRec& g, const uint32_t* emask,
-                                                              const typename Amp<REAL>::C* vals, uint32_t src,
-                                                              uint32_t u) {
-  typedef typename Amp<REAL>::C C;
-  if (g.kind == 0) {
-    const C* vp = vals + g.vbeg + u;
-    C f = sflip(vp[0], parity32(src & emask[g.ebeg]));
-    for (int e = g.ebeg + 1, j = 1; e < g.eend; ++e, ++j)
-      cadd(f, sflip(vp[j << g.ubits], parity32(src & emask[e])));
-    return f;
-  }
-  const uint32_t z0 = emask[g.ebeg];
-  uint32_t m = src & emask[g.ebeg + 1];
-  C f;
-  if (g.kind == 1) {
-    const C* vp = vals + g.vbeg + u;
-    f = vp[0];
-    while (m) {
-      const int r = __ffs(m) - 1;
-      m &= m - 1;
-      cadd(f, vp[(1 + r) << g.ubits]);
-    }
-  } else {
-    const C* q = vals + g.vbeg;
-    const int nq = g.nq;
-    f = q[0];
-    while (m) {
-      const int pb = __ffs(m) - 1;
-      m &= m - 1;
-      cadd(f, q[1 + pb]);
-      const C* row = q + 1 + nq + pb * nq;
-      uint32_t m2 = m;
-      while (m2) {
-        const int qb = __ffs(m2) - 1;
-        m2 &= m2 - 1;
-        cadd(f, row[qb]);
-      }
-    }
-  }
-  return sflip(f, parity32(src & z0));
-}
-
-template <bool REAL>
-__device__ __forceinline__ typename Amp<REAL>::C group_coef(const GroupRec& g, const uint32_t* emask,
-                                                            const typename Amp<REAL>::C* vals, uint32_t src) {
-  return group_coef_u<REAL>(g, emask, vals, src, pattern_of(src, g.upos, g.ubits));
-}
-
-// group_coef split at its first table term: v0 = vals[vbeg + u] and z = emask[ebeg]
-// (the first entry's value and mask in the entry form, B[u] or Q[0] and z0 in the
-// occupation forms) are loaded by the caller ahead of time; this adds the rest in
-// the same order as group_coef, so the result is bitwise the same.
-template <bool REAL>
-__device__ __forceinline__ typename Amp<REAL>::C group_coef_rest(const GroupRec& g, const uint32_t* emask,
-                                                                 const typename Amp<REAL>::C* vals, uint32_t src,
-                                                                 typename Amp<REAL>::C v0, uint32_t z) {
-  typedef typename Amp<REAL>::C C;
-  if (g.kind == 0) {
-    const uint32_t u = pattern_of(src, g.upos, g.ubits);
-    const C* vp = vals + g.vbeg + u;
-    C f = sflip(v0, parity32(src & z));
-    for (int e = g.ebeg + 1, j = 1; e < g.eend; ++e, ++j)
-      cadd(f, sflip(vp[j << g.ubits], parity32(src & emask[e])));
-    return f;
-  }
-  uint32_t m = src & emask[g.ebeg + 1];
-  C f = v0;
-  if (g.kind == 1) {
-    const uint32_t u = pattern_of(src, g.upos, g.ubits);
-    const C* vp = vals + g.vbeg + u;
-    while (m) {
-      const int r = __ffs(m) - 1;
-      m &= m - 1;
-      cadd(f, vp[(1 + r) << g.ubits]);
-    }
-  } else {
-    const C* q = vals + g.vbeg;
-    const int nq = g.nq;
-    while (m) {
-      const int pb = __ffs(m) - 1;
-      m &= m - 1;
-      cadd(f, q[1 + pb]);
-      const C* row = q + 1 + nq + pb * nq;
-      uint32_t m2 = m;
-      while (m2) {
-        const int qb = __ffs(m2) - 1;
-        m2 &= m2 - 1;
-        cadd(f, row[qb]);
-      }
-    }
-  }
-  return sflip(f, parity32(src & z));
-}
-
-
-__device__ __forceinline__ bool in_sector(uint32_t k, int n_elec, int n_alpha) {
-  if (__popc(k) != n_elec) return false;
-  return n_alpha < 0 || __popc(k & 0x55555555u) == n_alpha;
-}
-
-// Position of basis state k in the sector's sorted list (k must be in the
-// sector): the count of sector states with a smaller high part, plus the rank
-// of the low part among low parts with the same electron counts.
-__device__ __forceinline__ uint32_t sector_rank(const InstDesc& d, uint32_t k) {
-  return __ldg(d.rank_hi + (k >> d.lo_bits)) + __ldg(d.rank_lo + (k & ((1u << d.lo_bits) - 1u)));
-}
-
-// Entry j of output r's connectivity row (kEllPad past the row's end).
-__device__ __forceinline__ uint32_t ell_at(const uint32_t* ell, const uint16_t* ell16, int64_t idx) {
-  if (ell16) {
-    const uint32_t v = __ldg(ell16 + idx);
-    return v == 0xFFFFu ? kEllPad : v;
-  }
-  return __ldg(ell + idx);
-}
-
-// Calls f(gi) for the group indices of output r's connectivity row at slots
-// j = first, first + step, ... in order, up to the first pad. The indices are
-// read in chunks of kEllChunk and the next chunk is requested before the
-// current one is used, so a thread has a chunk of loads in flight instead of
-// one L2 round trip per entry.
-constexpr int kEllChunk = 8;
-template <class F>
-__device__ __forceinline__ void ell_row(const uint32_t* ell, const uint16_t* ell16, int W, int64_t D, int64_t r,
-                                       int first, int step, F&& f) {
-  constexpr int U = kEllChunk;
-  uint32_t cur[U];
-#pragma unroll
-  for (int u = 0; u < U; ++u) {
-    const int j = first + u * step;
-    cur[u] = j < W ? ell_at(ell, ell16, int64_t(j) * D + r) : kEllPad;
-  }
-  for (int j0 = first; j0 < W; j0 += U * step) {
-    const bool more = cur[U - 1] != kEllPad && j0 + U * step < W;
-    uint32_t nxt[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const int j = j0 + (U + u) * step;
-      nxt[u] = (more && j < W) ? ell_at(ell, ell16, int64_t(j) * D + r) : kEllPad;
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-      if (cur[u] != kEllPad) f(cur[u]);
-    if (!more) break;
-#pragma unroll
-    for (int u = 0; u < U; ++u) cur[u] = nxt[u];
-  }
-}
-
-// group_coef on fixed-point tables (int64, one common scale): the same terms,
-// summed exactly in the integer pipe.
-__device__ __forceinline__ long long group_coef_int(const GroupRec& g, const uint32_t* emask, const long long* vals,
-                                                    uint32_t src, uint32_t u) {
-  if (g.kind == 0) {
-    const long long* vp = vals + g.vbeg + u;
-    long long f = neg_if(vp[0], parity32(src & emask[g.ebeg]));
-    for (int e = g.ebeg + 1, j = 1; e < g.eend; ++e, ++j) f += neg_if(vp[j << g.ubits], parity32(src & emask[e]));
-    return f;
-  }
-  const uint32_t z0 = emask[g.ebeg];
-  uint32_t m = src & emask[g.ebeg + 1];
-  long long f;
-  if (g.kind == 1) {
-    const long long* vp = vals + g.vbeg + u;
-    f = vp[0];
-    while (m) {
-      const int r = __ffs(m) - 1;
-      m &= m - 1;
-      f += vp[(1 + r) << g.ubits];
-    }
-  } else {
-    const long long* q = vals + g.vbeg;
-    const int nq = g.nq;
-    f = q[0];
-    while (m) {
-      const int pb = __ffs(m) - 1;
-      m &= m - 1;
-      f += q[1 + pb];
-      const long long* row = q + 1 + nq + pb * nq;
-      uint32_t m2 = m;
-      while (m2) {
-        const int qb = __ffs(m2) - 1;
-        m2 &= m2 - 1;
-        f += row[qb];
-      }
-    }
-  }
-  return neg_if(f, parity32(src & z0));
-}
-
-// One output row of H psi over the compressed state (entry r of psi is sector
-// state r): sum over the row's connectivity entries j of f_{g_j}(src) psi[rank(src)],
-// src = k ^ x_{g_j}, in row order. Entries are taken in chunks of U: first every
-// entry's group record, source rank, psi value and first table term are loaded
-// (independent loads, all in flight together), then the chunk is combined in
-// order; only groups with more than one table term go back to memory there.
-template <bool REAL, int U>
-__device__ __forceinline__ typename Amp<REAL>::T hpsi_row(const uint32_t* ell, const uint16_t* ell16, int W, int64_t D,
-                                                          int64_t r, uint32_t k, const GroupRec* groups,
-                                                          const uint32_t* emask, const typename Amp<REAL>::C* vals,
-                                                          const typename Amp<REAL>::T* psi, const uint32_t* rank_hi,
-                                                          const uint32_t* rank_lo, int lo_bits) {
-  typedef Amp<REAL> A;
-  typedef typename A::T T;
-  typedef typename A::C C;
-  const uint32_t lo_mask = (1u << lo_bits) - 1u;
-  T acc = A::zero();
-  uint32_t cur[U];
-#pragma unroll
-  for (int u = 0; u < U; ++u) cur[u] = u < W ? ell_at(ell, ell16, int64_t(u) * D + r) : kEllPad;
-  for (int j0 = 0; j0 < W; j0 += U) {
-    const bool more = cur[U - 1] != kEllPad && j0 + U < W;
-    uint32_t nxt[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u)
-      nxt[u] = (more && j0 + U + u < W) ? ell_at(ell, ell16, int64_t(j0 + U + u) * D + r) : kEllPad;
-    uint32_t src[U], z[U], extra = 0;
-    T pv[U];
-    C v0[U];
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      const bool live = cur[u] != kEllPad;
-      const GroupRec g = load_group(groups + (live ? cur[u] : 0u));
-      src[u] = k ^ g.x;
-      // a pad slot reads row r itself (a valid index) and is dropped below
-      const uint32_t rs = live ? __ldg(rank_hi + (src[u] >> lo_bits)) + __ldg(rank_lo + (src[u] & lo_mask))
-                               : uint32_t(r);
-      pv[u] = psi[rs];
-      v0[u] = vals[g.vbeg + int(pattern_of(src[u], g.upos, g.ubits))];
-      z[u] = emask[g.ebeg];
-      if (g.kind != 0 || g.eend > g.ebeg + 1) extra |= 1u << u;
-    }
-#pragma unroll
-    for (int u = 0; u < U; ++u) {
-      if (cur[u] == kEllPad) continue;
-      C f;
-      if ((extra >> u) & 1u)
-        f = group_coef_rest<REAL>(load_group(groups + cur[u]), emask, vals, src[u], v0[u], z[u]);
-      else
-        f = sflip(v0[u], parity32(src[u] & z[u]));
-      A::mac(acc, f, pv[u]);
-    }
-    if (!more) break;
-#pragma unroll
-    for (int u = 0; u < U; ++u) cur[u] = nxt[u];
-  }
-  return acc;
-}
-
-// Deterministic block sum; the result is valid in thread 0.
-__device__ double block_sum(double v, double* red) {
-#pragma unroll
-  for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-  __syncthreads();
-  if (lane == 0) red[w] = v;
-  __syncthreads();
-  double s = 0.0;
-  if (threadIdx.x == 0)
-    for (int i = 0; i < int(blockDim.x >> 5); ++i) s += red[i];
-  return s;
-}
 
 // ---------------------------------------------------------------- resident kernel
 __device__ __forceinline__ void prefetch_l2(const void* p) {
@@ -674,6 +269,7 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
   // depends on nothing but the row, so every launch form gives the same bits.
   constexpr int TPR = REAL ? 2 : 1;
   const int rows = r_hi - r_lo, per_pass = bs / TPR, half = tid % TPR;
+  const bool fast = d.ellp_fast != 0;
   for (int base = 0; base < rows; base += per_pass) {  // same trip count in every thread
     const int lr = base + tid / TPR;
     const bool live = lr < rows;
@@ -686,8 +282,14 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
         if (live) {
           const long long* tvi = reinterpret_cast<const long long*>(tv);
           ell_row(d.ellp, nullptr, W, D, r, half, TPR, [&](uint32_t e) {
-            const GroupRec g = load_group(tg + (e >> 19));
-            acc += __mul64hi(group_coef_int(g, te, tvi, k ^ g.x, (e >> 15) & 15u), dbits(pl[e & 0x7fffu].x));
+            long long f;
+            if (fast && (e >> 31)) {
+              f = neg_if(tvi[(e >> 16) & 0x7fffu], int((e >> 15) & 1u));
+            } else {
+              const GroupRec g = load_group(tg + (e >> 19));
+              f = group_coef_int(g, te, tvi, k ^ g.x, (e >> 15) & 15u);
+            }
+            acc += __mul64hi(f, dbits(pl[e & 0x7fffu].x));
           });
         }
         acc += __shfl_xor_sync(0xffffffffu, acc, 1);  // even + odd slots (exact)
@@ -702,8 +304,13 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
     T acc = A::zero();
     if (live) {
       ell_row(d.ellp, nullptr, W, D, r, half, TPR, [&](uint32_t e) {
-        const GroupRec g = load_group(tg + (e >> 19));
-        const C f = group_coef_u<REAL>(g, te, tv, k ^ g.x, (e >> 15) & 15u);
+        C f;
+        if (fast && (e >> 31)) {
+          f = sflip(tv[(e >> 16) & 0x7fffu], int((e >> 15) & 1u));
+        } else {
+          const GroupRec g = load_group(tg + (e >> 19));
+          f = group_coef_u<REAL>(g, te, tv, k ^ g.x, (e >> 15) & 15u);
+        }
         if constexpr (REAL)
           A::mac(acc, f, pl[e & 0x7fffu].x);
         else
@@ -984,158 +591,6 @@ k_gate_adj(const uint2* __restrict__ rp, int64_t P, const double2* __restrict__ 
   if (threadIdx.x == 0) gpart[blockIdx.x] = s;
 }
 
-// Groups gi in [g0, g1) of one bucket against a staged source row: for each
-// group in order, lanes walk list entries [e0, e1) (this warp's share, or the
-// whole list) and add f_g(src) psi_s[Jb] into lam_s[Ib]. The next group's
-// record and range are loaded while the current group runs; U list entries per
-// lane are in flight (8 with real amplitudes in the wide block form and in the
-// warp form, else 4: the best measured for each). Entries of one list have
-// distinct Ib, and __syncwarp separates the groups, so each output is updated
-// by one lane at a time, in group order (U does not change the order).
-template <bool REAL, int U>
-__device__ __forceinline__ void str_groups(const StrPlan& sp, int g0, int g1, int w_lo, int w_hi, uint32_t ka,
-                                           const GroupRec* __restrict__ groups, const uint32_t* __restrict__ emask,
-                                           const typename Amp<REAL>::C* __restrict__ vals, const uint32_t* kb_s,
-                                           const typename Amp<REAL>::T* psi_s, typename Amp<REAL>::T* lam_s,
-                                           int lane) {
-  typedef Amp<REAL> A;
-  if (g0 >= g1) return;
-  GroupRec g = load_group(groups + __ldg(sp.bgrp + g0));
-  int e0 = __ldg(sp.bsplit + int64_t(g0) * (kStrWarps + 1) + w_lo);
-  int e1 = __ldg(sp.bsplit + int64_t(g0) * (kStrWarps + 1) + w_hi);
-  for (int gi = g0; gi < g1; ++gi) {
-    GroupRec gn = g;
-    int e0n = 0, e1n = 0;
-    if (gi + 1 < g1) {
-      gn = load_group(groups + __ldg(sp.bgrp + gi + 1));
-      e0n = __ldg(sp.bsplit + int64_t(gi + 1) * (kStrWarps + 1) + w_lo);
-      e1n = __ldg(sp.bsplit + int64_t(gi + 1) * (kStrWarps + 1) + w_hi);
-    }
-    for (int e = e0 + lane; e < e1; e += U * 32) {
-      uint32_t ent[U];
-#pragma unroll
-      for (int u = 0; u < U; ++u) ent[u] = (e + 32 * u < e1) ? __ldg(sp.lists + e + 32 * u) : 0xFFFFFFFFu;
-#pragma unroll
-      for (int u = 0; u < U; ++u) {
-        if (ent[u] == 0xFFFFFFFFu) break;
-        const uint32_t ib = ent[u] & 0xFFFFu, jb = ent[u] >> 16;
-        A::mac(lam_s[ib], group_coef<REAL>(g, emask, vals, ka | kb_s[jb]), psi_s[jb]);
-      }
-    }
-    __syncwarp();
-    g = gn;
-    e0 = e0n;
-    e1 = e1n;
-  }
-}
-
-// String-driven H psi (spin sectors; see StrPlan), block form for large beta
-// string sets: lambda[Ia, :] for one output alpha string per block. For each
-// bucket with a source alpha string Ja, the source row psi[Ja, :] is staged in
-// shared memory; then every warp walks its share (a fixed Ib range) of each
-// group's beta pair list. Needs blockDim.x == 32 * kStrWarps and 2 * Db
-// amplitudes (+ Db words of beta strings when Db < kStrWideDb; above, they are
-// read from global memory through L1) of shared memory.
-template <bool REAL, bool WIDE>
-__device__ __forceinline__ void hpsi_str_row(const StrPlan& sp, int ia, const GroupRec* __restrict__ groups,
-                                             const uint32_t* __restrict__ emask,
-                                             const typename Amp<REAL>::C* __restrict__ vals,
-                                             const typename Amp<REAL>::T* __restrict__ psi_am,
-                                             typename Amp<REAL>::T* __restrict__ lam_am, unsigned char* smem) {
-  typedef Amp<REAL> A;
-  typedef typename A::T T;
-  const int tid = threadIdx.x, bs = blockDim.x, w = tid >> 5, lane = tid & 31;
-  const int Db = sp.Db, NB = sp.NB;
-  T* psi_s = reinterpret_cast<T*>(smem);
-  T* lam_s = psi_s + Db;
-  uint32_t* kb_stage = reinterpret_cast<uint32_t*>(lam_s + Db);
-  const uint32_t* kb_s = WIDE ? sp.kb : kb_stage;
-  for (int j = tid; j < Db; j += bs) {
-    lam_s[j] = A::zero();
-    if (!WIDE) kb_stage[j] = __ldg(sp.kb + j);
-  }
-  for (int b = 0; b < NB; ++b) {
-    const int ja = __ldg(sp.ja + int64_t(ia) * NB + b);
-    if (ja < 0) continue;  // same for the whole block
-    const T* row = psi_am + int64_t(ja) * Db;
-    {
-      // A bucket holding a single group that leaves the beta string unchanged
-      // (an alpha-alpha double, most buckets at 24-30 qubits): every output
-      // beta string takes one term from the same position of the source row, so
-      // it is read straight from global memory, without staging or a pair list.
-      // Each output still gets its terms in bucket order: the same bits.
-      const int g0 = __ldg(sp.boff + b);
-      if (__ldg(sp.boff + b + 1) - g0 == 1) {
-        const GroupRec g = load_group(groups + __ldg(sp.bgrp + g0));
-        if ((g.x & 0xAAAAAAAAu) == 0) {
-          __syncthreads();  // outputs were last updated under the list path's thread mapping
-          const uint32_t ka = __ldg(sp.ka + ja);
-          for (int j = tid; j < Db; j += bs) A::mac(lam_s[j], group_coef<REAL>(g, emask, vals, ka | kb_s[j]), row[j]);
-          continue;
-        }
-      }
-    }
-    __syncthreads();       // the previous source row is no longer read
-    for (int j = tid; j < Db; j += bs) psi_s[j] = row[j];
-    __syncthreads();
-    str_groups<REAL, (WIDE && REAL) ? 8 : 4>(sp, __ldg(sp.boff + b), __ldg(sp.boff + b + 1), w, w + 1, __ldg(sp.ka + ja), groups, emask,
-                     vals, kb_s, psi_s, lam_s, lane);
-  }
-  __syncthreads();
-  T* out = lam_am + int64_t(ia) * Db;
-  for (int j = tid; j < Db; j += bs) out[j] = lam_s[j];
-}
-
-// Warp form for small beta string sets: each warp owns one output alpha string
-// (ia0 + warp), stages its own source rows and walks whole lists; the same
-// per-output order as the block form, so the same bits. Shared memory: Db
-// words of beta strings, then 2 * Db amplitudes per warp.
-template <bool REAL>
-__device__ __forceinline__ void hpsi_str_warps(const StrPlan& sp, int ia0, const GroupRec* __restrict__ groups,
-                                               const uint32_t* __restrict__ emask,
-                                               const typename Amp<REAL>::C* __restrict__ vals,
-                                               const typename Amp<REAL>::T* __restrict__ psi_am,
-                                               typename Amp<REAL>::T* __restrict__ lam_am, unsigned char* smem) {
-  typedef Amp<REAL> A;
-  typedef typename A::T T;
-  const int tid = threadIdx.x, bs = blockDim.x, w = tid >> 5, lane = tid & 31;
-  const int Db = sp.Db, NB = sp.NB;
-  uint32_t* kb_s = reinterpret_cast<uint32_t*>(smem);
-  T* psi_s = reinterpret_cast<T*>(smem + align_up(uint32_t(Db) * 4u, 16u)) + int64_t(w) * 2 * Db;
-  T* lam_s = psi_s + Db;
-  for (int j = tid; j < Db; j += bs) kb_s[j] = __ldg(sp.kb + j);
-  __syncthreads();
-  const int ia = ia0 + w;
-  if (ia >= sp.Da) return;  // no block-wide barrier follows
-  for (int j = lane; j < Db; j += 32) lam_s[j] = A::zero();
-  for (int b = 0; b < NB; ++b) {
-    const int ja = __ldg(sp.ja + int64_t(ia) * NB + b);
-    if (ja < 0) continue;  // same for the whole warp
-    const T* row = psi_am + int64_t(ja) * Db;
-    {
-      // single beta-diagonal group: read the source row directly (as in the block form)
-      const int g0 = __ldg(sp.boff + b);
-      if (__ldg(sp.boff + b + 1) - g0 == 1) {
-        const GroupRec g = load_group(groups + __ldg(sp.bgrp + g0));
-        if ((g.x & 0xAAAAAAAAu) == 0) {
-          __syncwarp();
-          const uint32_t ka = __ldg(sp.ka + ja);
-          for (int j = lane; j < Db; j += 32) A::mac(lam_s[j], group_coef<REAL>(g, emask, vals, ka | kb_s[j]), row[j]);
-          continue;
-        }
-      }
-    }
-    __syncwarp();
-    for (int j = lane; j < Db; j += 32) psi_s[j] = row[j];
-    __syncwarp();
-    str_groups<REAL, REAL ? 8 : 4>(sp, __ldg(sp.boff + b), __ldg(sp.boff + b + 1), 0, kStrWarps, __ldg(sp.ka + ja), groups, emask,
-                     vals, kb_s, psi_s, lam_s, lane);
-  }
-  __syncwarp();
-  T* out = lam_am + int64_t(ia) * Db;
-  for (int j = lane; j < Db; j += 32) out[j] = lam_s[j];
-}
-
 // WIDE: the block form for Db >= kStrWideDb (smaller shared-memory footprint,
 // four blocks per SM); the other instance runs three.
 template <bool REAL, bool WIDE>
@@ -1213,205 +668,6 @@ __global__ void k_gather_in(const uint32_t* __restrict__ sector, int64_t D, cons
 
 }  // namespace
 
-// ---------------------------------------------------------------- batched streaming (gate-major)
-__device__ __forceinline__ int find_seg(const int64_t* __restrict__ pref, int nseg, int64_t item) {
-  int lo = 0, hi = nseg;  // pref[lo] <= item < pref[hi]
-  while (hi - lo > 1) {
-    const int mid = (lo + hi) >> 1;
-    if (__ldg(pref + mid) <= item)
-      lo = mid;
-    else
-      hi = mid;
-  }
-  return lo;
-}
-
-// cos/sin of every (instance, gate)
-__global__ void kb_trig(BatchDev b, const double* __restrict__ theta, int64_t ld) {
-  const int64_t n_items = int64_t(b.n) * b.Mmax;
-  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < n_items; t += int64_t(gridDim.x) * blockDim.x) {
-    const int i = int(t / b.Mmax), m = int(t % b.Mmax);
-    const InstDesc* d = b.desc + i;
-    if (m < d->M) {
-      double sn, c;
-      sincos(theta[d->inst * ld + m], &sn, &c);
-      b.cs[t] = make_double2(c, sn);
-    }
-  }
-}
-
-__global__ void kb_init(BatchDev b, BatchSegs sg) {
-  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < sg.total; t += int64_t(gridDim.x) * blockDim.x) {
-    const int s = find_seg(sg.pref, sg.nseg, t);
-    const int i = __ldg(sg.inst + s);
-    const int64_t r = t - __ldg(sg.pref + s);
-    const InstDesc* d = b.desc + i;
-    double* psi = reinterpret_cast<double*>(b.ws + b.psi_off[i]);
-    const uint32_t k = __ldg(d->sector + r);
-    psi[r] = (k == d->hf) ? 1.0 : 0.0;
-  }
-}
-
-__global__ void __launch_bounds__(512) kb_gate_fwd(int m, BatchDev b, BatchSegs sg) {
-  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < sg.total; t += int64_t(gridDim.x) * blockDim.x) {
-    const int s = find_seg(sg.pref, sg.nseg, t);
-    const int i = __ldg(sg.inst + s);
-    const int64_t q = t - __ldg(sg.pref + s);
-    const InstDesc* d = b.desc + i;
-    double* psi = reinterpret_cast<double*>(b.ws + b.psi_off[i]);
-    const double2 c_s = b.cs[int64_t(i) * b.Mmax + m];
-    const uint2 pr = __ldg(d->rpairs + __ldg(d->pair_off + m) + q);
-    const uint32_t ra = pr.x & 0x7fffffffu, rb = pr.y;
-    const int sb = int(pr.x >> 31);
-    const double ss = sflip(c_s.y, sb), nss = sflip(c_s.y, sb ^ 1);
-    double a = psi[ra], bb = psi[rb];
-    Amp<true>::rot(a, bb, c_s.x, ss, nss);
-    psi[ra] = a;
-    psi[rb] = bb;
-  }
-}
-
-__global__ void __launch_bounds__(512, 1) kb_hpsi(BatchDev b, BatchSegs sg) {
-  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < sg.total; t += int64_t(gridDim.x) * blockDim.x) {
-    const int s = find_seg(sg.pref, sg.nseg, t);
-    const int i = __ldg(sg.inst + s);
-    const int64_t r = t - __ldg(sg.pref + s);
-    const InstDesc* d = b.desc + i;
-    const double* psi = reinterpret_cast<const double*>(b.ws + b.psi_off[i]);
-    double* lam = reinterpret_cast<double*>(b.ws + b.lam_off[i]);
-    const uint32_t k = __ldg(d->sector + r);
-    const GroupRec* groups = d->groups;
-    const uint32_t* emask = d->emask;
-    const double* vals = d->vals;
-    const int W = d->W, G = d->G;
-    const int64_t D = d->D;
-    double acc = 0.0;
-    if (W > 0) {
-      const uint32_t* ell = d->ell;
-      const uint16_t* ell16 = d->ell16;
-      acc = hpsi_row<true, 4>(ell, ell16, W, D, r, k, groups, emask, vals, psi, d->rank_hi, d->rank_lo,
-                              d->lo_bits);
-    } else {
-      const int ne = d->n_elec, na = d->n_alpha;
-      for (int gi = 0; gi < G; ++gi) {
-        const GroupRec g = load_group(groups + gi);
-        const uint32_t src = k ^ g.x;
-        if (!in_sector(src, ne, na)) continue;
-        acc = fma(group_coef<true>(g, emask, vals, src), psi[sector_rank(*d, src)], acc);
-      }
-    }
-    lam[r] = acc;
-    b.ebuf[b.ebase[i] + r] = psi[r] * acc;
-  }
-}
-
-// String-driven H psi over the batch: block -> (instance slot, output alpha string)
-__global__ void __launch_bounds__(kStrWarps * 32, 2) kb_hpsi_str(BatchDev b, BatchSegs sg) {
-  extern __shared__ __align__(16) unsigned char smem[];
-  const int s = find_seg(sg.pref, sg.nseg, int64_t(blockIdx.x));
-  const int i = __ldg(sg.inst + s);
-  const int blk = int(int64_t(blockIdx.x) - __ldg(sg.pref + s));
-  const InstDesc* d = b.desc + i;
-  const StrPlan sp = *d->str;
-  const double* psi_am = reinterpret_cast<const double*>(b.ws + b.am_off[i]);
-  double* lam_am = reinterpret_cast<double*>(b.ws + b.am_off[i]) + d->D;
-  if (sp.Db >= kStrMinDb)
-    if (sp.Db >= kStrWideDb)
-      hpsi_str_row<true, true>(sp, blk, d->groups, d->emask, d->vals, psi_am, lam_am, smem);
-    else
-      hpsi_str_row<true, false>(sp, blk, d->groups, d->emask, d->vals, psi_am, lam_am, smem);
-  else
-    hpsi_str_warps<true>(sp, blk * kStrWarps, d->groups, d->emask, d->vals, psi_am, lam_am, smem);
-}
-
-// alpha-major copy of every instance's psi
-__global__ void kb_perm_gather(BatchDev b, BatchSegs sg) {
-  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < sg.total; t += int64_t(gridDim.x) * blockDim.x) {
-    const int s = find_seg(sg.pref, sg.nseg, t);
-    const int i = __ldg(sg.inst + s);
-    const int64_t r = t - __ldg(sg.pref + s);
-    const InstDesc* d = b.desc + i;
-    const double* psi = reinterpret_cast<const double*>(b.ws + b.psi_off[i]);
-    double* psi_am = reinterpret_cast<double*>(b.ws + b.am_off[i]);
-    psi_am[r] = psi[__ldg(d->str->perm + r)];
-  }
-}
-
-// lambda back to sector order, and the per-output energy terms psi_r lambda_r
-__global__ void kb_perm_scatter(BatchDev b, BatchSegs sg) {
-  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < sg.total; t += int64_t(gridDim.x) * blockDim.x) {
-    const int s = find_seg(sg.pref, sg.nseg, t);
-    const int i = __ldg(sg.inst + s);
-    const int64_t r = t - __ldg(sg.pref + s);
-    const InstDesc* d = b.desc + i;
-    const double* psi = reinterpret_cast<const double*>(b.ws + b.psi_off[i]);
-    double* lam = reinterpret_cast<double*>(b.ws + b.lam_off[i]);
-    const double* lam_am = reinterpret_cast<const double*>(b.ws + b.am_off[i]) + d->D;
-    const uint32_t k = __ldg(d->str->perm + r);
-    const double v = lam_am[r];
-    lam[k] = v;
-    b.ebuf[b.ebase[i] + k] = psi[k] * v;
-  }
-}
-
-// E of instance slot blockIdx.x: fixed-order sum of its per-output terms
-__global__ void kb_energy(BatchDev b, double* __restrict__ energy) {
-  __shared__ double red[32];
-  const int i = blockIdx.x;
-  const InstDesc* d = b.desc + i;
-  const double* e = b.ebuf + b.ebase[i];
-  double acc = 0.0;
-  for (int64_t r = threadIdx.x; r < d->D; r += blockDim.x) acc += e[r];
-  const double tot = block_sum(acc, red);
-  if (threadIdx.x == 0) energy[d->inst] = tot;
-}
-
-__global__ void __launch_bounds__(512) kb_gate_adj(int m, BatchDev b, BatchSegs sg) {
-  for (int64_t t = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; t < sg.total; t += int64_t(gridDim.x) * blockDim.x) {
-    const int s = find_seg(sg.pref, sg.nseg, t);
-    const int i = __ldg(sg.inst + s);
-    const int64_t q = t - __ldg(sg.pref + s);
-    const InstDesc* d = b.desc + i;
-    double* phi = reinterpret_cast<double*>(b.ws + b.psi_off[i]);
-    double* lam = reinterpret_cast<double*>(b.ws + b.lam_off[i]);
-    const double2 c_s = b.cs[int64_t(i) * b.Mmax + m];
-    const int64_t p = __ldg(d->pair_off + m) + q;
-    const uint2 pr = __ldg(d->rpairs + p);
-    const uint32_t ra = pr.x & 0x7fffffffu, rb = pr.y;
-    const int sb = int(pr.x >> 31);
-    const double ss = sflip(c_s.y, sb), nss = sflip(c_s.y, sb ^ 1);
-    double pa = phi[ra], pb = phi[rb], la = lam[ra], lb = lam[rb];
-    b.gbuf[b.gbase[i] + p] = sflip(Amp<true>::cross(lb, pa, la, pb), sb);
-    Amp<true>::rot(pa, pb, c_s.x, nss, ss);
-    Amp<true>::rot(la, lb, c_s.x, nss, ss);
-    phi[ra] = pa;
-    phi[rb] = pb;
-    lam[ra] = la;
-    lam[rb] = lb;
-  }
-}
-
-// g of (instance, gate) pair blockIdx.x: fixed-order sum of its pair contributions
-__global__ void kb_grad(BatchDev b, const int32_t* __restrict__ gm_inst, const int32_t* __restrict__ gm_gate,
-                        double* __restrict__ grad, int64_t ld_grad) {
-  __shared__ double red[32];
-  const int i = gm_inst[blockIdx.x], m = gm_gate[blockIdx.x];
-  const InstDesc* d = b.desc + i;
-  const int64_t p0 = d->pair_off[m], p1 = d->pair_off[m + 1];
-  const double* gb = b.gbuf + b.gbase[i];
-  double acc = 0.0;
-  for (int64_t p = p0 + threadIdx.x; p < p1; p += blockDim.x) acc += gb[p];
-  const double tot = block_sum(acc, red);
-  if (threadIdx.x == 0) grad[d->inst * ld_grad + m] = 2.0 * tot;
-}
-
-inline int batch_grid(int64_t total, int threads) {
-  int64_t g = (total + threads - 1) / threads;
-  if (g < 1) g = 1;
-  if (g > 152 * 16) g = 152 * 16;
-  return int(g);
-}
-
 // ---------------------------------------------------------------- device-built connectivity
 __global__ void k_ell_count(const uint32_t* __restrict__ sector, int64_t D, const GroupRec* __restrict__ groups, int G,
                             int n_elec, int n_alpha, int32_t* __restrict__ len, int32_t* __restrict__ wmax) {
@@ -1449,7 +705,6 @@ cudaError_t set_str_smem_limit(size_t smem) {
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_hpsi_str<false, false>, a, b);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_hpsi_str<true, true>, a, b);
   if (e == cudaSuccess) e = cudaFuncSetAttribute(k_hpsi_str<false, true>, a, b);
-  if (e == cudaSuccess) e = cudaFuncSetAttribute(kb_hpsi_str, a, b);
   return e;
 }
 
@@ -1606,33 +861,9 @@ cudaError_t stream_apply_h(const InstDesc& d, const StreamPlan& sp, const Stream
   return cudaGetLastError();
 }
 
-cudaError_t batch_stream_run(const BatchDev& b, const BatchSegs* gate_segs, const BatchSegs& out_segs,
-                             const BatchSegs& str_segs, size_t str_smem,
-                             const int32_t* d_gm_inst, const int32_t* d_gm_gate, int64_t n_gm,
-                             const double* theta, int64_t ld_theta, double* energy, double* grad,
-                             int64_t ld_grad, int threads, cudaStream_t stream) {
-  if (b.n == 0) return cudaSuccess;
-  const int nt = threads;
-  if (b.Mmax > 0) kb_trig<<<batch_grid(int64_t(b.n) * b.Mmax, nt), nt, 0, stream>>>(b, theta, ld_theta);
-  kb_init<<<batch_grid(out_segs.total, nt), nt, 0, stream>>>(b, out_segs);
-  for (int m = 0; m < b.Mmax; ++m)
-    if (gate_segs[m].total > 0)
-      kb_gate_fwd<<<batch_grid(gate_segs[m].total, nt), nt, 0, stream>>>(m, b, gate_segs[m]);
-  if (str_segs.total > 0) {
-    kb_perm_gather<<<batch_grid(out_segs.total, nt), nt, 0, stream>>>(b, out_segs);
-    kb_hpsi_str<<<unsigned(str_segs.total), kStrWarps * 32, str_smem, stream>>>(b, str_segs);
-    kb_perm_scatter<<<batch_grid(out_segs.total, nt), nt, 0, stream>>>(b, out_segs);
-  } else {
-    kb_hpsi<<<batch_grid(out_segs.total, nt), nt, 0, stream>>>(b, out_segs);
-  }
-  kb_energy<<<b.n, 256, 0, stream>>>(b, energy);
-  if (grad) {
-    for (int m = b.Mmax - 1; m >= 0; --m)
-      if (gate_segs[m].total > 0)
-        kb_gate_adj<<<batch_grid(gate_segs[m].total, nt), nt, 0, stream>>>(m, b, gate_segs[m]);
-    if (n_gm > 0) kb_grad<<<int(n_gm), 128, 0, stream>>>(b, d_gm_inst, d_gm_gate, grad, ld_grad);
-  }
-  return cudaGetLastError();
+cudaError_t stream_apply_h_real(const InstDesc& d, const StreamPlan& sp, const StreamBuffers& b, double* energy,
+                                cudaStream_t stream) {
+  return stream_hpsi<true>(d, sp, b, energy, stream);
 }
 
 cudaError_t ell_device_count(const uint32_t* sector, int64_t D, const GroupRec* groups, int G, const int32_t* order,

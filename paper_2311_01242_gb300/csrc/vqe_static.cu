@@ -18,6 +18,12 @@
 // call (the state's sector entries, H psi, the cos/sin table and every
 // reduction partial), so nothing needs clearing. Calls whose work overlaps on
 // the GPU (two streams, or two threads) race on the array.
+//
+// H psi takes the fastest path that needs no new tables: when an earlier call
+// (vqe_workspace_bytes, vqe_energy_grad, a batch) already built the string or
+// connectivity tables of this (Hamiltonian, sector) pair, they are used, with
+// the same kernels and results as vqe_energy_grad; otherwise every output
+// scans all X-mask groups. The scratch holds only the vectors that path uses.
 #include <atomic>
 #include <string>
 
@@ -55,8 +61,8 @@ extern "C" int vqe_energy_grad_noalloc(vqe_hamiltonian_t h, vqe_ansatz_t a, cons
   vqe::InstDesc d;
   vqe::StreamPlan sp;
   bool real = true;
-  size_t off[5], need = 0;
-  int rc = vqe::prepare_noalloc(h, a, with_grad, &d, &sp, &real, off, &need);
+  size_t off[7], need = 0;
+  int rc = vqe::prepare_noalloc(h, a, with_grad, kScratchBytes, &d, &sp, &real, off, &need);
   if (rc != VQE_OK) return rc;
   if ((theta_dev == nullptr && d.M > 0) || energy_dev == nullptr)
     return vqe::set_error(VQE_ERR_INVALID_ARG, "NULL device pointer");
@@ -69,9 +75,13 @@ extern "C" int vqe_energy_grad_noalloc(vqe_hamiltonian_t h, vqe_ansatz_t a, cons
   vqe::StreamBuffers buf;
   buf.psi = b + off[0];
   buf.lam = b + off[1];
-  buf.cs = reinterpret_cast<double2*>(b + off[2]);
-  buf.epart = reinterpret_cast<double*>(b + off[3]);
-  buf.gpart = reinterpret_cast<double*>(b + off[4]);
+  if (sp.use_str) {
+    buf.psi_am = b + off[2];
+    buf.lam_am = b + off[3];
+  }
+  buf.cs = reinterpret_cast<double2*>(b + off[4]);
+  buf.epart = reinterpret_cast<double*>(b + off[5]);
+  buf.gpart = reinterpret_cast<double*>(b + off[6]);
   ce = vqe::stream_energy_grad(d, sp, buf, real, with_grad, theta_dev, energy_dev, grad_dev,
                                static_cast<cudaStream_t>(stream));
   if (ce != cudaSuccess)

@@ -178,5 +178,5 @@ def compare_starts(geom, starts, e_exact, gtol=1e-7, maxiter=3000, tol_ha=1e-3):
     for name, (_, e, hist) in runs.items():
         k = next((i for i, (ev, _) in enumerate(hist) if ev <= target), None)
         out[name] = {"evals": None if k is None else k + 1, "seconds": None if k is None else hist[k][1],
-                     "e_conv": e, "evals_total": len(hist)}
+                     "e_conv": e, "evals_total": len(hist), "seconds_total": hist[-1][1] if hist else 0.0}
     return out

@@ -76,9 +76,10 @@ def test_graph_replay_and_tuning_do_not_change_results(mixed, tmp_path):
     e2_ref, g2_ref = B.energy_grad(theta2.contiguous())
     assert _same(e2, g2, e2_ref, g2_ref, ms)
     cache = str(tmp_path / "tune.json")
-    choice, timings = vb.autotune(B, theta, stream_threads=(128, 512), sweep_threads=(64, 128), reps=2,
-                                  cache_path=cache)
-    assert len(timings) == 4 and choice in [(128, 64), (128, 128), (512, 64), (512, 128)]
+    choice, timings = vb.autotune(B, theta, ctas_per_sm=(1, 2), gate_chunk=(256, 1024), sweep_threads=(64, 128),
+                                  reps=2, cache_path=cache)
+    assert len(timings) == 8
+    assert choice in [(c, g, w) for c in (1, 2) for g in (256, 1024) for w in (64, 128)]
     e3, g3 = B.energy_grad(theta)
     assert _same(e3, g3, e_ref, g_ref, ms)
     choice2, _ = vb.autotune(B, theta, cache_path=cache)  # served from the cache
@@ -115,15 +116,14 @@ def test_host_entry_replays_graph_with_new_inputs(mixed):
     finally:
         vq.set_flags(old)
     B.energy_grad_host(th_h.numpy(), e_h.numpy(), g_h.numpy(), ws)
-    vb_threads = 128
-    assert vq.api._lib().vqe_batch_set_tuning(B.handle, vb_threads, 96) == 0
+    B.set_tuning(1, 512, 96)
     try:
         e2 = e_h.clone()
         B.energy_grad_host(th_h.numpy(), e_h.numpy(), g_h.numpy(), ws)
         B.energy_grad_host(th_h.numpy(), e_h.numpy(), g_h.numpy(), ws)
         assert torch.equal(e_h, e2)
     finally:
-        vq.api._lib().vqe_batch_set_tuning(B.handle, 256, 128)
+        B.set_tuning(0, 1024, 128)
 
 
 def test_prepared_host_call_matches_host_entry(mixed):
@@ -146,3 +146,64 @@ def test_prepared_host_call_matches_host_entry(mixed):
         assert np.array_equal(e_h.numpy(), e_ref), scale
         for i, a in enumerate(ans):
             assert np.array_equal(g_h.numpy()[i, :a.n_params], g_ref[i, :a.n_params]), (scale, i)
+
+
+def test_persistent_batch_equals_single_calls_bitwise(mixed):
+    """The streamed instances (14 and 16 qubits) run in the persistent launch;
+    every energy and gradient equals vqe_energy_grad's bit for bit, for every
+    launch shape."""
+    insts, hams, ans, B, theta = mixed
+    streamed = [i for i, (p, _, _) in enumerate(insts) if p.n_qubits >= 14]
+    ref = []
+    for i in streamed:
+        m = ans[i].n_params
+        e1, g1 = vq.energy_grad(hams[i], ans[i], theta[i, :m].contiguous())
+        ref.append((e1.clone(), g1.clone()))
+    for shape in ((0, 1024, 128), (1, 256, 128), (2, 4096, 128)):
+        B.set_tuning(*shape)
+        t = B.tuning()
+        assert t["grid"] > 0 and t["n_tasks"] > 0
+        e, g = B.energy_grad(theta)
+        for (e1, g1), i in zip(ref, streamed):
+            m = ans[i].n_params
+            assert torch.equal(e[i], e1), (shape, i)
+            assert torch.equal(g[i, :m], g1), (shape, i)
+    B.set_tuning(0, 1024, 128)
+
+
+def test_persistent_wait_runs_out_and_reports_timeout(mixed):
+    """A task made to wait for a count that nothing reaches: its wait ends after
+    the budget, the status word reports the task, every persistent output is
+    NaN, the resident instances are untouched, the host-buffer call returns
+    VQE_ERR_TIMEOUT, and the next normal call is correct again."""
+    insts, hams, ans, B, theta = mixed
+    streamed = [i for i, (p, _, _) in enumerate(insts) if p.n_qubits >= 14]
+    resident = [i for i in range(len(insts)) if i not in streamed]
+    e_ref, g_ref = [t.clone() for t in B.energy_grad(theta)]
+    ws = vq.alloc_workspace(B.workspace_bytes(True))
+    e = torch.zeros(len(insts), dtype=torch.float64, device="cuda")
+    g = torch.zeros(len(insts), B.max_params, dtype=torch.float64, device="cuda")
+    n_tasks = B.tuning()["n_tasks"]
+    for probe in (0, n_tasks // 2):
+        B.set_wait(budget_ns=2_000_000, probe_task=probe)
+        try:
+            B.energy_grad(theta, e, g, ws)
+            with pytest.raises(vq.VQEError) as ex:
+                B.status(ws)
+            assert ex.value.code == 4 and "ran out" in str(ex.value)
+            assert torch.isnan(e[streamed]).all()
+            for i in resident:
+                assert torch.equal(e[i], e_ref[i])
+            n, M = len(insts), B.max_params
+            th_h = theta.cpu().clone().pin_memory()
+            e_h = torch.empty(n, dtype=torch.float64).pin_memory()
+            g_h = torch.empty(n, M, dtype=torch.float64).pin_memory()
+            wsh = vq.alloc_workspace(B.host_workspace_bytes(True))
+            with pytest.raises(vq.VQEError) as ex:
+                B.energy_grad_host(th_h.numpy(), e_h.numpy(), g_h.numpy(), wsh)
+            assert ex.value.code == 4
+        finally:
+            B.set_wait(2_000_000_000, -1)
+    B.energy_grad(theta, e, g, ws)
+    B.status(ws)
+    assert torch.equal(e, e_ref)

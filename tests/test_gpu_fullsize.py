@@ -8,7 +8,10 @@ whose spectrum is {0, +-i}); one H psi pass on a random sector vector equals
 the oracle's explicit Pauli action at sampled rows; psi(theta) after 512 gates
 has unit norm and no weight outside the sector. 256 uneven instances (14-20 qubits): the batched
 launch agrees with single-instance calls on sampled instances, and with the
-oracle on the smallest ones.
+oracle on the smallest ones. The real-amplitude string-driven H psi of the
+energy and gradient calls, in each of its three forms (warp form at 20 qubits,
+staged block form at 24, wide block form at 30), equals the oracle's explicit
+Pauli action at sampled rows.
 """
 import numpy as np
 import pytest
@@ -76,8 +79,8 @@ def test_config2_full_batch_matches_single_calls_and_oracle():
     for i in rng.choice(256, size=6, replace=False):
         m = len(insts[i][2])
         e1, g1 = vq.energy_grad(hams[i], ans[i], theta[i, :m])
-        assert abs(float(e1) - e[i]) <= 1e-12
-        assert np.abs(g1.cpu().numpy() - g[i, :m]).max() <= 1e-12
+        assert float(e1) == e[i]                     # the persistent launch: the same bits
+        assert np.array_equal(g1.cpu().numpy(), g[i, :m])
     small = [i for i, (p, _, _) in enumerate(insts) if p.n_qubits == 14][:2]
     for i in small:
         p, exc, t = insts[i]
@@ -130,3 +133,44 @@ def test_30_qubits_hpsi_rows_norm_and_sector_support():
     e_real = float(vq.energy(H, A, th))
     _, e_cplx = vq.apply_hamiltonian(H, A, st)
     assert abs(e_real - float(e_cplx)) <= 1e-10
+
+
+def _real_rows(p, n, n_elec, drop, seed, n_rows=45):
+    """lambda = H psi through the real-amplitude kernels (vqe_apply_hamiltonian_sector)
+    on a random real sector vector, against oracle.pauli_sum_row on the oracle's
+    own Pauli list at sampled rows (first, last, HF and random ones)."""
+    xs, zs, cs = oracle.jordan_wigner(p, drop)
+    H = vq.Hamiltonian(n, xs, zs, cs)
+    A = vq.Ansatz(n, synth.hf_bitstring(n_elec), [[0, 2, -1, -1]])
+    na, nb = (n_elec + 1) // 2, n_elec // 2
+    sec = oracle.sector_basis(n, na, nb)
+    rng = np.random.default_rng(seed)
+    vals = rng.normal(size=len(sec))
+    vals /= np.linalg.norm(vals)
+    psi = torch.as_tensor(vals).cuda()
+    lam, e = vq.apply_hamiltonian_sector(H, A, psi)
+    lam = lam.cpu().numpy()
+    amp = _lookup(sec, vals)
+    rows = np.concatenate([[0, len(sec) - 1, int(np.searchsorted(sec, synth.hf_bitstring(n_elec)))],
+                           rng.choice(len(sec), n_rows, replace=False)])
+    for r in rows:
+        want = oracle.pauli_sum_row(xs, zs, cs, int(sec[r]), amp)
+        assert abs(want.imag) <= 1e-12  # a real Hamiltonian: real rows for a real state
+        assert abs(lam[r] - want.real) <= 1e-12, (n, r, lam[r], want)
+    assert abs(float(e) - float(np.dot(vals, lam))) <= 1e-12
+
+
+def test_real_string_hpsi_rows_warp_form_20_qubits():
+    ns, _ = synth.configs.config2_sizes()
+    p, _, _ = synth.config2_instance(int(np.nonzero(ns == 20)[0][0]))
+    _real_rows(p, 20, 10, 1e-14, 20)
+
+
+def test_real_string_hpsi_rows_staged_block_form_24_qubits():
+    p = synth.integrals.random_problem(np.random.default_rng(24), 12, 10, 6, label="q24")
+    _real_rows(p, 24, 10, 1e-14, 24)
+
+
+def test_real_string_hpsi_rows_wide_block_form_30_qubits():
+    w = synth.config3()
+    _real_rows(w.problems[0], 30, 10, w.drop_tol, 31)
