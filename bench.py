@@ -38,8 +38,8 @@ FP64_PEAK_TFLOPS = FP64_DFMA_PER_CLK_SM * N_SMS * SM_MAX_MHZ * 1e6 * 2 / 1e12
 # 64-bit integer high multiplies (__umul64hi) sustained per clock per SM, measured
 # by an integer throughput probe on this GB300 (the fixed-point kernels' multiply)
 INT_MUL64_PER_CLK_SM = 6.7
-PROFILE_SUMMARY = os.path.join(ROOT, "profiles", "k_resident_config1.md")
-KERNEL_SRC = os.path.join(ROOT, "paper_2311_01242_gb300", "csrc", "vqe_kernels.cu")
+# sources of the single-instance kernels (their ncu summaries name these files' sha256)
+RESIDENT_SRC = ["vqe_kernels.cu", "vqe_device.cuh"]
 
 
 def parse():
@@ -256,28 +256,6 @@ def reduce_max(value, world, device=None):
 def throughput(units_per_rank, world, steps, max_seconds):
     """Whole-job units per second: every rank did units_per_rank per step."""
     return units_per_rank * world * steps / max_seconds
-
-
-def kernel_source_hash():
-    with open(KERNEL_SRC, "rb") as f:
-        return hashlib.sha256(f.read()).hexdigest()[:16]
-
-
-def profiled_traffic(per_launch_units):
-    """dram bytes per launch from the committed ncu summary (profiles/), scaled
-    to per_launch_units, if it was taken on the current kernel source; else None."""
-    import re
-    try:
-        with open(PROFILE_SUMMARY) as f:
-            text = f.read()
-    except OSError:
-        return None
-    sha = re.search(r"sha256 \(first 16 hex\): `([0-9a-f]+)`", text)
-    b = re.search(r"dram_bytes_per_launch: (\d+)", text)
-    units = re.search(r"units_per_launch: (\d+)", text)
-    if not (sha and b and units) or sha.group(1) != kernel_source_hash():
-        return None
-    return int(b.group(1)) * per_launch_units / int(units.group(1))
 
 
 def _timed(fn, steps, warmup):
@@ -801,6 +779,16 @@ def entry_config3(args, gpu_index):
     flops, state_bytes = vq.work_estimate(H, A, True)
     counts = vq.work_counts(H, A)
     ms = tm["ms_per_step"]
+    # A/B: the same evaluation with one launch per gate instead of the persistent sweeps
+    old = vq.set_flags(vq.VQE_FLAG_GATE_LAUNCHES)
+    try:
+        e_l = torch.empty(1, dtype=torch.float64, device="cuda")
+        g_l = torch.empty(len(exc), dtype=torch.float64, device="cuda")
+        tl, clocks_l = _measure(lambda: vq.energy_grad(H, A, theta, workspace=ws, out=(e_l, g_l)), min(steps, 5), 3,
+                                gpu_index)
+        same_bits = bool(torch.equal(e_l, e_buf) and torch.equal(g_l, g_buf))
+    finally:
+        vq.set_flags(old)
     # complex128 amplitudes and full complex coefficients (the same kernels' complex form)
     old = vq.set_flags(vq.VQE_FLAG_FORCE_COMPLEX)
     try:
@@ -827,7 +815,7 @@ def entry_config3(args, gpu_index):
     assert abs(float(e_np[0]) - e_real) <= 1e-12, "host-buffer and device calls disagree"
     del wsh, B
     peak_hbm, hbm_src = measured_hbm_gbs()
-    hpsi_dram = _profile_field("k_hpsi_str_config3.md", ["vqe_kernels.cu"], "dram_bytes_per_launch")
+    hpsi_dram = _profile_field("k_hpsi_str_config3.md", RESIDENT_SRC, "dram_bytes_per_launch")
     achieved = flops / (ms / 1e3) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP64_PEAK_TFLOPS, "kernel": "k_hpsi_str (wide block form) + k_gate_fwd/k_gate_adj",
@@ -847,6 +835,8 @@ def entry_config3(args, gpu_index):
             "e2e": e2e, "cpu_baseline": cpu,
             "complex128": {"value": 1e3 / tc["ms_per_step"], "unit": "evals/s", **tc, "clocks": clocks_c,
                            "abs_diff_energy_vs_real": d_e, "max_abs_diff_grad_vs_real": d_g},
+            "gate_sweeps": {"persistent_ms_per_step": ms, "one_launch_per_gate_ms_per_step": tl["ms_per_step"],
+                            "same_bits": same_bits, "clocks_per_gate_launches": clocks_l},
             "l2": "flushed between timed steps (512 MB write)"}
 
 
@@ -895,7 +885,7 @@ def entry_config2(args, gpu_index):
     assert np.abs(e_np - e_dev.cpu().numpy()).max() <= 1e-12, "host-buffer and graph replay disagree"
     del wsh
     peak_hbm, hbm_src = measured_hbm_gbs()
-    dram = _profile_field("k_batch_config2.md", ["vqe_kernels.cu", "vqe_batch.cu"], "dram_bytes_per_launch")
+    dram = _profile_field("k_batch_config2.md", ["vqe_batch.cu", "vqe_device.cuh"], "dram_bytes_per_launch")
     achieved = flops / (ms / 1e3) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP64_PEAK_TFLOPS, "kernel": "batched kernels of one graph replay",
@@ -1058,7 +1048,9 @@ def main():
     assert np.allclose(e_np, energies.cpu().numpy(), rtol=0, atol=0), "host and device entries disagree"
 
     achieved = flops_per_launch / (ms_per_step / 1000.0) / 1e12
-    traffic = profiled_traffic(n_inst)
+    dram = _profile_field("k_resident_config1.md", RESIDENT_SRC, "dram_bytes_per_launch")
+    units = _profile_field("k_resident_config1.md", RESIDENT_SRC, "units_per_launch")
+    traffic = None if dram is None or not units else dram * n_inst / units
     probe = vq.probe_fp64()  # untimed: confirms the per-SM FP64 rate behind the peak
     # the resource the kernel actually uses: 64-bit integer multiplies (fixed-point
     # sweeps: 2 per lane forward, 3 per lane in reverse, two lanes per pair; H psi:
@@ -1066,7 +1058,7 @@ def main():
     wc = vq.work_counts(hams[0], A)
     muls = n_inst * (10 * wc["n_pairs"] + wc["n_entries"])
     mul_peak = INT_MUL64_PER_CLK_SM * N_SMS * SM_MAX_MHZ * 1e6
-    issue_pct = _profile_field("k_resident_config1.md", ["vqe_kernels.cu"], "issue_active_pct")
+    issue_pct = _profile_field("k_resident_config1.md", RESIDENT_SRC, "issue_active_pct")
     line = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": world, "steps": K,
         "warmup": max(3, args.warmup), "ms_per_step": ms_per_step, "higher_is_better": True,

@@ -31,8 +31,10 @@
  * pair (vqe_workspace_bytes, vqe_work_counts, vqe_create_batch, or the first
  * compute call with that pair) builds the pair's connectivity or string tables,
  * synchronously, and the pair keeps them until the Hamiltonian is destroyed.
- * After that the compute calls allocate nothing, so make that first call
- * before any stream capture. Every compute call is asynchronous on the given
+ * Likewise the first streaming evaluation of an ansatz (or vqe_workspace_bytes
+ * with it) builds the task queues of its persistent gate sweeps. After that the
+ * compute calls allocate nothing, so make those first calls before any stream
+ * capture. Every compute call is asynchronous on the given
  * stream (a cudaStream_t; NULL is the legacy default stream) except where
  * noted.
  *
@@ -80,7 +82,10 @@ int vqe_version(void);
  *                            instead of 64-bit fixed point (H psi, the energy
  *                            and every streaming kernel are FP64 either way);
  *   VQE_FLAG_NO_STRINGS      streaming H psi by connectivity rows (or a scan of
- *                            all groups) instead of alpha/beta strings.
+ *                            all groups) instead of alpha/beta strings;
+ *   VQE_FLAG_GATE_LAUNCHES   streaming gate sweeps as one launch per gate
+ *                            instead of one persistent launch per sweep (the
+ *                            same bits either way).
  * Returns the previous flags. Not thread-safe against concurrent compute calls.
  */
 enum {
@@ -88,7 +93,8 @@ enum {
   VQE_FLAG_FORCE_STREAMING = 2,
   VQE_FLAG_NO_CLUSTER = 4,
   VQE_FLAG_FP64_SWEEPS = 8,
-  VQE_FLAG_NO_STRINGS = 16
+  VQE_FLAG_NO_STRINGS = 16,
+  VQE_FLAG_GATE_LAUNCHES = 32
 };
 int vqe_set_flags(int flags);
 

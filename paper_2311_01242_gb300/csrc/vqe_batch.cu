@@ -282,6 +282,36 @@ k_batch_persistent(const PersistDev p, const double* __restrict__ theta, int64_t
         }
         break;
       }
+      case PT_ADJS: {
+        // partials b in [lo, hi) of a gate with more than 2^18 pairs: partial b sums
+        // pairs b * 256 + t + j * (nb * 256), j = 0, 1, ..., in that order, exactly
+        // as k_gate_adj's block b does with nb = 1024 blocks
+        double* gp = at<double>(ws, so.gp) + tk.aux;
+        const double2 c_s = __ldcg(cs + tk.m);
+        const int64_t p0 = __ldg(d.pair_off + tk.m), P = __ldg(d.pair_off + tk.m + 1) - p0;
+        const uint2* rp = d.rpairs + p0;
+        const int64_t stride = int64_t(kMaxPartials) * kPersistThreads;
+        for (int64_t b = tk.lo; b < tk.hi; ++b) {
+          double acc = 0.0;
+          for (int64_t q = b * kPersistThreads + tid; q < P; q += stride) {
+            const uint2 pr = __ldg(rp + q);
+            const uint32_t ra = pr.x & 0x7fffffffu, rb = pr.y;
+            const int sb = int(pr.x >> 31);
+            const double ss = sflip(c_s.y, sb), nss = sflip(c_s.y, sb ^ 1);
+            double pa = __ldcg(psi + ra), pb = __ldcg(psi + rb), la = __ldcg(lam + ra), lb = __ldcg(lam + rb);
+            acc += sflip(Amp<true>::cross(lb, pa, la, pb), sb);
+            Amp<true>::rot(pa, pb, c_s.x, nss, ss);
+            Amp<true>::rot(la, lb, c_s.x, nss, ss);
+            psi[ra] = pa;
+            psi[rb] = pb;
+            lam[ra] = la;
+            lam[rb] = lb;
+          }
+          const double s = block_sum(acc, red);
+          if (tid == 0) gp[b] = s;
+        }
+        break;
+      }
       default:
         break;
     }
@@ -324,6 +354,13 @@ cudaError_t set_persist_smem_limit(size_t smem) {
 
 cudaError_t persist_occupancy(size_t smem, int* blocks_per_sm) {
   return cudaOccupancyMaxActiveBlocksPerMultiprocessor(blocks_per_sm, k_batch_persistent, kPersistThreads, smem);
+}
+
+cudaError_t persistent_sweep_run(const PersistDev& p, int grid, const double* theta, cudaStream_t stream) {
+  cudaError_t e = cudaMemsetAsync(p.counters, 0, size_t(p.n + 2) * sizeof(int), stream);
+  if (e != cudaSuccess) return e;
+  k_batch_persistent<<<grid, kPersistThreads, 0, stream>>>(p, theta, 0);
+  return cudaGetLastError();
 }
 
 cudaError_t batch_persistent_run(const PersistDev& p, int grid, size_t smem, const PFinal* rows, int n_rows,

@@ -331,8 +331,16 @@ struct vqe_ansatz_s {
   uint32_t* d_sector = nullptr;
   int32_t* d_nb_rows = nullptr;
   uint64_t serial = 0;  // never reused: keys cached batch plans
+  std::mutex sweep_mu;
+  std::unique_ptr<vqe::SweepPlan> sweep;  // persistent gate sweeps, built on first streaming use
   std::tuple<int, int, int> key() const { return std::make_tuple(n, n_elec, n_alpha); }
   ~vqe_ansatz_s() {
+    if (sweep) {
+      dfree(sweep->d_desc);
+      dfree(sweep->d_slot);
+      dfree(sweep->d_fwd);
+      dfree(sweep->d_adj);
+    }
     dfree(d_gates);
     dfree(d_pair_off);
     dfree(d_chunk_off);
@@ -879,7 +887,7 @@ bool resident_fit(vqe_ansatz_t a, const vqe_hamiltonian_s::Ell* e, bool real, In
 }
 
 struct WsLayout {
-  size_t psi, lam, psi_am, lam_am, cs, epart, gpart, total;
+  size_t psi, lam, psi_am, lam_am, cs, epart, ctr, gpart, total;
 };
 
 WsLayout ws_layout(vqe_ansatz_t a, bool complex_amp, bool with_grad) {
@@ -892,7 +900,8 @@ WsLayout ws_layout(vqe_ansatz_t a, bool complex_amp, bool with_grad) {
   L.lam_am = 3 * vec;
   L.cs = 4 * vec;
   L.epart = L.cs + align256(size_t(std::max(a->M, 1)) * 16);
-  L.gpart = L.epart + align256(size_t(vqe::kMaxPartials) * 8);
+  L.ctr = L.epart + align256(size_t(vqe::kMaxPartials) * 8);  // task counters of the persistent sweeps
+  L.gpart = L.ctr + 256;
   L.total = L.gpart + (with_grad ? align256(size_t(std::max(a->M, 1)) * vqe::kMaxPartials * 8) : 0);
   return L;
 }
@@ -910,8 +919,82 @@ vqe::StreamBuffers buffers(void* ws, const WsLayout& L) {
   return s;
 }
 
+// Task queues of the persistent gate sweeps of ansatz a (real amplitudes): the
+// forward queue holds the HF init and each gate's rotation in 2,048-pair tasks,
+// the adjoint queue each gate's adjoint step in tasks of four partial sums laid
+// out as k_gate_adj's blocks (so the gradient has the same bits as with one
+// launch per gate). Built once per ansatz, on its first streaming use; null if
+// the device refuses (the caller then launches per gate).
+const vqe::SweepPlan* get_sweep(vqe_ansatz_t a) {
+  std::lock_guard<std::mutex> lk(a->sweep_mu);
+  if (a->sweep) return a->sweep->grid > 0 ? a->sweep.get() : nullptr;
+  std::unique_ptr<vqe::SweepPlan> sp(new vqe::SweepPlan);
+  InstDesc d;
+  std::memset(&d, 0, sizeof(d));
+  d.n = a->n;
+  d.M = a->M;
+  d.hf = uint32_t(a->hf);
+  d.D = int64_t(a->sector.size());
+  d.sector = a->d_sector;
+  d.gates = a->d_gates;
+  d.pair_off = a->d_pair_off;
+  d.pairs = a->d_pairs;
+  d.rpairs = a->d_rpairs;
+  d.rank_hi = a->d_rank_hi;
+  d.rank_lo = a->d_rank_lo;
+  d.lo_bits = a->lo_bits;
+  d.n_elec = a->n_elec;
+  d.n_alpha = a->n_alpha;
+  const WsLayout L = ws_layout(a, false, true);
+  const vqe::PSlot ps{int64_t(L.psi), int64_t(L.lam), -1, -1, int64_t(L.cs), int64_t(L.epart), int64_t(L.gpart)};
+  std::vector<vqe::PTask> fwd, adj;
+  auto task = [](std::vector<vqe::PTask>& q, int kind, int m, int need, int64_t lo, int64_t hi, int64_t aux) {
+    vqe::PTask t;
+    t.slot = 0;
+    t.kind = kind;
+    t.m = m;
+    t.need = need;
+    t.lo = lo;
+    t.hi = hi;
+    t.aux = aux;
+    q.push_back(t);
+  };
+  task(fwd, vqe::PT_INIT, 0, 0, 0, d.D, 0);
+  const int64_t gc = 2048;
+  for (int m = 0; m < a->M; ++m) {
+    const int need = int(fwd.size());
+    const int64_t P = a->pair_off[m + 1] - a->pair_off[m];
+    for (int64_t lo = 0; lo < P; lo += gc) task(fwd, vqe::PT_FWD, m, need, lo, std::min(P, lo + gc), 0);
+  }
+  for (int m = a->M - 1; m >= 0; --m) {
+    const int need = int(adj.size());
+    const int nb = vqe::stream_grid(a->pair_off[m + 1] - a->pair_off[m]);
+    for (int b0 = 0; b0 < nb; b0 += 4)
+      task(adj, vqe::PT_ADJS, m, need, b0, std::min(nb, b0 + 4), int64_t(m) * vqe::kMaxPartials);
+  }
+  int dev = 0, sms = 0, per_sm = 0;
+  bool ok = cudaGetDevice(&dev) == cudaSuccess &&
+            cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) == cudaSuccess &&
+            vqe::persist_occupancy(0, &per_sm) == cudaSuccess && per_sm > 0 &&
+            fwd.size() < size_t(INT32_MAX / 2) && adj.size() < size_t(INT32_MAX / 2);
+  std::vector<InstDesc> dv(1, d);
+  std::vector<vqe::PSlot> sv(1, ps);
+  ok = ok && upload(dv, &sp->d_desc) == VQE_OK && upload(sv, &sp->d_slot) == VQE_OK &&
+       upload(fwd, &sp->d_fwd) == VQE_OK && (adj.empty() || upload(adj, &sp->d_adj) == VQE_OK);
+  cudaGetLastError();
+  sp->n_fwd = int32_t(fwd.size());
+  sp->n_adj = int32_t(adj.size());
+  sp->grid = ok ? sms * per_sm : 0;
+  a->sweep = std::move(sp);
+  return ok ? a->sweep.get() : nullptr;
+}
+
 vqe::StreamPlan plan(vqe_ansatz_t a, const vqe_hamiltonian_s::Ell* e) {
   vqe::StreamPlan p;
+  if (use_real() && !(g_flags & VQE_FLAG_GATE_LAUNCHES)) {
+    p.sweep = get_sweep(a);
+    p.counters_off = int64_t(ws_layout(a, false, false).ctr);
+  }
   p.pair_off_host = a->pair_off.data();
   p.d_nb_rows = a->d_nb_rows;
   p.n_elec = a->n_elec;
@@ -1015,6 +1098,7 @@ int prepare_noalloc(vqe_hamiltonian_s* h, vqe_ansatz_s* a, bool with_grad, size_
   }
   *d = make_desc(h, a, e, 0);
   *sp = plan(a, e);
+  sp->sweep = nullptr;  // one launch per gate: the sweep queues address the regular workspace layout
   // the string-driven H psi needs two more sector-sized vectors; when they do
   // not fit, the connectivity rows (if built) or the group scan serve instead
   const size_t amp = *real ? 8 : 16;
@@ -1716,6 +1800,7 @@ size_t vqe_workspace_bytes(vqe_hamiltonian_t h, vqe_ansatz_t a, int mode) {
   int rc = VQE_OK;
   if (!get_ell(h, a, &rc)) return 0;
   const bool cplx_amp = (mode & VQE_WS_COMPLEX) || !use_real();
+  if (!cplx_amp) get_sweep(a);  // the sweep queues, before any stream capture
   return ws_layout(a, cplx_amp, (mode & VQE_WS_GRAD) != 0).total;
 }
 

@@ -114,7 +114,10 @@ struct InstDesc {
 // Persistent batched evaluation (vqe_batch.cu): a device work queue of tasks,
 // each instance a chain of levels (see PTaskKind), run by one launch.
 constexpr int kPersistThreads = 256;  // == kStrWarps * 32, the string-driven H psi's block
-enum PTaskKind : int32_t { PT_INIT = 0, PT_FWD = 1, PT_GATHER = 2, PT_HPSI = 3, PT_SCATTER = 4, PT_DOT = 5, PT_ADJ = 6 };
+enum PTaskKind : int32_t {
+  PT_INIT = 0, PT_FWD = 1, PT_GATHER = 2, PT_HPSI = 3, PT_SCATTER = 4, PT_DOT = 5, PT_ADJ = 6,
+  PT_ADJS = 7  // adjoint step of a large gate: partials [lo, hi) of k_gate_adj's grid-strided layout
+};
 struct PTask {
   int32_t slot;   // persistent slot (instance) of the task
   int32_t kind;   // PTaskKind
@@ -154,6 +157,20 @@ cudaError_t batch_persistent_run(const PersistDev& p, int grid, size_t smem, con
                                  int64_t ld_grad, cudaStream_t stream);
 cudaError_t set_persist_smem_limit(size_t smem);
 cudaError_t persist_occupancy(size_t smem, int* blocks_per_sm);
+// memset of the counters and the persistent launch alone (the gate sweeps of a
+// large single instance; no dynamic shared memory, no finalising launch)
+cudaError_t persistent_sweep_run(const PersistDev& p, int grid, const double* theta, cudaStream_t stream);
+
+// Persistent gate sweeps of one large instance (stream_energy_grad with real
+// amplitudes): queues of INIT + FWD tasks and of ADJS tasks for an ansatz, with
+// device copies of its descriptor (ansatz fields only) and workspace offsets.
+struct SweepPlan {
+  InstDesc* d_desc = nullptr;
+  PSlot* d_slot = nullptr;
+  PTask* d_fwd = nullptr;
+  PTask* d_adj = nullptr;
+  int32_t n_fwd = 0, n_adj = 0, grid = 0;
+};
 cudaError_t set_str_smem_limit(size_t smem);
 
 // Shared-memory layout of the resident kernel (byte offsets), computed the same
@@ -233,6 +250,8 @@ struct StreamBuffers {
 
 // Host-side facts the streaming launchers need besides the device descriptor.
 struct StreamPlan {
+  const SweepPlan* sweep = nullptr;  // persistent gate sweeps (null: one launch per gate)
+  int64_t counters_off = 0;          // byte offset of the sweep queue's counters in the workspace
   const int64_t* pair_off_host;  // [M+1]
   const int32_t* d_nb_rows;      // device [M+1]: blocks of each gate's adjoint launch, then of H psi
   int n_elec, n_alpha;           // sector test (n_alpha < 0: number sector only)

@@ -755,10 +755,30 @@ cudaError_t launch_resident(const InstDesc* d_descs, const InstDesc* one, int n_
 }
 
 namespace {
+// The gate sweeps of one instance as one persistent launch over its task queue
+// (sp.sweep; real amplitudes): PSlot offsets are relative to b.psi, the start of
+// the workspace layout.
+cudaError_t sweep_launch(const StreamPlan& sp, const StreamBuffers& b, bool adjoint, const double* theta,
+                         cudaStream_t stream) {
+  PersistDev p;
+  p.desc = sp.sweep->d_desc;
+  p.slots = sp.sweep->d_slot;
+  p.tasks = adjoint ? sp.sweep->d_adj : sp.sweep->d_fwd;
+  p.n_tasks = adjoint ? sp.sweep->n_adj : sp.sweep->n_fwd;
+  p.n = 1;
+  p.ws = static_cast<char*>(b.psi);
+  p.counters = reinterpret_cast<int*>(static_cast<char*>(b.psi) + sp.counters_off);
+  p.budget_ns = 2000000000ll;
+  p.probe_task = -1;
+  p.pad = 0;
+  return persistent_sweep_run(p, sp.sweep->grid, theta, stream);
+}
+
 template <bool REAL>
 cudaError_t stream_forward(const InstDesc& d, const StreamPlan& sp, const StreamBuffers& b,
                            const double* theta, cudaStream_t stream) {
   typedef typename Amp<REAL>::T T;
+  if (REAL && sp.sweep) return sweep_launch(sp, b, false, theta, stream);
   T* psi = static_cast<T*>(b.psi);
   const int nt = kStreamThreads;
   if (d.M > 0) k_trig<<<(d.M + 255) / 256, 256, 0, stream>>>(theta, d.M, b.cs);
@@ -809,6 +829,12 @@ cudaError_t stream_adjoint(const InstDesc& d, const StreamPlan& sp, const Stream
   typedef typename Amp<REAL>::T T;
   T* phi = static_cast<T*>(b.psi);
   T* lam = static_cast<T*>(b.lam);
+  if (REAL && sp.sweep) {
+    const cudaError_t e = sweep_launch(sp, b, true, nullptr, stream);
+    if (e != cudaSuccess) return e;
+    if (d.M > 0) k_finalize<<<d.M, 32, 0, stream>>>(b.gpart, sp.d_nb_rows, d.M, 2.0, grad);
+    return cudaGetLastError();
+  }
   for (int m = d.M - 1; m >= 0; --m) {
     const int64_t p0 = sp.pair_off_host[m], p1 = sp.pair_off_host[m + 1];
     double* gp = b.gpart + int64_t(m) * kMaxPartials;

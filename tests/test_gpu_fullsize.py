@@ -55,6 +55,13 @@ def test_30_qubits_hf_energy_and_shift_rule_gradient():
     assert abs(e0 - _slater_condon(p)) <= 1e-10 + dropped
     e, g = vq.energy_grad(H, A, th, workspace=ws)
     g = g.cpu().numpy()
+    # one launch per gate instead of the persistent sweeps: the same bits
+    old = vq.set_flags(vq.VQE_FLAG_GATE_LAUNCHES)
+    try:
+        e2, g2 = vq.energy_grad(H, A, th, workspace=ws)
+    finally:
+        vq.set_flags(old)
+    assert float(e2) == float(e) and np.array_equal(g2.cpu().numpy(), g)
     w_ = (np.sqrt(2.0) - 1.0) / 2.0
     for k in (0, 255, 511):
         def e_at(shift):

@@ -509,3 +509,26 @@ def test_adjoint_gradient_matches_central_differences(cfg):
             tm[k] -= h
             fd[k] = (float(vq.energy(H, A, tp)) - float(vq.energy(H, A, tm))) / (2 * h)
         assert np.abs(fd - g).max() <= 1e-7, (cfg, float(np.abs(fd - g).max()))
+
+
+@pytest.mark.parametrize("n", [14, 20])
+def test_persistent_sweeps_equal_per_gate_launches(n):
+    """The streaming gate sweeps run as one persistent launch per sweep; with
+    VQE_FLAG_GATE_LAUNCHES they run as one launch per gate. Both give the same
+    bits: the same rotation per pair and the same gradient partial sums."""
+    ns, _ = synth.configs.config2_sizes()
+    p, exc, th = synth.config2_instance(int(np.nonzero(ns == n)[0][0]))
+    H = vq.Hamiltonian.from_problem(p)
+    A = vq.Ansatz(n, synth.hf_bitstring(p.n_elec), exc)
+    out = []
+    for flags in (vq.VQE_FLAG_FORCE_STREAMING, vq.VQE_FLAG_FORCE_STREAMING | vq.VQE_FLAG_GATE_LAUNCHES):
+        old = vq.set_flags(flags)
+        try:
+            e, g = vq.energy_grad(H, A, th)
+            st = vq.state(A, H, th)
+            out.append((float(e), g.clone(), st))
+        finally:
+            vq.set_flags(old)
+    assert out[0][0] == out[1][0]
+    assert torch.equal(out[0][1], out[1][1])
+    assert torch.equal(out[0][2], out[1][2])
