@@ -31,10 +31,10 @@
  * pair (vqe_workspace_bytes, vqe_work_counts, vqe_create_batch, or the first
  * compute call with that pair) builds the pair's connectivity or string tables,
  * synchronously, and the pair keeps them until the Hamiltonian is destroyed.
- * Likewise the first streaming evaluation of an ansatz (or vqe_workspace_bytes
- * with it) builds the task queues of its persistent gate sweeps. After that the
- * compute calls allocate nothing, so make those first calls before any stream
- * capture. Every compute call is asynchronous on the given
+ * Under VQE_FLAG_PERSISTENT_SWEEPS the first streaming evaluation of an ansatz
+ * (or vqe_workspace_bytes with it) also builds the task queues of its
+ * persistent gate sweeps. After that the compute calls allocate nothing, so
+ * make those first calls before any stream capture. Every compute call is asynchronous on the given
  * stream (a cudaStream_t; NULL is the legacy default stream) except where
  * noted.
  *
@@ -83,9 +83,10 @@ int vqe_version(void);
  *                            and every streaming kernel are FP64 either way);
  *   VQE_FLAG_NO_STRINGS      streaming H psi by connectivity rows (or a scan of
  *                            all groups) instead of alpha/beta strings;
- *   VQE_FLAG_GATE_LAUNCHES   streaming gate sweeps as one launch per gate
- *                            instead of one persistent launch per sweep (the
- *                            same bits either way).
+ *   VQE_FLAG_PERSISTENT_SWEEPS streaming gate sweeps of a single instance as
+ *                            one persistent launch per sweep (a task queue)
+ *                            instead of one launch per gate; the same bits, and
+ *                            slower on the GPUs measured (kept for comparison).
  * Returns the previous flags. Not thread-safe against concurrent compute calls.
  */
 enum {
@@ -94,7 +95,7 @@ enum {
   VQE_FLAG_NO_CLUSTER = 4,
   VQE_FLAG_FP64_SWEEPS = 8,
   VQE_FLAG_NO_STRINGS = 16,
-  VQE_FLAG_GATE_LAUNCHES = 32
+  VQE_FLAG_PERSISTENT_SWEEPS = 32
 };
 int vqe_set_flags(int flags);
 

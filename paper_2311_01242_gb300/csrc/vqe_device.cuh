@@ -480,8 +480,11 @@ __device__ __forceinline__ C simple_value(const SimpleCoef& c, const C* __restri
 // lane are in flight (8 with real amplitudes in the wide block form and in the
 // warp form, else 4: the best measured for each). Entries of one list have
 // distinct Ib, and __syncwarp separates the groups, so each output is updated
-// by one lane at a time, in group order (U does not change the order).
-template <bool REAL, int U>
+// by one lane at a time, in group order (U does not change the order). HOIST:
+// single-term groups take the source alpha string's part once per group
+// (SimpleCoef); measured faster in the wide block form and the warp form, and
+// slower in the staged block form, which therefore keeps group_coef.
+template <bool REAL, int U, bool HOIST = true>
 __device__ __forceinline__ void str_groups(const StrPlan& sp, int g0, int g1, int w_lo, int w_hi, uint32_t ka,
                                            const GroupRec* __restrict__ groups, const uint32_t* __restrict__ emask,
                                            const typename Amp<REAL>::C* __restrict__ vals, const uint32_t* kb_s,
@@ -515,7 +518,7 @@ __device__ __forceinline__ void str_groups(const StrPlan& sp, int g0, int g1, in
       }
     };
     SimpleCoef sc;
-    if (simple_coef(g, emask, ka, sc))  // the same for the whole warp
+    if (HOIST && simple_coef(g, emask, ka, sc))  // the same for the whole warp
       walk([&](uint32_t kbv) { return simple_value(sc, vals, kbv); });
     else
       walk([&](uint32_t kbv) { return group_coef<REAL>(g, emask, vals, ka | kbv); });
@@ -523,6 +526,109 @@ __device__ __forceinline__ void str_groups(const StrPlan& sp, int g0, int g1, in
     g = gn;
     e0 = e0n;
     e1 = e1n;
+  }
+}
+
+// Real amplitudes, software-pipelined form of str_groups: while group gi's list
+// is walked, group gi+1's coefficient state and table values are computed and
+// loaded, and group gi+2's record is loaded (StrPlan::bgx, no group record or
+// mask needed for single-term groups). A single-term group with at most two
+// beta pattern bits has at most four distinct table values; they are loaded
+// once per group and each list entry selects one by its beta bits, so the entry
+// needs no table load. Every entry gets the same coefficient as from
+// group_coef, and outputs are summed in the same order: the same bits. Used by
+// the wide block form and the warp form (the staged block form measured
+// faster with str_groups).
+struct HotCoef {
+  SimpleCoef sc;
+  double v0, v1, v2, v3;  // vals[base + b0 * o0 + b1 * o1] for beta bits (b0, b1)
+  int32_t mode;           // 0: general group (group_coef), 1: preloaded values, 2: one table load per entry
+};
+
+__device__ __forceinline__ HotCoef hot_prep(uint4 r, uint32_t ka, const double* __restrict__ vals) {
+  HotCoef h;
+  h.v0 = h.v1 = h.v2 = h.v3 = 0.0;
+  h.sc.qu = r.y;
+  h.sc.eb = r.w & 0xAAAAAAAAu;
+  if (!(r.z >> 31)) {
+    h.mode = 0;
+    h.sc.base = 0u;
+    return h;
+  }
+  uint32_t base = r.z & 0x7fffffffu;
+#pragma unroll
+  for (int t = 0; t < kMaxPatternBits; ++t) {
+    const uint32_t b = (r.x >> (8 * t)) & 255u;
+    if (b == 255u) break;
+    base += ((ka >> (b & 31u)) & 1u) << (b >> 5);
+  }
+  h.sc.base = base | (uint32_t(parity32(ka & r.w)) << 31);
+  if (((r.y >> 16) & 255u) != 0u) {
+    h.mode = 2;
+    return h;
+  }
+  h.mode = 1;
+  const uint32_t q0 = r.y & 255u, q1 = (r.y >> 8) & 255u;
+  const uint32_t o0 = q0 ? (1u << (q0 >> 5)) : 0u, o1 = q1 ? (1u << (q1 >> 5)) : 0u;
+  h.v0 = __ldg(vals + base);
+  if (o0) h.v1 = __ldg(vals + base + o0);
+  if (o1) h.v2 = __ldg(vals + base + o1);
+  if (o0 && o1) h.v3 = __ldg(vals + base + o0 + o1);
+  return h;
+}
+
+template <int U>
+__device__ __forceinline__ void str_groups_hot(const StrPlan& sp, int g0, int g1, int w_lo, int w_hi, uint32_t ka,
+                                               const GroupRec* __restrict__ groups,
+                                               const uint32_t* __restrict__ emask, const double* __restrict__ vals,
+                                               const uint32_t* kb_s, const double* psi_s, double* lam_s, int lane) {
+  typedef Amp<true> A;
+  if (g0 >= g1) return;
+  constexpr int S = kStrWarps + 1;
+  HotCoef h = hot_prep(__ldg(sp.bgx + g0), ka, vals);
+  int e0 = __ldg(sp.bsplit + int64_t(g0) * S + w_lo);
+  int e1 = __ldg(sp.bsplit + int64_t(g0) * S + w_hi);
+  uint4 rn = g0 + 1 < g1 ? __ldg(sp.bgx + g0 + 1) : make_uint4(0u, 0u, 0u, 0u);
+  for (int gi = g0; gi < g1; ++gi) {
+    const uint4 rnn = gi + 2 < g1 ? __ldg(sp.bgx + gi + 2) : rn;
+    int e0n = 0, e1n = 0;
+    HotCoef hn = h;
+    if (gi + 1 < g1) {
+      e0n = __ldg(sp.bsplit + int64_t(gi + 1) * S + w_lo);
+      e1n = __ldg(sp.bsplit + int64_t(gi + 1) * S + w_hi);
+      hn = hot_prep(rn, ka, vals);
+    }
+    auto walk = [&](auto&& cf) {
+      for (int e = e0 + lane; e < e1; e += U * 32) {
+        uint32_t ent[U];
+#pragma unroll
+        for (int u = 0; u < U; ++u) ent[u] = (e + 32 * u < e1) ? __ldg(sp.lists + e + 32 * u) : 0xFFFFFFFFu;
+#pragma unroll
+        for (int u = 0; u < U; ++u) {
+          if (ent[u] == 0xFFFFFFFFu) break;
+          const uint32_t ib = ent[u] & 0xFFFFu, jb = ent[u] >> 16;
+          A::mac(lam_s[ib], cf(kb_s[jb]), psi_s[jb]);
+        }
+      }
+    };
+    if (h.mode == 1) {
+      const uint32_t s0 = h.sc.qu & 31u, s1 = (h.sc.qu >> 8) & 31u;
+      walk([&](uint32_t kbv) {
+        const uint32_t b0 = (kbv >> s0) & 1u, b1 = (kbv >> s1) & 1u;  // qubit 0 is alpha: a missing bit reads 0
+        const double v = b1 ? (b0 ? h.v3 : h.v2) : (b0 ? h.v1 : h.v0);
+        return sflip(v, int(h.sc.base >> 31) ^ parity32(kbv & h.sc.eb));
+      });
+    } else if (h.mode == 2) {
+      walk([&](uint32_t kbv) { return simple_value(h.sc, vals, kbv); });
+    } else {
+      const GroupRec g = load_group(groups + __ldg(sp.bgrp + gi));
+      walk([&](uint32_t kbv) { return group_coef<true>(g, emask, vals, ka | kbv); });
+    }
+    __syncwarp();
+    h = hn;
+    e0 = e0n;
+    e1 = e1n;
+    rn = rnn;
   }
 }
 
@@ -568,7 +674,7 @@ __device__ __forceinline__ void hpsi_str_row(const StrPlan& sp, int ia, const Gr
           __syncthreads();  // outputs were last updated under the list path's thread mapping
           const uint32_t ka = __ldg(sp.ka + ja);
           SimpleCoef sc;
-          if (simple_coef(g, emask, ka, sc)) {
+          if (WIDE && simple_coef(g, emask, ka, sc)) {
             for (int j = tid; j < Db; j += bs) A::mac(lam_s[j], simple_value(sc, vals, kb_s[j]), ld_state<CG>(row + j));
           } else {
             for (int j = tid; j < Db; j += bs)
@@ -581,8 +687,12 @@ __device__ __forceinline__ void hpsi_str_row(const StrPlan& sp, int ia, const Gr
     __syncthreads();       // the previous source row is no longer read
     for (int j = tid; j < Db; j += bs) psi_s[j] = ld_state<CG>(row + j);
     __syncthreads();
-    str_groups<REAL, (WIDE && REAL) ? 8 : 4>(sp, __ldg(sp.boff + b), __ldg(sp.boff + b + 1), w, w + 1, __ldg(sp.ka + ja), groups, emask,
-                     vals, kb_s, psi_s, lam_s, lane);
+    if constexpr (REAL && WIDE)  // four entries in flight: measured best with the pipelined loop
+      str_groups_hot<4>(sp, __ldg(sp.boff + b), __ldg(sp.boff + b + 1), w, w + 1, __ldg(sp.ka + ja), groups, emask,
+                        vals, kb_s, psi_s, lam_s, lane);
+    else
+      str_groups<REAL, (WIDE && REAL) ? 8 : 4, WIDE>(sp, __ldg(sp.boff + b), __ldg(sp.boff + b + 1), w, w + 1,
+                                                     __ldg(sp.ka + ja), groups, emask, vals, kb_s, psi_s, lam_s, lane);
   }
   __syncthreads();
   T* out = lam_am + int64_t(ia) * Db;
@@ -637,8 +747,12 @@ __device__ __forceinline__ void hpsi_str_warps(const StrPlan& sp, int ia0, const
     __syncwarp();
     for (int j = lane; j < Db; j += 32) psi_s[j] = ld_state<CG>(row + j);
     __syncwarp();
-    str_groups<REAL, REAL ? 8 : 4>(sp, __ldg(sp.boff + b), __ldg(sp.boff + b + 1), 0, kStrWarps, __ldg(sp.ka + ja), groups, emask,
-                     vals, kb_s, psi_s, lam_s, lane);
+    if constexpr (REAL)
+      str_groups_hot<8>(sp, __ldg(sp.boff + b), __ldg(sp.boff + b + 1), 0, kStrWarps, __ldg(sp.ka + ja), groups,
+                        emask, vals, kb_s, psi_s, lam_s, lane);
+    else
+      str_groups<REAL, 4>(sp, __ldg(sp.boff + b), __ldg(sp.boff + b + 1), 0, kStrWarps, __ldg(sp.ka + ja), groups,
+                          emask, vals, kb_s, psi_s, lam_s, lane);
   }
   __syncwarp();
   T* out = lam_am + int64_t(ia) * Db;

@@ -645,6 +645,27 @@ int build_strings(vqe_hamiltonian_t h, vqe_ansatz_t a, vqe_hamiltonian_s::Ell* e
     bgrp.push_back(0);
     bsplit.assign(SW + 1, 0);
   }
+  // compact per-entry records of single-term groups (no source string needed)
+  std::vector<uint4> bgx(bgrp.size());
+  for (size_t i = 0; i < bgrp.size(); ++i) {
+    const GroupRec& g = h->groups[size_t(bgrp[i])];
+    const bool single = g.kind == 0 && g.eend == g.ebeg + 1;
+    uint32_t qa = 0xFFFFFFFFu, qb = 0u;
+    int na = 0, nb = 0;
+    for (int j = 0; j < g.ubits; ++j) {
+      const uint32_t pos = (g.upos >> (8 * j)) & 31u;
+      const uint32_t byte = pos | (uint32_t(j) << 5);
+      if (pos & 1u) {
+        qb |= byte << (8 * nb);
+        ++nb;
+      } else {
+        qa = (qa & ~(0xFFu << (8 * na))) | (byte << (8 * na));
+        ++na;
+      }
+    }
+    bgx[i] = make_uint4(qa, qb, uint32_t(g.vbeg) | (single ? 0x80000000u : 0u), single ? h->emask[size_t(g.ebeg)] : 0u);
+  }
+  if (bgx.empty()) bgx.push_back(make_uint4(0xFFFFFFFFu, 0u, 0u, 0u));
   vqe::StrPlan& P = e->str;
   P.Da = int32_t(Da);
   P.Db = int32_t(Db);
@@ -657,11 +678,13 @@ int build_strings(vqe_hamiltonian_t h, vqe_ansatz_t a, vqe_hamiltonian_s::Ell* e
   };
   uint32_t *d_ka, *d_kb, *d_lists, *d_perm;
   int32_t *d_ja, *d_boff, *d_bgrp, *d_bsplit;
+  uint4* d_bgx;
   std::vector<uint32_t> ka_v(ka), kb_v(kb);
   if ((rc = up(ka_v, &d_ka)) || (rc = up(kb_v, &d_kb)) || (rc = up(ja, &d_ja)) || (rc = up(boff, &d_boff)) ||
       (rc = up(bgrp, &d_bgrp)) || (rc = up(bsplit, &d_bsplit)) || (rc = up(flat, &d_lists)) ||
-      (rc = up(perm, &d_perm)))
+      (rc = up(perm, &d_perm)) || (rc = up(bgx, &d_bgx)))
     return rc;
+  P.bgx = d_bgx;
   P.ka = d_ka;
   P.kb = d_kb;
   P.ja = d_ja;
@@ -919,12 +942,13 @@ vqe::StreamBuffers buffers(void* ws, const WsLayout& L) {
   return s;
 }
 
-// Task queues of the persistent gate sweeps of ansatz a (real amplitudes): the
-// forward queue holds the HF init and each gate's rotation in 2,048-pair tasks,
-// the adjoint queue each gate's adjoint step in tasks of four partial sums laid
-// out as k_gate_adj's blocks (so the gradient has the same bits as with one
-// launch per gate). Built once per ansatz, on its first streaming use; null if
-// the device refuses (the caller then launches per gate).
+// Task queues of the persistent gate sweeps of ansatz a (real amplitudes; used
+// under VQE_FLAG_PERSISTENT_SWEEPS): the forward queue holds the HF init and
+// each gate's rotation in 2,048-pair tasks, the adjoint queue each gate's
+// adjoint step in tasks of four partial sums laid out as k_gate_adj's blocks
+// (so the gradient has the same bits as with one launch per gate). Built once
+// per ansatz, on its first use; null if the device refuses (the caller then
+// launches per gate).
 const vqe::SweepPlan* get_sweep(vqe_ansatz_t a) {
   std::lock_guard<std::mutex> lk(a->sweep_mu);
   if (a->sweep) return a->sweep->grid > 0 ? a->sweep.get() : nullptr;
@@ -991,7 +1015,7 @@ const vqe::SweepPlan* get_sweep(vqe_ansatz_t a) {
 
 vqe::StreamPlan plan(vqe_ansatz_t a, const vqe_hamiltonian_s::Ell* e) {
   vqe::StreamPlan p;
-  if (use_real() && !(g_flags & VQE_FLAG_GATE_LAUNCHES)) {
+  if (use_real() && (g_flags & VQE_FLAG_PERSISTENT_SWEEPS)) {
     p.sweep = get_sweep(a);
     p.counters_off = int64_t(ws_layout(a, false, false).ctr);
   }
@@ -1800,7 +1824,7 @@ size_t vqe_workspace_bytes(vqe_hamiltonian_t h, vqe_ansatz_t a, int mode) {
   int rc = VQE_OK;
   if (!get_ell(h, a, &rc)) return 0;
   const bool cplx_amp = (mode & VQE_WS_COMPLEX) || !use_real();
-  if (!cplx_amp) get_sweep(a);  // the sweep queues, before any stream capture
+  if (!cplx_amp && (g_flags & VQE_FLAG_PERSISTENT_SWEEPS)) get_sweep(a);  // before any stream capture
   return ws_layout(a, cplx_amp, (mode & VQE_WS_GRAD) != 0).total;
 }
 

@@ -69,6 +69,11 @@ struct StrPlan {
   const int32_t* bsplit;   // [entries * (kStrWarps + 1)] absolute list offsets
   const uint32_t* lists;   // concatenated beta lists
   const uint32_t* perm;    // [Da * Db] alpha-major index -> position in the sorted sector
+  // per bucket entry (bgrp order), the parts of a single-term group's coefficient
+  // that need no source string: {qa, qb, vbeg | single << 31, em}; qa / qb: per
+  // alpha / beta pattern bit t, byte t = qubit | (bit of u) << 5 (qa: 0xFF ends
+  // the list; qb: 0 ends it, beta qubits are odd); em: the term's Z mask
+  const uint4* bgx;
 };
 
 struct InstDesc {

@@ -30,6 +30,9 @@ __device__ __forceinline__ void prefetch_l2(const void* p) {
   asm volatile("prefetch.global.L2 [%0];" ::"l"(p));
 }
 
+// Loads in flight per thread when staging tables into shared memory.
+constexpr int kStageLoads = 8;
+
 __device__ __forceinline__ void sweep_barrier(int nthreads) {
   asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
 }
@@ -92,6 +95,18 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
   const int64_t row = d.inst;
   const double* th = theta + row * ld_theta;
 
+  // pull the tables H psi reads later into L2 while the staging and the forward
+  // sweep run
+  {
+    const char* ell_b = reinterpret_cast<const char*>(d.ellp);
+    const int64_t ell_bytes = int64_t(W) * D * 4;
+    for (int64_t o = int64_t(tid) * 128; o < ell_bytes; o += int64_t(bs) * 128) prefetch_l2(ell_b + o);
+    const char* val_b = REAL ? reinterpret_cast<const char*>(d.vals) : reinterpret_cast<const char*>(d.cvals);
+    const int64_t val_bytes = int64_t(d.S) * (REAL ? 8 : 16);
+    for (int64_t o = int64_t(tid) * 128; o < val_bytes; o += int64_t(bs) * 128) prefetch_l2(val_b + o);
+    const char* sec_b = reinterpret_cast<const char*>(d.sector);
+    for (int64_t o = int64_t(tid) * 128; o < int64_t(D) * 4; o += int64_t(bs) * 128) prefetch_l2(sec_b + o);
+  }
   // stage ansatz tables, clear the state
   for (int m = tid; m < M; m += bs) {
     double s, c;
@@ -107,9 +122,19 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
     gates[m] = gr;
   }
   for (int m = tid; m <= M; m += bs) poff[m] = int32_t(__ldg(d.pair_off + m));
-  for (int p = tid; p < P; p += bs) {
-    const uint2 e = __ldg(d.rpairs + p);
-    rp[p] = (e.x & 0x7fffu) | ((e.x >> 31) << 15) | (e.y << 16);
+  // pair list: kStageLoads loads in flight per thread
+  for (int p0 = tid; p0 < P; p0 += kStageLoads * bs) {
+    uint2 e[kStageLoads];
+#pragma unroll
+    for (int k = 0; k < kStageLoads; ++k) {
+      const int p = p0 + k * bs;
+      e[k] = p < P ? __ldg(d.rpairs + p) : make_uint2(0u, 0u);
+    }
+#pragma unroll
+    for (int k = 0; k < kStageLoads; ++k) {
+      const int p = p0 + k * bs;
+      if (p < P) rp[p] = (e[k].x & 0x7fffu) | ((e[k].x >> 31) << 15) | (e[k].y << 16);
+    }
   }
   if constexpr (REAL) {
     for (int r = tid; r < D; r += bs) pl[r] = make_double2(0.0, 0.0);
@@ -118,17 +143,6 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
       psi[r] = A::zero();
       lam[r] = A::zero();
     }
-  }
-  // pull the tables H psi reads later into L2 while the forward sweep runs
-  {
-    const char* ell_b = reinterpret_cast<const char*>(d.ellp);
-    const int64_t ell_bytes = int64_t(W) * D * 4;
-    for (int64_t o = int64_t(tid) * 128; o < ell_bytes; o += int64_t(bs) * 128) prefetch_l2(ell_b + o);
-    const char* val_b = REAL ? reinterpret_cast<const char*>(d.vals) : reinterpret_cast<const char*>(d.cvals);
-    const int64_t val_bytes = int64_t(d.S) * (REAL ? 8 : 16);
-    for (int64_t o = int64_t(tid) * 128; o < val_bytes; o += int64_t(bs) * 128) prefetch_l2(val_b + o);
-    const char* sec_b = reinterpret_cast<const char*>(d.sector);
-    for (int64_t o = int64_t(tid) * 128; o < int64_t(D) * 4; o += int64_t(bs) * 128) prefetch_l2(sec_b + o);
   }
   __syncthreads();
   if (tid == 0) {
@@ -231,18 +245,36 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
     GroupRec* sg = reinterpret_cast<GroupRec*>(smem + L.tab);
     uint32_t* se = reinterpret_cast<uint32_t*>(smem + L.tab + uint32_t(G) * 32u);
     C* sv = reinterpret_cast<C*>(smem + L.tab + uint32_t(G) * 32u + align_up(uint32_t(d.E) * 4u, 16u));
-    const int4* gsrc = reinterpret_cast<const int4*>(d.groups);
-    int4* gdst = reinterpret_cast<int4*>(sg);
-    for (int i = tid; i < 2 * G; i += bs) gdst[i] = __ldg(gsrc + i);
-    for (int i = tid; i < d.E; i += bs) se[i] = __ldg(d.emask + i);
-    if constexpr (FIX) {
-      // fixed-point tables: v * 2^(62 - eh), where 2^eh bounds the sum of |v|
-      // over every slot and so every row sum of |H|
-      const int eh = bound_exp(*d.hbound);
-      const double sc = pow2(62 - eh);
-      for (int i = tid; i < d.S; i += bs) sv[i] = llbits(__double2ll_rn(__ldg(d.vals + i) * sc));
-    } else {
-      for (int i = tid; i < d.S; i += bs) sv[i] = A::coef(d, i);
+    // the threads outside the sweep stage the tables while the sweep runs (its
+    // shared-memory regions are disjoint from these); with no such threads, all
+    // threads stage after the sweep
+    const int st = (sw < bs && M > 0) ? tid - sw : tid, sbs = (sw < bs && M > 0) ? bs - sw : bs;
+    if (st >= 0) {
+      const int4* gsrc = reinterpret_cast<const int4*>(d.groups);
+      int4* gdst = reinterpret_cast<int4*>(sg);
+      for (int i = st; i < 2 * G; i += sbs) gdst[i] = __ldg(gsrc + i);
+      for (int i = st; i < d.E; i += sbs) se[i] = __ldg(d.emask + i);
+      if constexpr (FIX) {
+        // fixed-point tables: v * 2^(62 - eh), where 2^eh bounds the sum of |v|
+        // over every slot and so every row sum of |H|
+        const int eh = bound_exp(*d.hbound);
+        const double sc = pow2(62 - eh);
+        for (int i0 = st; i0 < d.S; i0 += kStageLoads * sbs) {
+          double v[kStageLoads];
+#pragma unroll
+          for (int k = 0; k < kStageLoads; ++k) {
+            const int i = i0 + k * sbs;
+            v[k] = i < d.S ? __ldg(d.vals + i) : 0.0;
+          }
+#pragma unroll
+          for (int k = 0; k < kStageLoads; ++k) {
+            const int i = i0 + k * sbs;
+            if (i < d.S) sv[i] = llbits(__double2ll_rn(v[k] * sc));
+          }
+        }
+      } else {
+        for (int i = st; i < d.S; i += sbs) sv[i] = A::coef(d, i);
+      }
     }
     tg = sg;
     te = se;

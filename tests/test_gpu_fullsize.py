@@ -55,8 +55,8 @@ def test_30_qubits_hf_energy_and_shift_rule_gradient():
     assert abs(e0 - _slater_condon(p)) <= 1e-10 + dropped
     e, g = vq.energy_grad(H, A, th, workspace=ws)
     g = g.cpu().numpy()
-    # one launch per gate instead of the persistent sweeps: the same bits
-    old = vq.set_flags(vq.VQE_FLAG_GATE_LAUNCHES)
+    # persistent sweeps instead of one launch per gate: the same bits
+    old = vq.set_flags(vq.VQE_FLAG_PERSISTENT_SWEEPS)
     try:
         e2, g2 = vq.energy_grad(H, A, th, workspace=ws)
     finally:

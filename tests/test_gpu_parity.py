@@ -513,15 +513,15 @@ def test_adjoint_gradient_matches_central_differences(cfg):
 
 @pytest.mark.parametrize("n", [14, 20])
 def test_persistent_sweeps_equal_per_gate_launches(n):
-    """The streaming gate sweeps run as one persistent launch per sweep; with
-    VQE_FLAG_GATE_LAUNCHES they run as one launch per gate. Both give the same
-    bits: the same rotation per pair and the same gradient partial sums."""
+    """The streaming gate sweeps run as one launch per gate; with
+    VQE_FLAG_PERSISTENT_SWEEPS as one persistent launch per sweep. Both give the
+    same bits: the same rotation per pair and the same gradient partial sums."""
     ns, _ = synth.configs.config2_sizes()
     p, exc, th = synth.config2_instance(int(np.nonzero(ns == n)[0][0]))
     H = vq.Hamiltonian.from_problem(p)
     A = vq.Ansatz(n, synth.hf_bitstring(p.n_elec), exc)
     out = []
-    for flags in (vq.VQE_FLAG_FORCE_STREAMING, vq.VQE_FLAG_FORCE_STREAMING | vq.VQE_FLAG_GATE_LAUNCHES):
+    for flags in (vq.VQE_FLAG_FORCE_STREAMING, vq.VQE_FLAG_FORCE_STREAMING | vq.VQE_FLAG_PERSISTENT_SWEEPS):
         old = vq.set_flags(flags)
         try:
             e, g = vq.energy_grad(H, A, th)
