@@ -489,7 +489,7 @@ __device__ __forceinline__ void str_groups(const StrPlan& sp, int g0, int g1, in
                                            const GroupRec* __restrict__ groups, const uint32_t* __restrict__ emask,
                                            const typename Amp<REAL>::C* __restrict__ vals, const uint32_t* kb_s,
                                            const typename Amp<REAL>::T* psi_s, typename Amp<REAL>::T* lam_s,
-                                           int lane) {
+                                           int lane, uint32_t ob) {
   typedef Amp<REAL> A;
   if (g0 >= g1) return;
   GroupRec g = load_group(groups + __ldg(sp.bgrp + g0));
@@ -512,8 +512,10 @@ __device__ __forceinline__ void str_groups(const StrPlan& sp, int g0, int g1, in
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           if (ent[u] == 0xFFFFFFFFu) break;
-          const uint32_t ib = ent[u] & 0xFFFFu, jb = ent[u] >> 16;
-          A::mac(lam_s[ib], cf(kb_s[jb]), psi_s[jb]);
+          const uint32_t ib = ent[u] & 0x1FFFu, jb = (ent[u] >> 16) & 0x1FFFu;
+          const uint32_t kbv = kb_s[jb];
+          // the staged row carries (-1)^{|Jb & ob|}; undo it on the coefficient
+          A::mac(lam_s[ib], sflip(cf(kbv), parity32(kbv & ob)), psi_s[jb]);
         }
       }
     };
@@ -542,7 +544,8 @@ __device__ __forceinline__ void str_groups(const StrPlan& sp, int g0, int g1, in
 struct HotCoef {
   SimpleCoef sc;
   double v0, v1, v2, v3;  // vals[base + b0 * o0 + b1 * o1] for beta bits (b0, b1)
-  int32_t mode;           // 0: general group (group_coef), 1: preloaded values, 2: one table load per entry
+  int32_t mode;           // 0: general group (group_coef), 1: preloaded values, 2: one table load per entry,
+                          // 3: alpha-hop x beta-hop group (v0, v1 signed; the list entry selects and signs)
 };
 
 __device__ __forceinline__ HotCoef hot_prep(uint4 r, uint32_t ka, const double* __restrict__ vals) {
@@ -563,6 +566,17 @@ __device__ __forceinline__ HotCoef hot_prep(uint4 r, uint32_t ka, const double* 
     base += ((ka >> (b & 31u)) & 1u) << (b >> 5);
   }
   h.sc.base = base | (uint32_t(parity32(ka & r.w)) << 31);
+  if (r.y >> 31) {
+    // alpha-hop x beta-hop group: the two coefficients, for a source holding the
+    // lower or the higher beta hop qubit, with every sign not carried by the
+    // staged row or the list entry folded in
+    h.mode = 3;
+    const uint32_t o0 = 1u << ((r.y >> 5) & 7u), o1 = 1u << ((r.y >> 13) & 7u);
+    const int sa = int(h.sc.base >> 31);
+    h.v0 = sflip(__ldg(vals + base + o0), sa ^ int((r.y >> 29) & 1u));
+    h.v1 = sflip(__ldg(vals + base + o1), sa ^ int((r.y >> 30) & 1u));
+    return h;
+  }
   if (((r.y >> 16) & 255u) != 0u) {
     h.mode = 2;
     return h;
@@ -581,7 +595,8 @@ template <int U>
 __device__ __forceinline__ void str_groups_hot(const StrPlan& sp, int g0, int g1, int w_lo, int w_hi, uint32_t ka,
                                                const GroupRec* __restrict__ groups,
                                                const uint32_t* __restrict__ emask, const double* __restrict__ vals,
-                                               const uint32_t* kb_s, const double* psi_s, double* lam_s, int lane) {
+                                               const uint32_t* kb_s, const double* psi_s, double* lam_s, int lane,
+                                               uint32_t ob) {
   typedef Amp<true> A;
   if (g0 >= g1) return;
   constexpr int S = kStrWarps + 1;
@@ -598,6 +613,8 @@ __device__ __forceinline__ void str_groups_hot(const StrPlan& sp, int g0, int g1
       e1n = __ldg(sp.bsplit + int64_t(gi + 1) * S + w_hi);
       hn = hot_prep(rn, ka, vals);
     }
+    // walks this warp's list entries; cf(entry, beta string) gives the coefficient
+    // for the staged row (which carries (-1)^{|Jb & ob|})
     auto walk = [&](auto&& cf) {
       for (int e = e0 + lane; e < e1; e += U * 32) {
         uint32_t ent[U];
@@ -606,23 +623,33 @@ __device__ __forceinline__ void str_groups_hot(const StrPlan& sp, int g0, int g1
 #pragma unroll
         for (int u = 0; u < U; ++u) {
           if (ent[u] == 0xFFFFFFFFu) break;
-          const uint32_t ib = ent[u] & 0xFFFFu, jb = ent[u] >> 16;
-          A::mac(lam_s[ib], cf(kb_s[jb]), psi_s[jb]);
+          const uint32_t ib = ent[u] & 0x1FFFu, jb = (ent[u] >> 16) & 0x1FFFu;
+          A::mac(lam_s[ib], cf(ent[u], jb), psi_s[jb]);
         }
       }
     };
-    if (h.mode == 1) {
+    if (h.mode == 3) {
+      // no beta string needed: the entry's bit 13 picks the coefficient, bit 14 its sign
+      walk([&](uint32_t en, uint32_t) { return sflip((en >> 13) & 1u ? h.v1 : h.v0, int((en >> 14) & 1u)); });
+    } else if (h.mode == 1) {
       const uint32_t s0 = h.sc.qu & 31u, s1 = (h.sc.qu >> 8) & 31u;
-      walk([&](uint32_t kbv) {
+      walk([&](uint32_t, uint32_t jb) {
+        const uint32_t kbv = kb_s[jb];
         const uint32_t b0 = (kbv >> s0) & 1u, b1 = (kbv >> s1) & 1u;  // qubit 0 is alpha: a missing bit reads 0
         const double v = b1 ? (b0 ? h.v3 : h.v2) : (b0 ? h.v1 : h.v0);
-        return sflip(v, int(h.sc.base >> 31) ^ parity32(kbv & h.sc.eb));
+        return sflip(v, int(h.sc.base >> 31) ^ parity32(kbv & h.sc.eb) ^ parity32(kbv & ob));
       });
     } else if (h.mode == 2) {
-      walk([&](uint32_t kbv) { return simple_value(h.sc, vals, kbv); });
+      walk([&](uint32_t, uint32_t jb) {
+        const uint32_t kbv = kb_s[jb];
+        return sflip(simple_value(h.sc, vals, kbv), parity32(kbv & ob));
+      });
     } else {
       const GroupRec g = load_group(groups + __ldg(sp.bgrp + gi));
-      walk([&](uint32_t kbv) { return group_coef<true>(g, emask, vals, ka | kbv); });
+      walk([&](uint32_t, uint32_t jb) {
+        const uint32_t kbv = kb_s[jb];
+        return sflip(group_coef<true>(g, emask, vals, ka | kbv), parity32(kbv & ob));
+      });
     }
     __syncwarp();
     h = hn;
@@ -685,14 +712,17 @@ __device__ __forceinline__ void hpsi_str_row(const StrPlan& sp, int ia, const Gr
       }
     }
     __syncthreads();       // the previous source row is no longer read
-    for (int j = tid; j < Db; j += bs) psi_s[j] = ld_state<CG>(row + j);
+    // only the pipelined loop of the wide form uses a signed row (measured slower in the staged form)
+    const uint32_t ob = (REAL && WIDE) ? __ldg(sp.bob + b) : 0u;  // the same for the whole block
+    for (int j = tid; j < Db; j += bs) psi_s[j] = sflip(ld_state<CG>(row + j), parity32(kb_s[j] & ob));
     __syncthreads();
     if constexpr (REAL && WIDE)  // four entries in flight: measured best with the pipelined loop
       str_groups_hot<4>(sp, __ldg(sp.boff + b), __ldg(sp.boff + b + 1), w, w + 1, __ldg(sp.ka + ja), groups, emask,
-                        vals, kb_s, psi_s, lam_s, lane);
+                        vals, kb_s, psi_s, lam_s, lane, ob);
     else
       str_groups<REAL, (WIDE && REAL) ? 8 : 4, WIDE>(sp, __ldg(sp.boff + b), __ldg(sp.boff + b + 1), w, w + 1,
-                                                     __ldg(sp.ka + ja), groups, emask, vals, kb_s, psi_s, lam_s, lane);
+                                                     __ldg(sp.ka + ja), groups, emask, vals, kb_s, psi_s, lam_s, lane,
+                                                     ob);
   }
   __syncthreads();
   T* out = lam_am + int64_t(ia) * Db;
@@ -745,14 +775,15 @@ __device__ __forceinline__ void hpsi_str_warps(const StrPlan& sp, int ia0, const
       }
     }
     __syncwarp();
-    for (int j = lane; j < Db; j += 32) psi_s[j] = ld_state<CG>(row + j);
+    const uint32_t ob = __ldg(sp.bob + b);  // the same for the whole warp
+    for (int j = lane; j < Db; j += 32) psi_s[j] = sflip(ld_state<CG>(row + j), parity32(kb_s[j] & ob));
     __syncwarp();
     if constexpr (REAL)
       str_groups_hot<8>(sp, __ldg(sp.boff + b), __ldg(sp.boff + b + 1), 0, kStrWarps, __ldg(sp.ka + ja), groups,
-                        emask, vals, kb_s, psi_s, lam_s, lane);
+                        emask, vals, kb_s, psi_s, lam_s, lane, ob);
     else
       str_groups<REAL, 4>(sp, __ldg(sp.boff + b), __ldg(sp.boff + b + 1), 0, kStrWarps, __ldg(sp.ka + ja), groups,
-                          emask, vals, kb_s, psi_s, lam_s, lane);
+                          emask, vals, kb_s, psi_s, lam_s, lane, ob);
   }
   __syncwarp();
   T* out = lam_am + int64_t(ia) * Db;

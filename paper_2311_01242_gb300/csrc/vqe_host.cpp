@@ -549,7 +549,7 @@ int build_strings(vqe_hamiltonian_t h, vqe_ansatz_t a, vqe_hamiltonian_s::Ell* e
   const int64_t Da = int64_t(ka.size()), Db = int64_t(kb.size());
   // shared memory of a block (complex amplitudes: the larger of the two)
   const size_t smem = vqe::str_smem_bytes(int(std::min<int64_t>(Db, 65535)), 16);
-  if (Da * Db != int64_t(a->sector.size()) || Db > 65535 || smem > size_t(200) * 1024) return VQE_OK;  // not used
+  if (Da * Db != int64_t(a->sector.size()) || Db > 8191 || smem > size_t(200) * 1024) return VQE_OK;  // not used
   {
     static std::mutex mu;
     static size_t set_to = 0;
@@ -613,13 +613,24 @@ int build_strings(vqe_hamiltonian_t h, vqe_ansatz_t a, vqe_hamiltonian_s::Ell* e
   // beta pair lists in output order, with each warp's share of outputs
   const int SW = vqe::kStrWarps;
   const int64_t share = (Db + SW - 1) / SW;
+  // an entry is Ib | Jb << 16 (13 bits each); for a list whose beta mask is a
+  // single hop {q_lo < q_hi}, bit 13 says the source string holds q_hi (else q_lo)
+  // and bit 14 is the parity of the source's beta qubits strictly between them
   std::vector<std::vector<uint32_t>> lists(static_cast<size_t>(NL));
   parallel_for(NL, [&](int64_t lo, int64_t hi) {
-    for (int64_t l = lo; l < hi; ++l)
+    for (int64_t l = lo; l < hi; ++l) {
+      const uint32_t xb = lxb[size_t(l)];
+      const bool hop = pc32(xb) == 2;
+      const int q_lo = hop ? __builtin_ctz(xb) : 0, q_hi = hop ? 31 - __builtin_clz(xb) : 0;
+      const uint32_t between = hop ? (((1u << q_hi) - 1u) & ~((2u << q_lo) - 1u) & odd) : 0u;
       for (int64_t j = 0; j < Db; ++j) {
-        const uint32_t src = kb[size_t(j)] ^ lxb[size_t(l)];
-        if (pc32(src) == Nb) lists[size_t(l)].push_back(uint32_t(j) | (uint32_t(index_of(kb, src)) << 16));
+        const uint32_t src = kb[size_t(j)] ^ xb;
+        if (pc32(src) != Nb) continue;
+        uint32_t ent = uint32_t(j) | (uint32_t(index_of(kb, src)) << 16);
+        if (hop) ent |= ((src >> q_hi) & 1u) << 13 | uint32_t(pc32(src & between) & 1) << 14;
+        lists[size_t(l)].push_back(ent);
       }
+    }
   });
   std::vector<uint32_t> flat;
   std::vector<int32_t> split(static_cast<size_t>(NL) * (SW + 1));
@@ -629,7 +640,7 @@ int build_strings(vqe_hamiltonian_t h, vqe_ansatz_t a, vqe_hamiltonian_s::Ell* e
     for (int w = 0; w <= SW; ++w) {
       const uint32_t first = uint32_t(std::min<int64_t>(Db, int64_t(w) * share));
       const int64_t pos = std::lower_bound(L.begin(), L.end(), first,
-                                           [](uint32_t ent, uint32_t v) { return (ent & 0xFFFFu) < v; }) -
+                                           [](uint32_t ent, uint32_t v) { return (ent & 0x1FFFu) < v; }) -
                           L.begin();
       split[size_t(l) * (SW + 1) + w] = int32_t(base + pos);
     }
@@ -645,6 +656,18 @@ int build_strings(vqe_hamiltonian_t h, vqe_ansatz_t a, vqe_hamiltonian_s::Ell* e
     bgrp.push_back(0);
     bsplit.assign(SW + 1, 0);
   }
+  // per bucket: for a single alpha hop {p < q}, the beta qubits strictly between
+  // p and q; the bucket's staged source row is multiplied by (-1)^{|Jb & bob|}
+  auto between_odd = [&](uint32_t x2) -> uint32_t {
+    if (pc32(x2) != 2) return 0u;
+    const int lo_q = __builtin_ctz(x2), hi_q = 31 - __builtin_clz(x2);
+    return ((1u << hi_q) - 1u) & ~((2u << lo_q) - 1u) & odd;
+  };
+  std::vector<uint32_t> bob(size_t(std::max(NB, 1)), 0u);
+  for (int b = 0; b < NB; ++b) bob[size_t(b)] = between_odd(bxa[size_t(b)]);
+  std::vector<int32_t> bucket_of(bgrp.size(), 0);
+  for (int b = 0; b < NB; ++b)
+    for (int32_t i = boff[size_t(b)]; i < boff[size_t(b) + 1]; ++i) bucket_of[size_t(i)] = b;
   // compact per-entry records of single-term groups (no source string needed)
   std::vector<uint4> bgx(bgrp.size());
   for (size_t i = 0; i < bgrp.size(); ++i) {
@@ -663,6 +686,18 @@ int build_strings(vqe_hamiltonian_t h, vqe_ansatz_t a, vqe_hamiltonian_s::Ell* e
         ++na;
       }
     }
+    // an alpha-hop x beta-hop single-term group whose beta sign is the bucket's
+    // row sign times its list entries' sign, up to a term fixed by which hop
+    // qubit the source holds: flag (bit 31 of qb) and those two terms (bits 29, 30)
+    const uint32_t xb = g.x & odd;
+    if (single && na == 2 && nb == 2 && pc32(g.x & even) == 2 && pc32(xb) == 2) {
+      const uint32_t em = h->emask[size_t(g.ebeg)];
+      const uint32_t rest = (em & odd) ^ bob[size_t(bucket_of[i])] ^ between_odd(xb);
+      if ((rest & ~xb) == 0u) {
+        const int q_lo = __builtin_ctz(xb), q_hi = 31 - __builtin_clz(xb);
+        qb |= 0x80000000u | ((rest >> q_lo) & 1u) << 29 | ((rest >> q_hi) & 1u) << 30;
+      }
+    }
     bgx[i] = make_uint4(qa, qb, uint32_t(g.vbeg) | (single ? 0x80000000u : 0u), single ? h->emask[size_t(g.ebeg)] : 0u);
   }
   if (bgx.empty()) bgx.push_back(make_uint4(0xFFFFFFFFu, 0u, 0u, 0u));
@@ -679,12 +714,14 @@ int build_strings(vqe_hamiltonian_t h, vqe_ansatz_t a, vqe_hamiltonian_s::Ell* e
   uint32_t *d_ka, *d_kb, *d_lists, *d_perm;
   int32_t *d_ja, *d_boff, *d_bgrp, *d_bsplit;
   uint4* d_bgx;
+  uint32_t* d_bob;
   std::vector<uint32_t> ka_v(ka), kb_v(kb);
   if ((rc = up(ka_v, &d_ka)) || (rc = up(kb_v, &d_kb)) || (rc = up(ja, &d_ja)) || (rc = up(boff, &d_boff)) ||
       (rc = up(bgrp, &d_bgrp)) || (rc = up(bsplit, &d_bsplit)) || (rc = up(flat, &d_lists)) ||
-      (rc = up(perm, &d_perm)) || (rc = up(bgx, &d_bgx)))
+      (rc = up(perm, &d_perm)) || (rc = up(bgx, &d_bgx)) || (rc = up(bob, &d_bob)))
     return rc;
   P.bgx = d_bgx;
+  P.bob = d_bob;
   P.ka = d_ka;
   P.kb = d_kb;
   P.ja = d_ja;

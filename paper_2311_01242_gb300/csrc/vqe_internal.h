@@ -53,7 +53,9 @@ struct GateRec {
 // Da x Db matrix in alpha-major order. Groups are bucketed by their alpha mask;
 // a bucket maps output alpha string Ia to source alpha string ja[Ia * NB + b]
 // (-1: none). Each group's beta mask selects a list of (output, source) beta
-// string pairs (Ib | Jb << 16, increasing Ib); bsplit gives, per bucket entry,
+// string pairs (Ib | Jb << 16, 13 bits each, increasing Ib; for a beta mask of
+// one hop {q_lo < q_hi}, bit 13 = the source holds q_hi, bit 14 = parity of the
+// source's beta qubits strictly between q_lo and q_hi); bsplit gives, per bucket entry,
 // the entry range of its list for each of the kStrWarps warps (a fixed share of
 // the Ib range each).
 constexpr int kStrWarps = 8;
@@ -72,8 +74,14 @@ struct StrPlan {
   // per bucket entry (bgrp order), the parts of a single-term group's coefficient
   // that need no source string: {qa, qb, vbeg | single << 31, em}; qa / qb: per
   // alpha / beta pattern bit t, byte t = qubit | (bit of u) << 5 (qa: 0xFF ends
-  // the list; qb: 0 ends it, beta qubits are odd); em: the term's Z mask
+  // the list; qb: 0 ends it, beta qubits are odd); em: the term's Z mask. For an
+  // alpha-hop x beta-hop group whose sign splits as described at bob, qb bit 31
+  // is set and bits 29 / 30 hold the remaining sign bit when the source holds
+  // the lower / higher beta hop qubit.
   const uint4* bgx;
+  // per bucket: for a single alpha hop {p < q}, the beta qubits strictly between
+  // p and q (else 0); the staged source row is multiplied by (-1)^{|Jb & bob|}
+  const uint32_t* bob;
 };
 
 struct InstDesc {
