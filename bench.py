@@ -258,23 +258,13 @@ def throughput(units_per_rank, world, steps, max_seconds):
     return units_per_rank * world * steps / max_seconds
 
 
-def _timed(fn, steps, warmup):
-    """Per-step CUDA-event times (ms) of fn() after warmup calls, flushing L2 between steps."""
-    import torch
-    flush = torch.empty(512 * 1024 * 1024 // 4, dtype=torch.float32, device="cuda")
-    for _ in range(max(1, warmup)):
-        fn()
-    torch.cuda.synchronize()
-    out = []
-    for i in range(steps):
-        flush.fill_(float(i))
-        s, e = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-        s.record()
-        fn()
-        e.record()
-        torch.cuda.synchronize()
-        out.append(s.elapsed_time(e))
-    return out
+def _timed(fn, steps, warmup, clocks_out=None):
+    """Per-step CUDA-event times (ms) of fn() after warmup calls, flushing L2 between
+    steps; SM clocks sampled during the timed steps are appended to clocks_out."""
+    tm, clocks = _measure(fn, steps, warmup, 0)
+    if clocks_out is not None:
+        clocks_out.append(clocks)
+    return tm["per_step"]
 
 
 def run_large(args):
@@ -291,6 +281,7 @@ def run_large(args):
     torch.cuda.set_device(0)
     vq.load()
     steps, warmup = min(args.steps, 20), max(3, min(args.warmup, 5))
+    clk = []
     t0 = time.perf_counter()
     if args.workload in ("puccd11", "puccd24"):
         if args.workload == "puccd11":
@@ -315,7 +306,7 @@ def run_large(args):
         e_buf = torch.empty(len(hams), dtype=torch.float64, device="cuda")
         g_buf = torch.empty(len(hams), max(B.max_params, 1), dtype=torch.float64, device="cuda")
         t_create = time.perf_counter() - t0
-        ms = _timed(lambda: B.energy_grad(theta, e_buf, g_buf, ws), steps, warmup)
+        ms = _timed(lambda: B.energy_grad(theta, e_buf, g_buf, ws), steps, warmup, clk)
         flops = state_bytes = 0.0
         for h, a in zip(hams, ans):
             f, b = vq.work_estimate(h, a, True)
@@ -339,7 +330,7 @@ def run_large(args):
         e_buf = torch.empty(1, dtype=torch.float64, device="cuda")
         g_buf = torch.empty(len(exc), dtype=torch.float64, device="cuda")
         t_create = time.perf_counter() - t0
-        ms = _timed(lambda: vq.energy_grad(H, A, theta, workspace=ws, out=(e_buf, g_buf)), steps, warmup)
+        ms = _timed(lambda: vq.energy_grad(H, A, theta, workspace=ws, out=(e_buf, g_buf)), steps, warmup, clk)
         flops, state_bytes = vq.work_estimate(H, A, True)
         units, unit = 1, "evals/s"
         workload = ("30 qubits, 10 electrons, 512 UCCSD angles (9.0M sector amplitudes)" if nq == 30 else
@@ -358,7 +349,7 @@ def run_large(args):
         gb = vb.GraphBatch(B)
         gb(theta)
         t_create = time.perf_counter() - t0
-        ms = _timed(lambda: gb(), steps, warmup)
+        ms = _timed(lambda: gb(), steps, warmup, clk)
         flops = state_bytes = 0.0
         for h, a in zip(hams, ans):
             f, b = vq.work_estimate(h, a, True)
@@ -378,7 +369,7 @@ def run_large(args):
                          "frac": achieved_tf / FP64_PEAK_TFLOPS, "traffic": None,
                          "state_bytes_per_step": state_bytes,
                          "state_gbs": state_bytes / (ms_step / 1e3) / 1e9},
-            "gpu_launches_per_step": launches}
+            "gpu_launches_per_step": launches, "clocks": clk[0] if clk else None}
     print(json.dumps(line), flush=True)
 
 
@@ -451,8 +442,9 @@ def run_adapt(args):
     theta = torch.as_tensor(th).cuda()
     e_buf = torch.empty(1, dtype=torch.float64, device="cuda")
     g_buf = torch.empty(len(pool), dtype=torch.float64, device="cuda")
-    ms_pool = _timed(lambda: vq.pool_gradients(H, A, P, theta, workspace=ws, out=(e_buf, g_buf)), steps, warmup)
-    ms_e = _timed(lambda: vq.energy(H, A, theta, workspace=ws), steps, warmup)
+    clk = []
+    ms_pool = _timed(lambda: vq.pool_gradients(H, A, P, theta, workspace=ws, out=(e_buf, g_buf)), steps, warmup, clk)
+    ms_e = _timed(lambda: vq.energy(H, A, theta, workspace=ws), steps, warmup, clk)
     ms_step, ms_fwd_h = float(np.median(ms_pool)), float(np.median(ms_e))
     ms_screen = max(ms_step - ms_fwd_h, 1e-6)
     n_pairs = P.info()["n_pairs"]
@@ -470,7 +462,8 @@ def run_adapt(args):
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": pool_profile_traffic(n_pairs), "peak_source": src,
                          "kernel": "k_pool_grad + k_pool_finalize"},
-            "gpu_launches_per_step": 2 * len(exc) + 8}
+            "gpu_launches_per_step": 2 * len(exc) + 8, "clocks": clk[0] if clk else None,
+            "clocks_energy_only": clk[1] if len(clk) > 1 else None}
     print(json.dumps(line), flush=True)
 
 
@@ -639,7 +632,7 @@ def _measure(fn, steps, warmup, gpu_index):
     clocks = sampler.stop(t0, t1)
     per = [s.elapsed_time(e) for s, e in zip(starts, ends)]
     return ({"ms_per_step": sum(per) / steps, "ms_median": statistics.median(per), "ms_min": min(per),
-             "steps": steps, "warmup": warm}, clocks)
+             "steps": steps, "warmup": warm, "per_step": per}, clocks)
 
 
 def _e2e(call, steps, h2d, d2h, unit, units_per_call):
@@ -775,6 +768,7 @@ def entry_config3(args, gpu_index):
     g_buf = torch.empty(len(exc), dtype=torch.float64, device="cuda")
     tm, clocks = _measure(lambda: vq.energy_grad(H, A, theta, workspace=ws, out=(e_buf, g_buf)), steps, warmup,
                           gpu_index)
+    tm.pop("per_step")
     e_real = float(e_buf[0])
     flops, state_bytes = vq.work_estimate(H, A, True)
     counts = vq.work_counts(H, A)
@@ -798,6 +792,7 @@ def entry_config3(args, gpu_index):
         g_c = torch.empty(len(exc), dtype=torch.float64, device="cuda")
         tc, clocks_c = _measure(lambda: vq.energy_grad(H, A, theta, workspace=wsc, out=(e_c, g_c)), min(steps, 5),
                                 3, gpu_index)
+        tc.pop("per_step")
         d_e = abs(float(e_c[0]) - e_real)
         d_g = float((g_c - g_buf).abs().max())
         del wsc
@@ -865,6 +860,7 @@ def entry_config2(args, gpu_index):
     gb(theta_d)
     t_create = time.perf_counter() - t0
     tm, clocks = _measure(lambda: gb(), steps, warmup, gpu_index)
+    tm.pop("per_step")
     ms = tm["ms_per_step"]
     flops = state_bytes = 0.0
     n_entries = n_pairs = 0
@@ -916,6 +912,7 @@ def entry_config1_complex(B, theta, n_inst, M, steps, warmup, gpu_index):
         g = torch.empty(n_inst, M, dtype=torch.float64, device="cuda")
         ws = vq.alloc_workspace(B.workspace_bytes(True))
         tm, clocks = _measure(lambda: B.energy_grad(theta, e, g, ws), steps, warmup, gpu_index)
+        tm.pop("per_step")
     finally:
         vq.set_flags(old)
     return {"workload": WORKLOAD + " (complex128 amplitudes and coefficients)", "value": n_inst * 1e3 / tm["ms_per_step"],

@@ -518,6 +518,16 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
 }
 
 // ---------------------------------------------------------------- streaming kernels
+// Programmatic dependent launch of the per-gate kernels: each waits until the
+// previous kernel on the stream has completed and its writes are visible
+// (a no-op when launched without the attribute), then lets the next gate's
+// launch begin, so that launch overlaps this kernel's execution instead of
+// following its end.
+__device__ __forceinline__ void pdl_wait_and_release() {
+  asm volatile("griddepcontrol.wait;" ::: "memory");
+  asm volatile("griddepcontrol.launch_dependents;" ::: "memory");
+}
+
 __global__ void k_trig(const double* __restrict__ theta, int M, double2* __restrict__ cs) {
   const int m = blockIdx.x * blockDim.x + threadIdx.x;
   if (m < M) {
@@ -546,6 +556,7 @@ __global__ void k_gate_fwd(const uint2* __restrict__ rp, int64_t P, const double
                            typename Amp<REAL>::T* __restrict__ psi) {
   typedef Amp<REAL> A;
   typedef typename A::T T;
+  pdl_wait_and_release();
   const double2 c_s = __ldg(cs);
   for (int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; p < P;
        p += int64_t(gridDim.x) * blockDim.x) {
@@ -602,6 +613,7 @@ k_gate_adj(const uint2* __restrict__ rp, int64_t P, const double2* __restrict__ 
   typedef Amp<REAL> A;
   typedef typename A::T T;
   __shared__ double red[32];
+  pdl_wait_and_release();
   const double2 c_s = __ldg(cs);
   double acc = 0.0;
   for (int64_t p = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; p < P;
@@ -787,6 +799,22 @@ cudaError_t launch_resident(const InstDesc* d_descs, const InstDesc* one, int n_
 }
 
 namespace {
+// Launch with programmatic stream serialization allowed (see pdl_wait_and_release).
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kernel)(KArgs...), int grid, int block, cudaStream_t stream, Args... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned(grid));
+  cfg.blockDim = dim3(unsigned(block));
+  cfg.dynamicSmemBytes = 0;
+  cfg.stream = stream;
+  cudaLaunchAttribute attr[1];
+  attr[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  attr[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = attr;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kernel, args...);
+}
+
 // The gate sweeps of one instance as one persistent launch over its task queue
 // (sp.sweep; real amplitudes): PSlot offsets are relative to b.psi, the start of
 // the workspace layout.
@@ -817,8 +845,11 @@ cudaError_t stream_forward(const InstDesc& d, const StreamPlan& sp, const Stream
   k_init_sector<REAL><<<stream_grid(d.D), nt, 0, stream>>>(d.sector, d.D, d.hf, psi);
   for (int m = 0; m < d.M; ++m) {
     const int64_t p0 = sp.pair_off_host[m], p1 = sp.pair_off_host[m + 1];
-    if (p1 > p0)
-      k_gate_fwd<REAL><<<stream_grid(p1 - p0), nt, 0, stream>>>(d.rpairs + p0, p1 - p0, b.cs + m, psi);
+    if (p1 > p0) {
+      const cudaError_t e = launch_pdl(k_gate_fwd<REAL>, stream_grid(p1 - p0), nt, stream, d.rpairs + p0, p1 - p0,
+                                       static_cast<const double2*>(b.cs + m), psi);
+      if (e != cudaSuccess) return e;
+    }
   }
   return cudaGetLastError();
 }
@@ -870,8 +901,9 @@ cudaError_t stream_adjoint(const InstDesc& d, const StreamPlan& sp, const Stream
   for (int m = d.M - 1; m >= 0; --m) {
     const int64_t p0 = sp.pair_off_host[m], p1 = sp.pair_off_host[m + 1];
     double* gp = b.gpart + int64_t(m) * kMaxPartials;
-    k_gate_adj<REAL><<<stream_grid(p1 - p0), kStreamThreads, 0, stream>>>(d.rpairs + p0, p1 - p0, b.cs + m,
-                                                                          phi, lam, gp);
+    const cudaError_t e = launch_pdl(k_gate_adj<REAL>, stream_grid(p1 - p0), kStreamThreads, stream, d.rpairs + p0,
+                                     p1 - p0, static_cast<const double2*>(b.cs + m), phi, lam, gp);
+    if (e != cudaSuccess) return e;
   }
   if (d.M > 0) k_finalize<<<d.M, 32, 0, stream>>>(b.gpart, sp.d_nb_rows, d.M, 2.0, grad);
   return cudaGetLastError();
