@@ -312,6 +312,42 @@ __device__ __forceinline__ void ell_row(const uint32_t* ell, const uint16_t* ell
   }
 }
 
+// ell_row over packed entries together with their precomputed coefficients
+// (InstDesc::hmat, the same [W][D] layout): calls f(entry, coefficient).
+template <int U, class F>
+__device__ __forceinline__ void ell_row_mat(const uint32_t* ell, const long long* mat, int W, int64_t D, int64_t r,
+                                            int first, int step, F&& f) {
+  uint32_t cur[U];
+  long long cv[U];
+#pragma unroll
+  for (int u = 0; u < U; ++u) {
+    const int j = first + u * step;
+    cur[u] = j < W ? __ldg(ell + int64_t(j) * D + r) : kEllPad;
+    cv[u] = j < W ? __ldg(mat + int64_t(j) * D + r) : 0ll;
+  }
+  for (int j0 = first; j0 < W; j0 += U * step) {
+    const bool more = cur[U - 1] != kEllPad && j0 + U * step < W;
+    uint32_t nxt[U];
+    long long nv[U];
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      const int j = j0 + (U + u) * step;
+      const bool ok = more && j < W;
+      nxt[u] = ok ? __ldg(ell + int64_t(j) * D + r) : kEllPad;
+      nv[u] = ok ? __ldg(mat + int64_t(j) * D + r) : 0ll;
+    }
+#pragma unroll
+    for (int u = 0; u < U; ++u)
+      if (cur[u] != kEllPad) f(cur[u], cv[u]);
+    if (!more) break;
+#pragma unroll
+    for (int u = 0; u < U; ++u) {
+      cur[u] = nxt[u];
+      cv[u] = nv[u];
+    }
+  }
+}
+
 // group_coef on fixed-point tables (int64, one common scale): the same terms,
 // summed exactly in the integer pipe.
 __device__ __forceinline__ long long group_coef_int(const GroupRec& g, const uint32_t* emask, const long long* vals,

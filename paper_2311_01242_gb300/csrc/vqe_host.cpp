@@ -268,6 +268,7 @@ struct vqe_hamiltonian_s {
   int32_t* d_lin_term = nullptr;
   float* d_lin_w = nullptr;
   double* d_bound = nullptr;  // sum of |vals| over all slots (device)
+  long long* d_ivals = nullptr;  // fixed-point copy of the value tables (entry coefficient builds)
   GroupRec* d_groups = nullptr;
   uint32_t* d_emask = nullptr;
   double* d_vals = nullptr;
@@ -279,6 +280,9 @@ struct vqe_hamiltonian_s {
     uint16_t* d_ell16 = nullptr;      // device-built 16-bit table (large sectors)
     uint32_t* d_ellp = nullptr;       // packed entries for the resident kernel (small sectors)
     bool ellp_fast = false;           // d_ellp holds single-slot entries (flag bit 31)
+    long long* d_hmat = nullptr;      // fixed-point coefficient of each packed entry (this H's values)
+    uint32_t* d_hsec = nullptr;       // the sector's basis states, for rebuilding d_hmat
+    int64_t hD = 0;
     int64_t nnz = 0;                  // connected (output, group) pairs
     double extra_adds = 0;            // sum over nnz of (entries - 1)
     // spin sectors: alpha/beta string tables of the string-driven H psi
@@ -298,7 +302,10 @@ struct vqe_hamiltonian_s {
     dfree(d_lin_term);
     dfree(d_lin_w);
     dfree(d_bound);
+    dfree(d_ivals);
     for (auto& kv : ells) {
+      dfree(kv.second.d_hmat);
+      dfree(kv.second.d_hsec);
       ell_release(kv.second.d_ell);
       ell_release(kv.second.d_ellp);
       ell16_release(kv.second.d_ell16);
@@ -852,6 +859,29 @@ const vqe_hamiltonian_s::Ell* get_ell(vqe_hamiltonian_t h, vqe_ansatz_t a, int* 
           *err = rc;
           return nullptr;
         }
+        // small sectors: each entry's fixed-point coefficient for the resident
+        // kernel's H psi (rebuilt by vqe_set_coefs); without it the kernel
+        // computes them from the staged tables, with the same bits
+        const size_t mat_bytes = size_t(W) * size_t(D) * 8;
+        const size_t S = h->cvals.size();
+        if (D <= 8192 && mat_bytes <= (size_t(64) << 20) && S > 0) {
+          cudaError_t ce = cudaSuccess;
+          if (!h->d_ivals) ce = cudaMalloc(&h->d_ivals, S * sizeof(long long));
+          if (ce == cudaSuccess) ce = cudaMalloc(&e.d_hmat, mat_bytes);
+          if (ce == cudaSuccess && upload(a->sector, &e.d_hsec) != VQE_OK) ce = cudaErrorMemoryAllocation;
+          e.hD = D;
+          if (ce == cudaSuccess)
+            ce = vqe::build_hmat(e.d_ellp, W, D, e.d_hsec, h->d_groups, h->d_emask, h->d_vals, int64_t(S),
+                                 h->d_bound, e.ellp_fast ? 1 : 0, h->d_ivals, e.d_hmat, 0);
+          if (ce == cudaSuccess) ce = cudaDeviceSynchronize();
+          if (ce != cudaSuccess) {
+            cudaGetLastError();
+            dfree(e.d_hmat);
+            dfree(e.d_hsec);
+            e.d_hmat = nullptr;  // the table path serves instead
+            e.d_hsec = nullptr;
+          }
+        }
       }
     }
   }
@@ -896,6 +926,7 @@ InstDesc make_desc(vqe_hamiltonian_t h, vqe_ansatz_t a, const vqe_hamiltonian_s:
   d.str = e->use_str ? e->d_str : nullptr;
   d.ellp = e->d_ellp;
   d.ellp_fast = e->ellp_fast ? 1 : 0;
+  d.hmat = e->d_hmat;
   d.hbound = h->d_bound;
   d.gates = a->d_gates;
   d.pair_off = a->d_pair_off;
@@ -1590,6 +1621,15 @@ int vqe_set_coefs(vqe_hamiltonian_t h, const double* coefs_dev, vqe_stream_t str
                                    h->d_cvals, static_cast<cudaStream_t>(stream));
   if (ce == cudaSuccess) ce = vqe::abs_sum(h->d_vals, n_slots, h->d_bound, static_cast<cudaStream_t>(stream));
   if (ce != cudaSuccess) return cuda_fail(ce, "coefficient refold");
+  // the resident kernel's precomputed entry coefficients follow the new values
+  std::lock_guard<std::mutex> lock(h->mu);
+  for (auto& kv : h->ells) {
+    vqe_hamiltonian_s::Ell& e = kv.second;
+    if (!e.d_hmat) continue;
+    ce = vqe::build_hmat(e.d_ellp, e.W, e.hD, e.d_hsec, h->d_groups, h->d_emask, h->d_vals, n_slots,
+                         h->d_bound, e.ellp_fast ? 1 : 0, h->d_ivals, e.d_hmat, static_cast<cudaStream_t>(stream));
+    if (ce != cudaSuccess) return cuda_fail(ce, "entry coefficient rebuild");
+  }
   return VQE_OK;
 }
 

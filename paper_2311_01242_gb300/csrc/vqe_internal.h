@@ -107,6 +107,10 @@ struct InstDesc {
   // excitations of Jordan-Wigner chemistry) is instead
   // rank(src) | s << 15 | slot << 16 | 1 << 31 (slot < 32768).
   const uint32_t* ellp;
+  // resident kernel, same shape as ellp: each entry's coefficient f_g(src) in the
+  // fixed-point scale of the staged tables (v * 2^(62 - eh), 2^eh bounding hbound),
+  // summed exactly as group_coef_int does; null when not built
+  const long long* hmat;
   const double* hbound;      // device: sum of |vals| (bounds every row sum of |H|)
   // Hamiltonian
   int32_t G, W;              // groups, connectivity slots per output
@@ -292,6 +296,13 @@ cudaError_t stream_apply_h(const InstDesc& d, const StreamPlan& sp, const Stream
 // lambda = H psi with real amplitudes compressed to the sector (b.psi in, b.lam out).
 cudaError_t stream_apply_h_real(const InstDesc& d, const StreamPlan& sp, const StreamBuffers& b, double* energy,
                                 cudaStream_t stream);
+
+// The fixed-point coefficient of every packed connectivity entry (InstDesc::hmat):
+// ivals (S int64) receives the scaled table values first. Asynchronous on stream,
+// after the values and hbound are final.
+cudaError_t build_hmat(const uint32_t* ellp, int W, int64_t D, const uint32_t* sector, const GroupRec* groups,
+                       const uint32_t* emask, const double* vals, int64_t S, const double* hbound, int fast,
+                       long long* ivals, long long* hmat, cudaStream_t stream);
 
 // Device-built connectivity table (16-bit group indices) for large sectors:
 // len[r] = groups connected to output r; then rows filled in `order`.

@@ -97,6 +97,7 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
 
   // pull the tables H psi reads later into L2 while the staging and the forward
   // sweep run
+  const bool mat_h = FIX && d.hmat != nullptr;
   {
     const char* ell_b = reinterpret_cast<const char*>(d.ellp);
     const int64_t ell_bytes = int64_t(W) * D * 4;
@@ -106,6 +107,10 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
     for (int64_t o = int64_t(tid) * 128; o < val_bytes; o += int64_t(bs) * 128) prefetch_l2(val_b + o);
     const char* sec_b = reinterpret_cast<const char*>(d.sector);
     for (int64_t o = int64_t(tid) * 128; o < int64_t(D) * 4; o += int64_t(bs) * 128) prefetch_l2(sec_b + o);
+    if (mat_h) {
+      const char* mat_b = reinterpret_cast<const char*>(d.hmat);
+      for (int64_t o = int64_t(tid) * 128; o < ell_bytes * 2; o += int64_t(bs) * 128) prefetch_l2(mat_b + o);
+    }
   }
   // stage ansatz tables, clear the state
   for (int m = tid; m < M; m += bs) {
@@ -241,7 +246,7 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
   const uint32_t* te = d.emask;
   const C* tv;
   if constexpr (REAL) tv = d.vals; else tv = d.cvals;
-  if (stage) {
+  if (stage && !mat_h) {
     GroupRec* sg = reinterpret_cast<GroupRec*>(smem + L.tab);
     uint32_t* se = reinterpret_cast<uint32_t*>(smem + L.tab + uint32_t(G) * 32u);
     C* sv = reinterpret_cast<C*>(smem + L.tab + uint32_t(G) * 32u + align_up(uint32_t(d.E) * 4u, 16u));
@@ -283,7 +288,7 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
   __syncthreads();
   // fixed-point H psi: staged integer tables times psi in Q1.62 (needs the
   // staged tables; otherwise psi goes to FP64 for the FP64 H psi)
-  const bool int_h = FIX && stage;
+  const bool int_h = FIX && (stage || mat_h);  // precomputed entry coefficients need no tables
   const int eh = int_h ? bound_exp(*d.hbound) : 0;
   if (FIX && !int_h) {
     for (int r = tid; r < D; r += bs) pl[r].x = __ll2double_rn(dbits(pl[r].x)) * 0x1p-62;
@@ -311,7 +316,11 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
       if (int_h) {
         // lambda in units of 2^(eh - 60): the high word of (table value) x (psi)
         long long acc = 0;
-        if (live) {
+        if (live && mat_h) {
+          ell_row_mat<kEllChunk>(d.ellp, d.hmat, W, D, r, half, TPR, [&](uint32_t e, long long f) {
+            acc += __mul64hi(f, dbits(pl[e & 0x7fffu].x));
+          });
+        } else if (live) {
           const long long* tvi = reinterpret_cast<const long long*>(tv);
           ell_row(d.ellp, nullptr, W, D, r, half, TPR, [&](uint32_t e) {
             long long f;
@@ -741,6 +750,37 @@ __global__ void k_ell_fill(const uint32_t* __restrict__ sector, int64_t D, const
   }
 }
 
+// ---------------------------------------------------------------- fixed-point entry coefficients
+// The staged tables of the resident kernel, v * 2^(62 - eh), and from them every
+// packed entry's coefficient exactly as the kernel's H psi computes it.
+__global__ void k_int_vals(const double* __restrict__ vals, int64_t S, const double* __restrict__ hbound,
+                           long long* __restrict__ ivals) {
+  const int eh = bound_exp(*hbound);
+  const double sc = pow2(62 - eh);
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < S; i += int64_t(gridDim.x) * blockDim.x)
+    ivals[i] = __double2ll_rn(__ldg(vals + i) * sc);
+}
+
+__global__ void k_build_hmat(const uint32_t* __restrict__ ellp, int64_t n, int64_t D,
+                             const uint32_t* __restrict__ sector, const GroupRec* __restrict__ groups,
+                             const uint32_t* __restrict__ emask, const long long* __restrict__ ivals, int fast,
+                             long long* __restrict__ hmat) {
+  for (int64_t i = blockIdx.x * int64_t(blockDim.x) + threadIdx.x; i < n; i += int64_t(gridDim.x) * blockDim.x) {
+    const uint32_t e = __ldg(ellp + i);
+    long long f = 0;
+    if (e != kEllPad) {
+      if (fast && (e >> 31)) {
+        f = neg_if(__ldg(ivals + ((e >> 16) & 0x7fffu)), int((e >> 15) & 1u));
+      } else {
+        const uint32_t k = __ldg(sector + i % D);
+        const GroupRec g = load_group(groups + (e >> 19));
+        f = group_coef_int(g, emask, ivals, k ^ g.x, (e >> 15) & 15u);
+      }
+    }
+    hmat[i] = f;
+  }
+}
+
 // ---------------------------------------------------------------- launchers
 cudaError_t set_str_smem_limit(size_t smem) {
   const int b = int(smem);
@@ -954,6 +994,15 @@ cudaError_t stream_apply_h(const InstDesc& d, const StreamPlan& sp, const Stream
 cudaError_t stream_apply_h_real(const InstDesc& d, const StreamPlan& sp, const StreamBuffers& b, double* energy,
                                 cudaStream_t stream) {
   return stream_hpsi<true>(d, sp, b, energy, stream);
+}
+
+cudaError_t build_hmat(const uint32_t* ellp, int W, int64_t D, const uint32_t* sector, const GroupRec* groups,
+                       const uint32_t* emask, const double* vals, int64_t S, const double* hbound, int fast,
+                       long long* ivals, long long* hmat, cudaStream_t stream) {
+  if (S > 0) k_int_vals<<<stream_grid(S), kStreamThreads, 0, stream>>>(vals, S, hbound, ivals);
+  const int64_t n = int64_t(W) * D;
+  if (n > 0) k_build_hmat<<<stream_grid(n), kStreamThreads, 0, stream>>>(ellp, n, D, sector, groups, emask, ivals, fast, hmat);
+  return cudaGetLastError();
 }
 
 cudaError_t ell_device_count(const uint32_t* sector, int64_t D, const GroupRec* groups, int G, const int32_t* order,
