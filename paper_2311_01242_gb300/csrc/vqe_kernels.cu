@@ -96,21 +96,21 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
   const double* th = theta + row * ld_theta;
 
   // pull the tables H psi reads later into L2 while the staging and the forward
-  // sweep run
+  // sweep run (the precomputed entry coefficients, when used, are pulled in by
+  // the warps outside the sweep once it has started, so that they do not
+  // compete with the staging)
   const bool mat_h = FIX && d.hmat != nullptr;
   {
     const char* ell_b = reinterpret_cast<const char*>(d.ellp);
     const int64_t ell_bytes = int64_t(W) * D * 4;
     for (int64_t o = int64_t(tid) * 128; o < ell_bytes; o += int64_t(bs) * 128) prefetch_l2(ell_b + o);
-    const char* val_b = REAL ? reinterpret_cast<const char*>(d.vals) : reinterpret_cast<const char*>(d.cvals);
-    const int64_t val_bytes = int64_t(d.S) * (REAL ? 8 : 16);
-    for (int64_t o = int64_t(tid) * 128; o < val_bytes; o += int64_t(bs) * 128) prefetch_l2(val_b + o);
+    if (!mat_h) {
+      const char* val_b = REAL ? reinterpret_cast<const char*>(d.vals) : reinterpret_cast<const char*>(d.cvals);
+      const int64_t val_bytes = int64_t(d.S) * (REAL ? 8 : 16);
+      for (int64_t o = int64_t(tid) * 128; o < val_bytes; o += int64_t(bs) * 128) prefetch_l2(val_b + o);
+    }
     const char* sec_b = reinterpret_cast<const char*>(d.sector);
     for (int64_t o = int64_t(tid) * 128; o < int64_t(D) * 4; o += int64_t(bs) * 128) prefetch_l2(sec_b + o);
-    if (mat_h) {
-      const char* mat_b = reinterpret_cast<const char*>(d.hmat);
-      for (int64_t o = int64_t(tid) * 128; o < ell_bytes * 2; o += int64_t(bs) * 128) prefetch_l2(mat_b + o);
-    }
   }
   // stage ansatz tables, clear the state
   for (int m = tid; m < M; m += bs) {
@@ -246,7 +246,13 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
   const uint32_t* te = d.emask;
   const C* tv;
   if constexpr (REAL) tv = d.vals; else tv = d.cvals;
-  if (stage && !mat_h) {
+  if (mat_h) {
+    const int st = (sw < bs && M > 0) ? tid - sw : tid, sbs = (sw < bs && M > 0) ? bs - sw : bs;
+    const char* mat_b = reinterpret_cast<const char*>(d.hmat);
+    const int64_t mat_bytes = int64_t(W) * D * 8;
+    if (st >= 0)
+      for (int64_t o = int64_t(st) * 128; o < mat_bytes; o += int64_t(sbs) * 128) prefetch_l2(mat_b + o);
+  } else if (stage) {
     GroupRec* sg = reinterpret_cast<GroupRec*>(smem + L.tab);
     uint32_t* se = reinterpret_cast<uint32_t*>(smem + L.tab + uint32_t(G) * 32u);
     C* sv = reinterpret_cast<C*>(smem + L.tab + uint32_t(G) * 32u + align_up(uint32_t(d.E) * 4u, 16u));
