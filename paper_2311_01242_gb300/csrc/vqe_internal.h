@@ -223,7 +223,9 @@ __host__ __device__ inline ResidentLayout resident_layout(int n, int M, int P, i
   ResidentLayout L;
   L.psi = 0;
   L.lam = real ? 0u : uint32_t(D) * 16u;
-  uint32_t o = (real ? 1u : 2u) * uint32_t(D) * 16u;
+  // real amplitudes: {psi, lambda} rows plus one scratch row (index D) that the
+  // sweep lanes past a gate's end read and write
+  uint32_t o = real ? (uint32_t(D) + 1u) * 16u : 2u * uint32_t(D) * 16u;
   L.cs = align_up(o, 16u);
   o = L.cs + uint32_t(M) * 16u;
   L.gates = align_up(o, 16u);
@@ -238,7 +240,7 @@ __host__ __device__ inline ResidentLayout resident_layout(int n, int M, int P, i
   // holding the forward sweep's output and later the gradient contribution; with
   // complex amplitudes one gradient contribution per pair
   L.gbuf = align_up(o, 16u);
-  o = L.gbuf + uint32_t(P) * (real ? 16u : 8u);
+  o = L.gbuf + (real ? (uint32_t(P) + 1u) * 16u : uint32_t(P) * 8u);  // real: two scratch slots at 2P
   L.tab = align_up(o, 16u);
   o = L.tab + (stage ? staged_table_bytes(G, E, S, real) : 0u);
   L.red = align_up(o, 16u);

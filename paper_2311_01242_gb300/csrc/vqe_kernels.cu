@@ -37,6 +37,17 @@ __device__ __forceinline__ void sweep_barrier(int nthreads) {
   asm volatile("bar.sync 1, %0;" ::"r"(nthreads) : "memory");
 }
 
+// A gate as the sweeps read it from shared memory: its pair range and the
+// signs of cos and sin (bit 0, bit 1); cos and sin themselves sit in cs[m].
+struct SweepRec {
+  int32_t p0, cnt, unused, signs;
+};
+
+// The lane's pair entry at position q of a gate; past the gate's end, `pad`.
+__device__ __forceinline__ uint32_t entry_or(const uint32_t* rp, const SweepRec& g, int q, uint32_t pad) {
+  return q < g.cnt ? rp[g.p0 + q] : pad;
+}
+
 // One CTA evaluates one instance with its state in shared memory, compressed to
 // the sector (entry r is the amplitude of sector[r]): HF init, forward sweep,
 // H psi with the energy, and the reverse sweep with per-pair gradient
@@ -87,7 +98,7 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
   T* lam = reinterpret_cast<T*>(smem + L.lam);
   double2* pl = reinterpret_cast<double2*>(smem + L.psi);  // real: pl[r] = {psi_r, lambda_r}
   double2* cs = reinterpret_cast<double2*>(smem + L.cs);
-  GateRec* gates = reinterpret_cast<GateRec*>(smem + L.gates);
+  SweepRec* gates = reinterpret_cast<SweepRec*>(smem + L.gates);
   int32_t* poff = reinterpret_cast<int32_t*>(smem + L.poff);
   uint32_t* rp = reinterpret_cast<uint32_t*>(smem + L.pairs);
   double* gbuf = reinterpret_cast<double*>(smem + L.gbuf);
@@ -116,11 +127,16 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
   for (int m = tid; m < M; m += bs) {
     double s, c;
     sincos(th[m], &s, &c);
-    GateRec gr = load_gate(d.gates + m);
+    const int64_t pa = __ldg(d.pair_off + m), pb = __ldg(d.pair_off + m + 1);
+    SweepRec gr;
+    gr.p0 = int32_t(pa);
+    gr.cnt = int32_t(pb - pa);
+    gr.unused = 0;
+    gr.signs = 0;
     if constexpr (FIX) {
-      // magnitudes in Q0.64 (bit patterns kept in the double2 slot), signs in pad
+      // magnitudes in Q0.64 (bit patterns kept in the double2 slot), signs apart
       cs[m] = make_double2(llbits(static_cast<long long>(fix_mag(c))), llbits(static_cast<long long>(fix_mag(s))));
-      gr.pad = (c < 0.0 ? 1 : 0) | (s < 0.0 ? 2 : 0);
+      gr.signs = (c < 0.0 ? 1 : 0) | (s < 0.0 ? 2 : 0);
     } else {
       cs[m] = make_double2(c, s);
     }
@@ -142,7 +158,7 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
     }
   }
   if constexpr (REAL) {
-    for (int r = tid; r < D; r += bs) pl[r] = make_double2(0.0, 0.0);
+    for (int r = tid; r <= D; r += bs) pl[r] = make_double2(0.0, 0.0);
   } else {
     for (int r = tid; r < D; r += bs) {
       psi[r] = A::zero();
@@ -169,76 +185,56 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
   const int pstride = REAL ? (sw >> 1) : sw;
   const int spos = REAL ? (((tid & 31) >> 1) * swarps + (tid >> 5)) : ((tid & 31) * swarps + (tid >> 5));
 
-  // a2: forward sweep. The next gate's record, cos/sin and first pair are
-  // loaded before the current gate runs, off the barrier-to-barrier path.
+  // a2: forward sweep. A gate's record and cos/sin are loaded at its start (they
+  // are first needed after the amplitude loads), the lane's first pair entry one
+  // gate ahead. Lanes past a gate's end (real amplitudes) get a scratch entry:
+  // state row D and slot 2P + role, so every lane loads and stores without a
+  // predicate and the gate body is straight-line code; later slices of a gate
+  // with more pairs than lanes run in a loop.
+  const uint32_t pad_e = REAL ? (uint32_t(D) | (uint32_t(D) << 16)) : 0u;
+  const int scratch = 2 * P + role;
   if (tid < sw && M > 0) {
-    GateRec gr = gates[0];
-    int p0 = poff[0], cnt = poff[1] - p0;
-    double2 c_s = cs[0];
-    uint32_t ef = (spos < cnt) ? rp[p0 + spos] : 0u;
+    uint32_t ea = entry_or(rp, gates[0], spos, pad_e);
     for (int m = 0; m < M; ++m) {
-      GateRec grn = gr;
-      int p0n = 0, cntn = 0;
-      double2 c_sn = c_s;
-      uint32_t efn = 0u;
-      if (m + 1 < M) {
-        grn = gates[m + 1];
-        p0n = poff[m + 1];
-        cntn = poff[m + 2] - p0n;
-        c_sn = cs[m + 1];
-        if (spos < cntn) efn = rp[p0n + spos];
-      }
+      const SweepRec g0 = gates[m];
+      const double2 c0 = cs[m];
+      const uint32_t ean = entry_or(rp, gates[min(m + 1, M - 1)], spos, pad_e);
       if constexpr (REAL) {
         // two lanes per pair: role 0 writes c a - s b at ra, role 1 writes c b + s a
-        // at rb; both lanes read before either writes (warp-uniform trip count,
-        // lanes past the gate's end read entry 0 and store nothing)
-        for (int q0 = 0; q0 < cnt; q0 += pstride) {
-          const int q = q0 + spos;
-          const bool act = q < cnt;
-          const uint32_t e = (q0 == 0) ? ef : rp[p0 + min(q, cnt - 1)];
+        // at rb; both lanes read before either writes
+        auto slice = [&](uint32_t e, int q) {
           const uint32_t ra = e & 0x7fffu, rb = e >> 16;
-          const int sgn = int((e >> 15) & 1u);
           const uint32_t kd = role ? rb : ra, ko = role ? ra : rb;
-          const int slot = 2 * (p0 + q) + role;
+          const int sg = int((e >> 15) & 1u) ^ role ^ 1;
+          const double self = pl[kd].x, other = pl[ko].x;
+          __syncwarp();
+          double out;
           if constexpr (FIX) {
-            const long long self = dbits(pl[kd].x), other = dbits(pl[ko].x);
-            const int sneg = sgn ^ role ^ 1 ^ ((gr.pad >> 1) & 1);
-            __syncwarp();
-            const long long out = neg_if(mulhi_su(self, static_cast<unsigned long long>(dbits(c_s.x))), gr.pad & 1) +
-                                  neg_if(mulhi_su(other, static_cast<unsigned long long>(dbits(c_s.y))), sneg);
-            if (act) {
-              pl[kd].x = llbits(out);
-              gbuf[slot] = llbits(out);
-            }
+            out = llbits(neg_if(mulhi_su(dbits(self), static_cast<unsigned long long>(dbits(c0.x))), g0.signs & 1) +
+                         neg_if(mulhi_su(dbits(other), static_cast<unsigned long long>(dbits(c0.y))),
+                                sg ^ ((g0.signs >> 1) & 1)));
           } else {
-            const double self = pl[kd].x, other = pl[ko].x;
-            const double coef = sflip(c_s.y, sgn ^ role ^ 1);
-            __syncwarp();
-            const double out = fma(coef, other, c_s.x * self);
-            if (act) {
-              pl[kd].x = out;
-              gbuf[slot] = out;
-            }
+            out = fma(sflip(c0.y, sg), other, c0.x * self);
           }
-        }
+          pl[kd].x = out;
+          gbuf[q < g0.cnt ? 2 * (g0.p0 + q) + role : scratch] = out;
+        };
+        slice(ea, spos);
+        for (int q0 = pstride; q0 < g0.cnt; q0 += pstride) slice(entry_or(rp, g0, q0 + spos, pad_e), q0 + spos);
       } else {
-        for (int q = spos; q < cnt; q += sw) {
-          const uint32_t e = (q == spos) ? ef : rp[p0 + q];
+        for (int q = spos; q < g0.cnt; q += sw) {
+          const uint32_t e = (q == spos) ? ea : rp[g0.p0 + q];
           const uint32_t ra = e & 0x7fffu, rb = e >> 16;
           const int sb = int((e >> 15) & 1u);
-          const double ss = sflip(c_s.y, sb), nss = sflip(c_s.y, sb ^ 1);
+          const double ss = sflip(c0.y, sb), nss = sflip(c0.y, sb ^ 1);
           T a = psi[ra], b = psi[rb];
-          A::rot(a, b, c_s.x, ss, nss);
+          A::rot(a, b, c0.x, ss, nss);
           psi[ra] = a;
           psi[rb] = b;
         }
       }
       sweep_barrier(sw);
-      gr = grn;
-      p0 = p0n;
-      cnt = cntn;
-      c_s = c_sn;
-      ef = efn;
+      ea = ean;
     }
   }
   // stage the H psi tables
@@ -417,72 +413,62 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
     __syncthreads();
   }
 
-  // a4: reverse sweep (same prefetch of the next gate as the forward sweep)
+  // a4: reverse sweep (loads ahead as in the forward sweep; the lane's slot of the
+  // next gate is also computed one gate ahead, since the slot is the address of a
+  // load here)
   if (tid < sw && M > 0) {
-    int m = M - 1;
-    GateRec gr = gates[m];
-    int p0 = poff[m], cnt = poff[m + 1] - p0;
-    double2 c_s = cs[m];
-    uint32_t ef = (spos < cnt) ? rp[p0 + spos] : 0u;
-    for (; m >= 0; --m) {
-      GateRec grn = gr;
-      int p0n = 0, cntn = 0;
-      double2 c_sn = c_s;
-      uint32_t efn = 0u;
-      if (m > 0) {
-        grn = gates[m - 1];
-        p0n = poff[m - 1];
-        cntn = poff[m] - p0n;
-        c_sn = cs[m - 1];
-        if (spos < cntn) efn = rp[p0n + spos];
-      }
+    uint32_t ea;
+    int slot0;
+    {
+      const SweepRec g = gates[M - 1];
+      ea = entry_or(rp, g, spos, pad_e);
+      slot0 = spos < g.cnt ? 2 * (g.p0 + spos) + role : scratch;
+    }
+    for (int m = M - 1; m >= 0; --m) {
+      const SweepRec g0 = gates[m];
+      const double2 c0 = cs[m];
+      const SweepRec g1 = gates[max(m - 1, 0)];
+      const uint32_t ean = entry_or(rp, g1, spos, pad_e);
+      const int slotn = spos < g1.cnt ? 2 * (g1.p0 + spos) + role : scratch;
       if constexpr (REAL) {
         // two lanes per pair: the lane's slot holds phi at its own index (role 0
         // at ra, role 1 at rb); role 0 keeps s lambda_b phi_a, role 1 keeps
         // -s lambda_a phi_b, and each un-applies the gate to lambda at its index
-        for (int q0 = 0; q0 < cnt; q0 += pstride) {
-          const int q = q0 + spos;
-          const bool act = q < cnt;
-          const int qc = min(q, cnt - 1);
-          const uint32_t e = (q0 == 0) ? ef : rp[p0 + qc];
+        auto slice = [&](uint32_t e, int slot) {
           const uint32_t ra = e & 0x7fffu, rb = e >> 16;
-          const int sr_bit = int((e >> 15) & 1u) ^ role;
+          const int sr = int((e >> 15) & 1u) ^ role;
           const uint32_t ks = role ? rb : ra, ko = role ? ra : rb;
-          const int slot = 2 * (p0 + qc) + role;
+          const double ph = gbuf[slot], ls = pl[ks].y, lo = pl[ko].y;
+          __syncwarp();
+          double g_term, nl;
           if constexpr (FIX) {
-            const long long ph = dbits(gbuf[slot]), ls = dbits(pl[ks].y), lo = dbits(pl[ko].y);
-            __syncwarp();
-            const unsigned long long cm = static_cast<unsigned long long>(dbits(c_s.x));
-            const unsigned long long sm = static_cast<unsigned long long>(dbits(c_s.y));
-            const int cneg = gr.pad & 1, sneg = ((gr.pad >> 1) & 1) ^ sr_bit;
-            const long long g_term = neg_if(__mul64hi(ph, lo), sr_bit);
-            const long long nl = neg_if(mulhi_su(ls, cm), cneg) + neg_if(mulhi_su(lo, sm), sneg);
-            if (act) {
-              gbuf[slot] = llbits(g_term);
-              pl[ks].y = llbits(nl);
-            }
+            const unsigned long long cm = static_cast<unsigned long long>(dbits(c0.x));
+            const unsigned long long sm = static_cast<unsigned long long>(dbits(c0.y));
+            const int cneg = g0.signs & 1, sneg = ((g0.signs >> 1) & 1) ^ sr;
+            g_term = llbits(neg_if(__mul64hi(dbits(ph), dbits(lo)), sr));
+            nl = llbits(neg_if(mulhi_su(dbits(ls), cm), cneg) + neg_if(mulhi_su(dbits(lo), sm), sneg));
           } else {
-            const double ph = gbuf[slot], ls = pl[ks].y, lo = pl[ko].y;
-            __syncwarp();
-            const double sr = sflip(c_s.y, sr_bit);
-            const double g_term = sflip(lo * ph, sr_bit);
-            const double nl = fma(sr, lo, c_s.x * ls);
-            if (act) {
-              gbuf[slot] = g_term;
-              pl[ks].y = nl;
-            }
+            g_term = sflip(lo * ph, sr);
+            nl = fma(sflip(c0.y, sr), lo, c0.x * ls);
           }
+          gbuf[slot] = g_term;
+          pl[ks].y = nl;
+        };
+        slice(ea, slot0);
+        for (int q0 = pstride; q0 < g0.cnt; q0 += pstride) {
+          const int q = q0 + spos;
+          slice(entry_or(rp, g0, q, pad_e), q < g0.cnt ? 2 * (g0.p0 + q) + role : scratch);
         }
       } else {
-        for (int q = spos; q < cnt; q += sw) {
-          const uint32_t e = (q == spos) ? ef : rp[p0 + q];
+        for (int q = spos; q < g0.cnt; q += sw) {
+          const uint32_t e = (q == spos) ? ea : rp[g0.p0 + q];
           const uint32_t ra = e & 0x7fffu, rb = e >> 16;
           const int sb = int((e >> 15) & 1u);
-          const double ss = sflip(c_s.y, sb), nss = sflip(c_s.y, sb ^ 1);
+          const double ss = sflip(c0.y, sb), nss = sflip(c0.y, sb ^ 1);
           T pa = psi[ra], pb = psi[rb], la = lam[ra], lb = lam[rb];
-          gbuf[p0 + q] = sflip(A::cross(lb, pa, la, pb), sb);
-          A::rot(pa, pb, c_s.x, nss, ss);
-          A::rot(la, lb, c_s.x, nss, ss);
+          gbuf[g0.p0 + q] = sflip(A::cross(lb, pa, la, pb), sb);
+          A::rot(pa, pb, c0.x, nss, ss);
+          A::rot(la, lb, c0.x, nss, ss);
           psi[ra] = pa;
           psi[rb] = pb;
           lam[ra] = la;
@@ -490,11 +476,8 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
         }
       }
       sweep_barrier(sw);
-      gr = grn;
-      p0 = p0n;
-      cnt = cntn;
-      c_s = c_sn;
-      ef = efn;
+      ea = ean;
+      slot0 = slotn;
     }
   }
   __syncthreads();
