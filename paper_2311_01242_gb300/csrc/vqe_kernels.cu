@@ -96,7 +96,10 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
   const ResidentLayout L = resident_layout(n, M, P, G, d.E, d.S, D, d.lo_bits, REAL, stage);
   T* psi = reinterpret_cast<T*>(smem + L.psi);
   T* lam = reinterpret_cast<T*>(smem + L.lam);
-  double2* pl = reinterpret_cast<double2*>(smem + L.psi);  // real: pl[r] = {psi_r, lambda_r}
+  // real amplitudes: psi and lambda in two arrays of D + 1 doubles (entry D is the
+  // sweeps' scratch row), 8-byte strides for the scattered accesses
+  double* pr = reinterpret_cast<double*>(smem + L.psi);
+  double* lr = pr + (D + 1);
   double2* cs = reinterpret_cast<double2*>(smem + L.cs);
   SweepRec* gates = reinterpret_cast<SweepRec*>(smem + L.gates);
   int32_t* poff = reinterpret_cast<int32_t*>(smem + L.poff);
@@ -158,7 +161,10 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
     }
   }
   if constexpr (REAL) {
-    for (int r = tid; r <= D; r += bs) pl[r] = make_double2(0.0, 0.0);
+    for (int r = tid; r <= D; r += bs) {
+      pr[r] = 0.0;
+      lr[r] = 0.0;
+    }
   } else {
     for (int r = tid; r < D; r += bs) {
       psi[r] = A::zero();
@@ -168,22 +174,21 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
   __syncthreads();
   if (tid == 0) {
     if constexpr (FIX)
-      pl[d.hf_rank].x = llbits(1ll << 62);
+      pr[d.hf_rank] = llbits(1ll << 62);
     else if constexpr (REAL)
-      pl[d.hf_rank].x = 1.0;
+      pr[d.hf_rank] = 1.0;
     else
       psi[d.hf_rank] = A::unit();
   }
   __syncthreads();
 
-  // lane-interleaved position of this thread in the sweep: consecutive pairs go
-  // to consecutive warps so every sub-partition gets work on small gates
-  const int swarps = sw >> 5;
-  // complex: one lane per pair, consecutive pairs on consecutive warps;
-  // real: two adjacent lanes per pair (role 0 and 1), pairs dealt the same way
+  // position of this thread in the sweep: warp w takes the pairs [16 w, 16 w + 16)
+  // of each slice of a gate's pairs (real: two adjacent lanes per pair, role 0
+  // and 1; complex: one lane per pair, [32 w, 32 w + 32)), so a warp's slot
+  // stores are contiguous
   const int role = REAL ? (tid & 1) : 0;
   const int pstride = REAL ? (sw >> 1) : sw;
-  const int spos = REAL ? (((tid & 31) >> 1) * swarps + (tid >> 5)) : ((tid & 31) * swarps + (tid >> 5));
+  const int spos = REAL ? ((tid >> 5) * 16 + ((tid & 31) >> 1)) : tid;
 
   // a2: forward sweep. A gate's record and cos/sin are loaded at its start (they
   // are first needed after the amplitude loads), the lane's first pair entry one
@@ -206,7 +211,7 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
           const uint32_t ra = e & 0x7fffu, rb = e >> 16;
           const uint32_t kd = role ? rb : ra, ko = role ? ra : rb;
           const int sg = int((e >> 15) & 1u) ^ role ^ 1;
-          const double self = pl[kd].x, other = pl[ko].x;
+          const double self = pr[kd], other = pr[ko];
           __syncwarp();
           double out;
           if constexpr (FIX) {
@@ -216,7 +221,7 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
           } else {
             out = fma(sflip(c0.y, sg), other, c0.x * self);
           }
-          pl[kd].x = out;
+          pr[kd] = out;
           gbuf[q < g0.cnt ? 2 * (g0.p0 + q) + role : scratch] = out;
         };
         slice(ea, spos);
@@ -293,7 +298,7 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
   const bool int_h = FIX && (stage || mat_h);  // precomputed entry coefficients need no tables
   const int eh = int_h ? bound_exp(*d.hbound) : 0;
   if (FIX && !int_h) {
-    for (int r = tid; r < D; r += bs) pl[r].x = __ll2double_rn(dbits(pl[r].x)) * 0x1p-62;
+    for (int r = tid; r < D; r += bs) pr[r] = __ll2double_rn(dbits(pr[r])) * 0x1p-62;
     __syncthreads();
   }
 
@@ -301,8 +306,8 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
   double e_part = 0.0;
   const int r_half = (D + CL - 1) / CL;
   const int r_lo = crank * r_half, r_hi = min(D, r_lo + r_half);
-  double2* pl_peer = pl;
-  if constexpr (CL == 2) pl_peer = cooperative_groups::this_cluster().map_shared_rank(pl, crank ^ 1);
+  double* lr_peer = lr;
+  if constexpr (CL == 2) lr_peer = cooperative_groups::this_cluster().map_shared_rank(lr, crank ^ 1);
   // Real amplitudes: two threads per output row, one on the row's even slots and
   // one on its odd slots, added (even + odd) by a fixed shuffle; the split
   // depends on nothing but the row, so every launch form gives the same bits.
@@ -310,9 +315,9 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
   const int rows = r_hi - r_lo, per_pass = bs / TPR, half = tid % TPR;
   const bool fast = d.ellp_fast != 0;
   for (int base = 0; base < rows; base += per_pass) {  // same trip count in every thread
-    const int lr = base + tid / TPR;
-    const bool live = lr < rows;
-    const int r = r_lo + (live ? lr : 0);
+    const int lrow = base + tid / TPR;
+    const bool live = lrow < rows;
+    const int r = r_lo + (live ? lrow : 0);
     const uint32_t k = __ldg(d.sector + r);
     if constexpr (FIX) {
       if (int_h) {
@@ -320,7 +325,7 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
         long long acc = 0;
         if (live && mat_h) {
           ell_row_mat<kEllChunk>(d.ellp, d.hmat, W, D, r, half, TPR, [&](uint32_t e, long long f) {
-            acc += __mul64hi(f, dbits(pl[e & 0x7fffu].x));
+            acc += __mul64hi(f, dbits(pr[e & 0x7fffu]));
           });
         } else if (live) {
           const long long* tvi = reinterpret_cast<const long long*>(tv);
@@ -332,14 +337,14 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
               const GroupRec g = load_group(tg + (e >> 19));
               f = group_coef_int(g, te, tvi, k ^ g.x, (e >> 15) & 15u);
             }
-            acc += __mul64hi(f, dbits(pl[e & 0x7fffu].x));
+            acc += __mul64hi(f, dbits(pr[e & 0x7fffu]));
           });
         }
         acc += __shfl_xor_sync(0xffffffffu, acc, 1);  // even + odd slots (exact)
         if (live && half == 0) {
-          pl[r].y = llbits(acc);
-          if constexpr (CL == 2) pl_peer[r].y = llbits(acc);
-          e_part += (__ll2double_rn(dbits(pl[r].x)) * 0x1p-62) * (__ll2double_rn(acc) * pow2(eh - 60));
+          lr[r] = llbits(acc);
+          if constexpr (CL == 2) lr_peer[r] = llbits(acc);
+          e_part += (__ll2double_rn(dbits(pr[r])) * 0x1p-62) * (__ll2double_rn(acc) * pow2(eh - 60));
         }
         continue;
       }
@@ -355,7 +360,7 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
           f = group_coef_u<REAL>(g, te, tv, k ^ g.x, (e >> 15) & 15u);
         }
         if constexpr (REAL)
-          A::mac(acc, f, pl[e & 0x7fffu].x);
+          A::mac(acc, f, pr[e & 0x7fffu]);
         else
           A::mac(acc, f, psi[e & 0x7fffu]);
       });
@@ -366,9 +371,9 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
     }
     if (live && half == 0) {
       if constexpr (REAL) {
-        pl[r].y = acc;
-        if constexpr (CL == 2) pl_peer[r].y = acc;
-        e_part += pl[r].x * acc;
+        lr[r] = acc;
+        if constexpr (CL == 2) lr_peer[r] = acc;
+        e_part += pr[r] * acc;
       } else {
         lam[r] = acc;
         e_part += A::redot(psi[r], acc);
@@ -399,7 +404,7 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
   } else if constexpr (FIX) {
     double l2 = 0.0;
     for (int r = tid; r < D; r += bs) {
-      const double v = pl[r].y;
+      const double v = lr[r];
       l2 = fma(v, v, l2);
     }
     const double tot = block_sum(l2, red);
@@ -409,7 +414,7 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
     // ||lambda||^2 < 2^(ex - 1022) <= 2^(2 lam_e)
     lam_e = ex == 0 ? -500 : (ex - 1022 + 1) >> 1;
     const double sc = pow2(61 - lam_e);
-    for (int r = tid; r < D; r += bs) pl[r].y = llbits(__double2ll_rn(pl[r].y * sc));
+    for (int r = tid; r < D; r += bs) lr[r] = llbits(__double2ll_rn(lr[r] * sc));
     __syncthreads();
   }
 
@@ -438,7 +443,7 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
           const uint32_t ra = e & 0x7fffu, rb = e >> 16;
           const int sr = int((e >> 15) & 1u) ^ role;
           const uint32_t ks = role ? rb : ra, ko = role ? ra : rb;
-          const double ph = gbuf[slot], ls = pl[ks].y, lo = pl[ko].y;
+          const double ph = gbuf[slot], ls = lr[ks], lo = lr[ko];
           __syncwarp();
           double g_term, nl;
           if constexpr (FIX) {
@@ -452,7 +457,7 @@ k_resident(const InstDesc* __restrict__ descs, const InstDesc one, const double*
             nl = fma(sflip(c0.y, sr), lo, c0.x * ls);
           }
           gbuf[slot] = g_term;
-          pl[ks].y = nl;
+          lr[ks] = nl;
         };
         slice(ea, slot0);
         for (int q0 = pstride; q0 < g0.cnt; q0 += pstride) {
