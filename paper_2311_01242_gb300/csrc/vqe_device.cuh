@@ -313,28 +313,36 @@ __device__ __forceinline__ void ell_row(const uint32_t* ell, const uint16_t* ell
 }
 
 // ell_row over packed entries together with their precomputed coefficients
-// (InstDesc::hmat, the same [W][D] layout): calls f(entry, coefficient).
+// (InstDesc::hmat, the same [W][D] layout): calls f(entry, coefficient) for the
+// thread's slots first, first + step, ... in order. The walk advances two
+// pointers by a fixed stride and counts the thread's slots once, so a slot
+// costs its two loads and no index arithmetic; the next U slots are loaded
+// while the current U are combined.
 template <int U, class F>
 __device__ __forceinline__ void ell_row_mat(const uint32_t* ell, const long long* mat, int W, int64_t D, int64_t r,
                                             int first, int step, F&& f) {
+  const int n = (W - first + step - 1) / step;  // this thread's slots
+  const int64_t stride = int64_t(step) * D;
+  const uint32_t* pe = ell + int64_t(first) * D + r;
+  const long long* pm = mat + int64_t(first) * D + r;
   uint32_t cur[U];
   long long cv[U];
 #pragma unroll
   for (int u = 0; u < U; ++u) {
-    const int j = first + u * step;
-    cur[u] = j < W ? __ldg(ell + int64_t(j) * D + r) : kEllPad;
-    cv[u] = j < W ? __ldg(mat + int64_t(j) * D + r) : 0ll;
+    cur[u] = u < n ? __ldg(pe + u * stride) : kEllPad;
+    cv[u] = u < n ? __ldg(pm + u * stride) : 0ll;
   }
-  for (int j0 = first; j0 < W; j0 += U * step) {
-    const bool more = cur[U - 1] != kEllPad && j0 + U * step < W;
+  for (int i0 = 0; i0 < n; i0 += U) {
+    const bool more = cur[U - 1] != kEllPad && i0 + U < n;
+    pe += U * stride;
+    pm += U * stride;
     uint32_t nxt[U];
     long long nv[U];
 #pragma unroll
     for (int u = 0; u < U; ++u) {
-      const int j = j0 + (U + u) * step;
-      const bool ok = more && j < W;
-      nxt[u] = ok ? __ldg(ell + int64_t(j) * D + r) : kEllPad;
-      nv[u] = ok ? __ldg(mat + int64_t(j) * D + r) : 0ll;
+      const bool ok = more && i0 + U + u < n;
+      nxt[u] = ok ? __ldg(pe + u * stride) : kEllPad;
+      nv[u] = ok ? __ldg(pm + u * stride) : 0ll;
     }
 #pragma unroll
     for (int u = 0; u < U; ++u)
