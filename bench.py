@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--workload", choices=["scan12", "warmstart", "config3", "config2", "q24", "adapt30",
-                                           "puccd11", "puccd24", "adapt24", "adapt12"],
+                                           "puccd11", "puccd24", "adapt24", "adapt12", "noalloc16"],
                     default="scan12",
                     help="scan12: the throughput line (default); warmstart: the 16-qubit learned-warm-start "
                          "comparison (time to 1 mHa vs the plain HF start); config3: one 30-qubit instance; "
@@ -61,7 +61,8 @@ def parse():
                          "state); adapt12: the whole ADAPT-VQE loop on one 12-qubit geometry (pool gradient "
                          "norm below 1e-3 or 60 operators); puccd11: pUCCD in the hard-core boson "
                          "form, 11 orbitals x 64 geometries in one launch; puccd24: one 24-orbital pUCCD "
-                         "instance (12 pairs, 2.7M boson states)")
+                         "instance (12 pairs, 2.7M boson states); noalloc16: the allocation-free entry point "
+                         "against vqe_energy_grad on one 16-qubit instance")
     ap.add_argument("--held-out", type=int, default=24, help="warmstart: held-out scan points compared")
     ap.add_argument("--skip", nargs="*", default=[], choices=["config3", "config2", "warmstart", "complex"],
                     help="default line: leave these per-config entries out")
@@ -370,6 +371,56 @@ def run_large(args):
                          "state_bytes_per_step": state_bytes,
                          "state_gbs": state_bytes / (ms_step / 1e3) / 1e9},
             "gpu_launches_per_step": launches, "clocks": clk[0] if clk else None}
+    print(json.dumps(line), flush=True)
+
+
+def run_noalloc(args):
+    """noalloc16: one 16-qubit instance (8 electrons, the first such instance of the
+    uneven batch), energy + gradient per step through vqe_energy_grad (caller's
+    workspace) and through vqe_energy_grad_noalloc (the library's static scratch),
+    the latter before and after the regular call has built the pair's string
+    tables; CUDA-event timed, L2 flushed between steps."""
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_2311_01242_gb300 as vq
+    from paper_2311_01242_gb300.api import _ptr, _stream
+
+    torch.cuda.set_device(0)
+    lib = vq.load()
+    steps, warmup = min(args.steps, 50), max(3, min(args.warmup, 5))
+    ns, _ = synth.configs.config2_sizes()
+    p, exc, th = synth.config2_instance(int(np.nonzero(ns == 16)[0][0]))
+    theta = torch.as_tensor(th).cuda()
+    e = torch.empty(1, dtype=torch.float64, device="cuda")
+    g = torch.empty(len(th), dtype=torch.float64, device="cuda")
+
+    def noalloc(H, A):
+        rc = lib.vqe_energy_grad_noalloc(H.handle, A.handle, _ptr(theta), _ptr(e), _ptr(g), _stream())
+        if rc != 0:
+            raise RuntimeError(lib.vqe_last_error().decode(errors="replace"))
+
+    clk = []
+    # a fresh pair: no string or connectivity tables built yet
+    H0 = vq.Hamiltonian.from_problem(p)
+    A0 = vq.Ansatz(p.n_qubits, synth.hf_bitstring(p.n_elec), exc)
+    ms_before = float(np.median(_timed(lambda: noalloc(H0, A0), steps, warmup, clk)))
+    H = vq.Hamiltonian.from_problem(p)
+    A = vq.Ansatz(p.n_qubits, synth.hf_bitstring(p.n_elec), exc)
+    ws = vq.alloc_workspace(vq.workspace_bytes(H, A, vq.VQE_WS_GRAD))
+    ms_reg = float(np.median(_timed(lambda: vq.energy_grad(H, A, theta, workspace=ws, out=(e, g)), steps, warmup,
+                                    clk)))
+    ms_after = float(np.median(_timed(lambda: noalloc(H, A), steps, warmup, clk)))
+    line = {"metric": METRIC + " [noalloc16]", "value": 1e3 / ms_after, "unit": "evals/s", "n_gpus": 1,
+            "steps": steps, "warmup": warmup, "ms_per_step": ms_after, "higher_is_better": True,
+            "dtype": "f64", "data": "synthetic",
+            "config": {"workload": f"16 qubits, {p.n_elec} electrons, {len(th)} UCCSD angles "
+                                   f"({A.info()['sector_dim']} sector amplitudes), energy + gradient",
+                       "l2": "flushed between timed steps (512 MB write)"},
+            "energy_grad_ms": ms_reg, "noalloc_ms_tables_built": ms_after, "noalloc_ms_no_tables": ms_before,
+            "ratio_tables_built": ms_after / ms_reg, "ratio_no_tables": ms_before / ms_reg,
+            "clocks": clk[0] if clk else None}
     print(json.dumps(line), flush=True)
 
 
@@ -963,6 +1014,10 @@ def main():
     if args.workload == "adapt12":
         if rank == 0:
             run_adapt_loop(args)
+        return
+    if args.workload == "noalloc16":
+        if rank == 0:
+            run_noalloc(args)
         return
 
     import numpy as np
