@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--workload", choices=["scan12", "warmstart", "config3", "config2", "q24", "adapt30",
-                                           "puccd11", "puccd24", "adapt24", "adapt12", "noalloc16"],
+                                           "puccd11", "puccd24", "adapt24", "adapt12", "noalloc16", "hpsi30s"],
                     default="scan12",
                     help="scan12: the throughput line (default); warmstart: the 16-qubit learned-warm-start "
                          "comparison (time to 1 mHa vs the plain HF start); config3: one 30-qubit instance; "
@@ -62,7 +62,9 @@ def parse():
                          "norm below 1e-3 or 60 operators); puccd11: pUCCD in the hard-core boson "
                          "form, 11 orbitals x 64 geometries in one launch; puccd24: one 24-orbital pUCCD "
                          "instance (12 pairs, 2.7M boson states); noalloc16: the allocation-free entry point "
-                         "against vqe_energy_grad on one 16-qubit instance")
+                         "against vqe_energy_grad on one 16-qubit instance; hpsi30s: the 30-qubit Hamiltonian in "
+                         "the 4-alpha/5-beta sector (4.1M states, the same wide block form of the string-driven "
+                         "H psi as config3 on a smaller case, for full ncu captures)")
     ap.add_argument("--held-out", type=int, default=24, help="warmstart: held-out scan points compared")
     ap.add_argument("--skip", nargs="*", default=[], choices=["config3", "config2", "warmstart", "complex"],
                     help="default line: leave these per-config entries out")
@@ -314,10 +316,22 @@ def run_large(args):
             flops += f
             state_bytes += b
         launches = None
-    elif args.workload in ("config3", "q24"):
+    elif args.workload in ("config3", "q24", "hpsi30s"):
+        hf = synth.hf_bitstring(10)
         if args.workload == "config3":
             w = synth.config3()
             p, exc, th, drop, nq = w.problems[0], w.excitations[0], w.thetas[0], w.drop_tol, 30
+        elif args.workload == "hpsi30s":
+            # 4 alpha and 5 beta electrons: the 5-alpha/4-beta UCCSD pool with alpha and
+            # beta qubits swapped (q -> q ^ 1), 256 of its excitations
+            w = synth.config3()
+            p, drop, nq = w.problems[0], w.drop_tol, 30
+            rng = np.random.default_rng(30)
+            pool = synth.uccsd_pool(30, 9)
+            pool = np.where(pool >= 0, pool ^ 1, pool)
+            exc = pool[rng.permutation(len(pool))[:256]]
+            th = rng.normal(0.0, 0.05, size=256)
+            hf = sum(1 << q for q in (0, 2, 4, 6, 1, 3, 5, 7, 9))
         else:
             rng = np.random.default_rng(24)
             p = synth.integrals.random_problem(rng, 12, 10, 6, label="q24")
@@ -325,7 +339,7 @@ def run_large(args):
             exc = pool[rng.permutation(len(pool))[:256]]
             th, drop, nq = rng.normal(0.0, 0.05, size=256), 1e-14, 24
         H = vq.Hamiltonian.from_problem(p, drop)
-        A = vq.Ansatz(nq, synth.hf_bitstring(10), exc)
+        A = vq.Ansatz(nq, hf, exc)
         ws = vq.alloc_workspace(vq.workspace_bytes(H, A, vq.VQE_WS_GRAD))
         theta = torch.as_tensor(th).cuda()
         e_buf = torch.empty(1, dtype=torch.float64, device="cuda")
@@ -334,8 +348,10 @@ def run_large(args):
         ms = _timed(lambda: vq.energy_grad(H, A, theta, workspace=ws, out=(e_buf, g_buf)), steps, warmup, clk)
         flops, state_bytes = vq.work_estimate(H, A, True)
         units, unit = 1, "evals/s"
-        workload = ("30 qubits, 10 electrons, 512 UCCSD angles (9.0M sector amplitudes)" if nq == 30 else
-                    "24 qubits, 10 electrons, 256 UCCSD angles (627k sector amplitudes)")
+        workload = {"config3": "30 qubits, 10 electrons, 512 UCCSD angles (9.0M sector amplitudes)",
+                    "q24": "24 qubits, 10 electrons, 256 UCCSD angles (627k sector amplitudes)",
+                    "hpsi30s": "30 qubits, 4 alpha + 5 beta electrons, 256 UCCSD angles (4.1M sector "
+                               "amplitudes)"}[args.workload]
         launches = 2 * len(exc) + 8  # trig, init, gates, 4 H psi launches + energy sum, gates, gradient sums
     else:
         insts = [synth.config2_instance(j) for j in range(256)]
@@ -1003,7 +1019,7 @@ def main():
         if rank == 0:
             run_warmstart(args)
         return
-    if args.workload in ("config3", "config2", "q24", "puccd11", "puccd24"):
+    if args.workload in ("config3", "config2", "q24", "puccd11", "puccd24", "hpsi30s"):
         if rank == 0:
             run_large(args)
         return
