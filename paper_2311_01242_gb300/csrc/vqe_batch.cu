@@ -177,7 +177,7 @@ k_batch_persistent(const PersistDev p, const double* __restrict__ theta, int64_t
           else if (sp.Db < kStrWideDb)
             hpsi_str_row<true, false, true>(sp, int(tk.lo), d.groups, d.emask, d.vals, psi_am, lam_am, smem);
           else
-            hpsi_str_row<true, true, true>(sp, int(tk.lo), d.groups, d.emask, d.vals, psi_am, lam_am, smem);
+            hpsi_str_row<true, true, true, 4>(sp, int(tk.lo), d.groups, d.emask, d.vals, psi_am, lam_am, smem);
         } else {
           for (int64_t r = tk.lo + tid; r < tk.hi; r += kPersistThreads) {
             const uint32_t k = __ldg(d.sector + r);

@@ -709,8 +709,10 @@ __device__ __forceinline__ void str_groups_hot(const StrPlan& sp, int g0, int g1
 // shared memory; then every warp walks its share (a fixed Ib range) of each
 // group's beta pair list. Needs blockDim.x == 32 * kStrWarps and 2 * Db
 // amplitudes (+ Db words of beta strings when Db < kStrWideDb; above, they are
-// read from global memory through L1) of shared memory.
-template <bool REAL, bool WIDE, bool CG = false>
+// read from global memory through L1) of shared memory. UW: list entries per lane
+// in flight in the real wide form's pipelined group loop (16 for the standalone
+// kernel; the persistent batch kernel, which has fewer registers to spare, uses 4).
+template <bool REAL, bool WIDE, bool CG = false, int UW = 16>
 __device__ __forceinline__ void hpsi_str_row(const StrPlan& sp, int ia, const GroupRec* __restrict__ groups,
                                              const uint32_t* __restrict__ emask,
                                              const typename Amp<REAL>::C* __restrict__ vals,
@@ -760,10 +762,10 @@ __device__ __forceinline__ void hpsi_str_row(const StrPlan& sp, int ia, const Gr
     const uint32_t ob = (REAL && WIDE) ? __ldg(sp.bob + b) : 0u;  // the same for the whole block
     for (int j = tid; j < Db; j += bs) psi_s[j] = sflip(ld_state<CG>(row + j), parity32(kb_s[j] & ob));
     __syncthreads();
-    // up to 16 list entries per lane in flight in the pipelined loop: measured best at
+    // UW list entries per lane in flight in the pipelined loop: 16 measured best at
     // 30 qubits (H psi 4: 88.5 ms, 8: 86.3, 12: 87.5, 16: 85.3; the same bits)
     if constexpr (REAL && WIDE)
-      str_groups_hot<16>(sp, __ldg(sp.boff + b), __ldg(sp.boff + b + 1), w, w + 1, __ldg(sp.ka + ja), groups, emask,
+      str_groups_hot<UW>(sp, __ldg(sp.boff + b), __ldg(sp.boff + b + 1), w, w + 1, __ldg(sp.ka + ja), groups, emask,
                         vals, kb_s, psi_s, lam_s, lane, ob);
     else
       str_groups<REAL, (WIDE && REAL) ? 8 : 4, WIDE>(sp, __ldg(sp.boff + b), __ldg(sp.boff + b + 1), w, w + 1,
