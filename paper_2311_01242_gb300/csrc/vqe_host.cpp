@@ -268,7 +268,6 @@ struct vqe_hamiltonian_s {
   int32_t* d_lin_term = nullptr;
   float* d_lin_w = nullptr;
   double* d_bound = nullptr;  // sum of |vals| over all slots (device)
-  long long* d_ivals = nullptr;  // fixed-point copy of the value tables (entry coefficient builds)
   GroupRec* d_groups = nullptr;
   uint32_t* d_emask = nullptr;
   double* d_vals = nullptr;
@@ -281,6 +280,8 @@ struct vqe_hamiltonian_s {
     uint32_t* d_ellp = nullptr;       // packed entries for the resident kernel (small sectors)
     bool ellp_fast = false;           // d_ellp holds single-slot entries (flag bit 31)
     long long* d_hmat = nullptr;      // fixed-point coefficient of each packed entry (this H's values)
+    long long* d_ivals = nullptr;     // scratch of its builds: the value tables in fixed point (one
+                                      // per sector, so builds on different streams never share it)
     uint32_t* d_hsec = nullptr;       // the sector's basis states, for rebuilding d_hmat
     int64_t hD = 0;
     int64_t nnz = 0;                  // connected (output, group) pairs
@@ -302,9 +303,9 @@ struct vqe_hamiltonian_s {
     dfree(d_lin_term);
     dfree(d_lin_w);
     dfree(d_bound);
-    dfree(d_ivals);
     for (auto& kv : ells) {
       dfree(kv.second.d_hmat);
+      dfree(kv.second.d_ivals);
       dfree(kv.second.d_hsec);
       ell_release(kv.second.d_ell);
       ell_release(kv.second.d_ellp);
@@ -866,20 +867,22 @@ const vqe_hamiltonian_s::Ell* get_ell(vqe_hamiltonian_t h, vqe_ansatz_t a, int* 
         const size_t S = h->cvals.size();
         if (D <= 8192 && mat_bytes <= (size_t(64) << 20) && S > 0) {
           cudaError_t ce = cudaSuccess;
-          if (!h->d_ivals) ce = cudaMalloc(&h->d_ivals, S * sizeof(long long));
+          ce = cudaMalloc(&e.d_ivals, S * sizeof(long long));
           if (ce == cudaSuccess) ce = cudaMalloc(&e.d_hmat, mat_bytes);
           if (ce == cudaSuccess && upload(a->sector, &e.d_hsec) != VQE_OK) ce = cudaErrorMemoryAllocation;
           e.hD = D;
           if (ce == cudaSuccess)
             ce = vqe::build_hmat(e.d_ellp, W, D, e.d_hsec, h->d_groups, h->d_emask, h->d_vals, int64_t(S),
-                                 h->d_bound, e.ellp_fast ? 1 : 0, h->d_ivals, e.d_hmat, 0);
+                                 h->d_bound, e.ellp_fast ? 1 : 0, e.d_ivals, e.d_hmat, 0);
           if (ce == cudaSuccess) ce = cudaDeviceSynchronize();
           if (ce != cudaSuccess) {
             cudaGetLastError();
             dfree(e.d_hmat);
             dfree(e.d_hsec);
+            dfree(e.d_ivals);
             e.d_hmat = nullptr;  // the table path serves instead
             e.d_hsec = nullptr;
+            e.d_ivals = nullptr;
           }
         }
       }
@@ -1627,7 +1630,7 @@ int vqe_set_coefs(vqe_hamiltonian_t h, const double* coefs_dev, vqe_stream_t str
     vqe_hamiltonian_s::Ell& e = kv.second;
     if (!e.d_hmat) continue;
     ce = vqe::build_hmat(e.d_ellp, e.W, e.hD, e.d_hsec, h->d_groups, h->d_emask, h->d_vals, n_slots,
-                         h->d_bound, e.ellp_fast ? 1 : 0, h->d_ivals, e.d_hmat, static_cast<cudaStream_t>(stream));
+                         h->d_bound, e.ellp_fast ? 1 : 0, e.d_ivals, e.d_hmat, static_cast<cudaStream_t>(stream));
     if (ce != cudaSuccess) return cuda_fail(ce, "entry coefficient rebuild");
   }
   return VQE_OK;
