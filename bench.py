@@ -51,7 +51,7 @@ def parse():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--e2e-steps", type=int, default=None)
     ap.add_argument("--workload", choices=["scan12", "warmstart", "config3", "config2", "q24", "adapt30",
-                                           "puccd11", "puccd24", "adapt24", "adapt12", "noalloc16", "hpsi30s"],
+                                           "puccd11", "puccd24", "adapt24", "adapt12", "noalloc16", "hpsi30s", "q20"],
                     default="scan12",
                     help="scan12: the throughput line (default); warmstart: the 16-qubit learned-warm-start "
                          "comparison (time to 1 mHa vs the plain HF start); config3: one 30-qubit instance; "
@@ -64,9 +64,10 @@ def parse():
                          "instance (12 pairs, 2.7M boson states); noalloc16: the allocation-free entry point "
                          "against vqe_energy_grad on one 16-qubit instance; hpsi30s: the 30-qubit Hamiltonian in "
                          "the 4-alpha/5-beta sector (4.1M states, the same wide block form of the string-driven "
-                         "H psi as config3 on a smaller case, for full ncu captures)")
+                         "H psi as config3 on a smaller case, for full ncu captures); q20: one 20-qubit instance "
+                         "(the first of config2's 20-qubit instances)")
     ap.add_argument("--held-out", type=int, default=24, help="warmstart: held-out scan points compared")
-    ap.add_argument("--skip", nargs="*", default=[], choices=["config3", "config2", "warmstart", "complex"],
+    ap.add_argument("--skip", nargs="*", default=[], choices=["config3", "config2", "q20", "warmstart", "complex"],
                     help="default line: leave these per-config entries out")
     ap.add_argument("--no-per-config", action="store_true", help="default line: headline only")
     ap.add_argument("--pool-ops", type=int, default=None,
@@ -316,9 +317,13 @@ def run_large(args):
             flops += f
             state_bytes += b
         launches = None
-    elif args.workload in ("config3", "q24", "hpsi30s"):
+    elif args.workload in ("config3", "q24", "hpsi30s", "q20"):
         hf = synth.hf_bitstring(10)
-        if args.workload == "config3":
+        if args.workload == "q20":
+            ns, _ = synth.configs.config2_sizes()
+            p, exc, th = synth.config2_instance(int(np.nonzero(ns == 20)[0][0]))
+            drop, nq, hf = 1e-14, 20, synth.hf_bitstring(p.n_elec)
+        elif args.workload == "config3":
             w = synth.config3()
             p, exc, th, drop, nq = w.problems[0], w.excitations[0], w.thetas[0], w.drop_tol, 30
         elif args.workload == "hpsi30s":
@@ -351,7 +356,9 @@ def run_large(args):
         workload = {"config3": "30 qubits, 10 electrons, 512 UCCSD angles (9.0M sector amplitudes)",
                     "q24": "24 qubits, 10 electrons, 256 UCCSD angles (627k sector amplitudes)",
                     "hpsi30s": "30 qubits, 4 alpha + 5 beta electrons, 256 UCCSD angles (4.1M sector "
-                               "amplitudes)"}[args.workload]
+                               "amplitudes)",
+                    "q20": f"20 qubits, {p.n_elec} electrons, {len(exc)} UCCSD angles (63,504 sector amplitudes)"
+                    }[args.workload]
         launches = 2 * len(exc) + 8  # trig, init, gates, 4 H psi launches + energy sum, gates, gradient sums
     else:
         insts = [synth.config2_instance(j) for j in range(256)]
@@ -840,15 +847,23 @@ def entry_config3(args, gpu_index):
     flops, state_bytes = vq.work_estimate(H, A, True)
     counts = vq.work_counts(H, A)
     ms = tm["ms_per_step"]
-    # A/B: the same evaluation with the gate sweeps as one persistent launch each
-    # instead of one launch per gate
+    # A/B: the reverse sweep un-applying each gate to psi instead of reading the kept
+    # forward outputs, and that path with each sweep as one persistent launch
+    old = vq.set_flags(vq.VQE_FLAG_NO_PHI_STORE)
+    try:
+        e_u = torch.empty(1, dtype=torch.float64, device="cuda")
+        g_u = torch.empty(len(exc), dtype=torch.float64, device="cuda")
+        tu, clocks_u = _measure(lambda: vq.energy_grad(H, A, theta, workspace=ws, out=(e_u, g_u)), min(steps, 5), 3,
+                                gpu_index)
+    finally:
+        vq.set_flags(old)
     old = vq.set_flags(vq.VQE_FLAG_PERSISTENT_SWEEPS)
     try:
         e_l = torch.empty(1, dtype=torch.float64, device="cuda")
         g_l = torch.empty(len(exc), dtype=torch.float64, device="cuda")
         tl, clocks_l = _measure(lambda: vq.energy_grad(H, A, theta, workspace=ws, out=(e_l, g_l)), min(steps, 5), 3,
                                 gpu_index)
-        same_bits = bool(torch.equal(e_l, e_buf) and torch.equal(g_l, g_buf))
+        same_bits = bool(torch.equal(e_l, e_u) and torch.equal(g_l, g_u))
     finally:
         vq.set_flags(old)
     # complex128 amplitudes and full complex coefficients (the same kernels' complex form)
@@ -878,7 +893,11 @@ def entry_config3(args, gpu_index):
     assert abs(float(e_np[0]) - e_real) <= 1e-12, "host-buffer and device calls disagree"
     del wsh, B
     peak_hbm, hbm_src = measured_hbm_gbs()
-    hpsi_dram = _profile_field("k_hpsi_str_config3.md", RESIDENT_SRC, "dram_bytes_per_launch")
+    # DRAM bytes of one whole evaluation (every kernel, warm L2 as in the timed steps),
+    # else those of the H psi launch alone (cold L2)
+    hpsi_dram = _profile_field("dram_config3_eval.md", RESIDENT_SRC + ["vqe_phi.cu"], "dram_bytes_per_eval")
+    if hpsi_dram is None:
+        hpsi_dram = _profile_field("k_hpsi_str_config3.md", RESIDENT_SRC, "dram_bytes_per_launch")
     achieved = flops / (ms / 1e3) / 1e12
     roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
             "frac": achieved / FP64_PEAK_TFLOPS, "kernel": "k_hpsi_str (wide block form) + k_gate_fwd/k_gate_adj",
@@ -898,8 +917,53 @@ def entry_config3(args, gpu_index):
             "e2e": e2e, "cpu_baseline": cpu,
             "complex128": {"value": 1e3 / tc["ms_per_step"], "unit": "evals/s", **tc, "clocks": clocks_c,
                            "abs_diff_energy_vs_real": d_e, "max_abs_diff_grad_vs_real": d_g},
-            "gate_sweeps": {"one_launch_per_gate_ms_per_step": ms, "persistent_ms_per_step": tl["ms_per_step"],
-                            "same_bits": same_bits, "clocks_persistent": clocks_l},
+            "reverse_sweep": {"kept_forward_outputs_ms_per_step": ms, "unapplying_ms_per_step": tu["ms_per_step"],
+                              "energy_same_bits": bool(torch.equal(e_u, e_buf)),
+                              "max_abs_diff_grad": float((g_u - g_buf).abs().max()), "clocks_unapplying": clocks_u},
+            "gate_sweeps": {"one_launch_per_gate_ms_per_step": tu["ms_per_step"],
+                            "persistent_ms_per_step": tl["ms_per_step"], "same_bits": same_bits,
+                            "clocks_persistent": clocks_l},
+            "l2": "flushed between timed steps (512 MB write)"}
+
+
+def entry_q20(args, gpu_index):
+    """One 20-qubit instance (the first of config 2's 20-qubit instances): one energy +
+    adjoint gradient per step; HBM bytes per evaluation from the committed launch list
+    of one evaluation (every kernel, warm L2 as in the timed steps)."""
+    import numpy as np
+    import torch
+
+    import synth
+    import paper_2311_01242_gb300 as vq
+
+    steps, warmup = min(args.steps, 20), max(3, min(args.warmup, 5))
+    ns, _ = synth.configs.config2_sizes()
+    p, exc, th = synth.config2_instance(int(np.nonzero(ns == 20)[0][0]))
+    H = vq.Hamiltonian.from_problem(p)
+    A = vq.Ansatz(20, synth.hf_bitstring(p.n_elec), exc)
+    ws = vq.alloc_workspace(vq.workspace_bytes(H, A, vq.VQE_WS_GRAD))
+    theta = torch.as_tensor(th).cuda()
+    e_buf = torch.empty(1, dtype=torch.float64, device="cuda")
+    g_buf = torch.empty(len(exc), dtype=torch.float64, device="cuda")
+    tm, clocks = _measure(lambda: vq.energy_grad(H, A, theta, workspace=ws, out=(e_buf, g_buf)), steps, warmup,
+                          gpu_index)
+    tm.pop("per_step")
+    ms = tm["ms_per_step"]
+    flops, state_bytes = vq.work_estimate(H, A, True)
+    peak_hbm, hbm_src = measured_hbm_gbs()
+    dram = _profile_field("dram_q20_eval.md", RESIDENT_SRC, "dram_bytes_per_eval")
+    achieved = flops / (ms / 1e3) / 1e12
+    roof = {"bound": "alu", "achieved": achieved, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+            "frac": achieved / FP64_PEAK_TFLOPS, "kernel": "k_hpsi_str (warp form) + k_gate_fwd/k_gate_adj",
+            "traffic": dram, "dram_bytes_per_step": dram,
+            "hbm_gbs": None if dram is None else dram / (ms / 1e3) / 1e9,
+            "hbm_frac": None if dram is None else dram / (ms / 1e3) / 1e9 / peak_hbm,
+            "hbm_peak": peak_hbm, "hbm_peak_source": hbm_src,
+            "state_bytes_per_step": state_bytes, "state_gbs": state_bytes / (ms / 1e3) / 1e9,
+            "fp64_flops_per_step": flops}
+    return {"workload": f"20 qubits, {p.n_elec} electrons, {len(exc)} UCCSD angles (63,504 sector amplitudes), "
+                        "energy + adjoint gradient", "metric": "energy+adjoint-grad evals/s", "value": 1e3 / ms,
+            "unit": "evals/s", **tm, "dtype": "f64 (real amplitudes)", "clocks": clocks, "roofline": roof,
             "l2": "flushed between timed steps (512 MB write)"}
 
 
@@ -993,6 +1057,7 @@ def per_config(args, gpu_index, extra=None):
     out = dict(extra or {})
     for name, fn in (("config3", lambda: entry_config3(args, gpu_index)),
                      ("config2", lambda: entry_config2(args, gpu_index)),
+                     ("q20", lambda: entry_q20(args, gpu_index)),
                      ("warmstart", lambda: warmstart_summary(args))):
         if name in args.skip:
             continue
@@ -1019,7 +1084,7 @@ def main():
         if rank == 0:
             run_warmstart(args)
         return
-    if args.workload in ("config3", "config2", "q24", "puccd11", "puccd24", "hpsi30s"):
+    if args.workload in ("config3", "config2", "q24", "puccd11", "puccd24", "hpsi30s", "q20"):
         if rank == 0:
             run_large(args)
         return

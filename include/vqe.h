@@ -85,8 +85,18 @@ int vqe_version(void);
  *                            all groups) instead of alpha/beta strings;
  *   VQE_FLAG_PERSISTENT_SWEEPS streaming gate sweeps of a single instance as
  *                            one persistent launch per sweep (a task queue)
- *                            instead of one launch per gate; the same bits, and
- *                            slower on the GPUs measured (kept for comparison).
+ *                            instead of one launch per gate; the same bits as
+ *                            one launch per gate without the kept forward
+ *                            outputs (below), and slower on the GPUs measured
+ *                            (kept for comparison);
+ *   VQE_FLAG_NO_PHI_STORE    real instances of 6,000,000 sector states or more
+ *                            normally keep the forward sweep's outputs of every
+ *                            amplitude pair in the workspace (16 bytes per pair)
+ *                            and run the reverse sweep on them and lambda alone;
+ *                            with this flag (or VQE_FLAG_PERSISTENT_SWEEPS) the
+ *                            reverse sweep un-applies each gate to psi instead.
+ *                            The gradients agree to rounding; psi, lambda and the
+ *                            energy are the same bits either way.
  * Returns the previous flags. Not thread-safe against concurrent compute calls.
  */
 enum {
@@ -95,7 +105,8 @@ enum {
   VQE_FLAG_NO_CLUSTER = 4,
   VQE_FLAG_FP64_SWEEPS = 8,
   VQE_FLAG_NO_STRINGS = 16,
-  VQE_FLAG_PERSISTENT_SWEEPS = 32
+  VQE_FLAG_PERSISTENT_SWEEPS = 32,
+  VQE_FLAG_NO_PHI_STORE = 64
 };
 int vqe_set_flags(int flags);
 
@@ -241,7 +252,11 @@ void vqe_destroy_ansatz(vqe_ansatz_t a);
  * It holds two state vectors (|psi> or |phi>, and |lambda>) compressed to the
  * ansatz's sector (entry r is the amplitude of the r-th sector state in
  * increasing order), their copies in alpha-major order (string-driven H psi),
- * and reduction partials. The workspace must be 256-byte aligned.
+ * and reduction partials; with VQE_WS_GRAD and real amplitudes, for sectors of
+ * 6,000,000 states or more, also the forward sweep's outputs of every
+ * (gate, amplitude pair) unit (16 bytes each: 4.5 GB at 30 qubits with 512
+ * angles), which the reverse sweep reads (see VQE_FLAG_NO_PHI_STORE). The
+ * workspace must be 256-byte aligned.
  * The first call for a (Hamiltonian, sector) pair builds that pair's
  * connectivity table (synchronous, allocates); call it before any stream
  * capture. Returns 0 and sets the error message on failure.
@@ -258,8 +273,10 @@ int vqe_energy(vqe_hamiltonian_t h, vqe_ansatz_t a, const double* theta_dev,
 
 /*
  * E(theta) and grad_dev[k] = dE/dtheta_k by one forward sweep, one H|psi>, and
- * one reverse (adjoint) sweep that un-applies each gate to both |phi> and
- * |lambda> = H|psi> while reducing g_k = 2 Re <lambda| T_k - T_k^dagger |phi>.
+ * one reverse (adjoint) sweep that un-applies each gate to |lambda> = H|psi>
+ * while reducing g_k = 2 Re <lambda| T_k - T_k^dagger |phi_k>, phi_k being the
+ * state after gate k: un-applied from the final psi, or, for large real
+ * sectors, read from the forward sweep's kept outputs (vqe_workspace_bytes).
  */
 int vqe_energy_grad(vqe_hamiltonian_t h, vqe_ansatz_t a, const double* theta_dev,
                     double* energy_dev, double* grad_dev, void* workspace,

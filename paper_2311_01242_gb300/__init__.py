@@ -6,7 +6,7 @@ from .api import (Hamiltonian, Ansatz, Batch, VQEError, energy, energy_grad, sta
                   apply_hamiltonian, apply_hamiltonian_sector, jordan_wigner, hcb_hamiltonian, fold_frozen, workspace_bytes, alloc_workspace,
                   work_estimate, work_counts, set_flags, VQE_WS_ENERGY, VQE_WS_GRAD, VQE_WS_COMPLEX,
                   VQE_FLAG_FORCE_COMPLEX, VQE_FLAG_FORCE_STREAMING, VQE_FLAG_NO_CLUSTER, VQE_FLAG_FP64_SWEEPS,
-                  VQE_FLAG_NO_STRINGS, VQE_FLAG_PERSISTENT_SWEEPS,
+                  VQE_FLAG_NO_STRINGS, VQE_FLAG_PERSISTENT_SWEEPS, VQE_FLAG_NO_PHI_STORE,
                   probe_fp64,
                   GraphEnergyGrad, batched_workspace_bytes, energy_grad_batched,
                   pool_workspace_bytes, pool_gradients)
@@ -16,7 +16,7 @@ __all__ = [
     "build", "load", "Hamiltonian", "Ansatz", "Batch", "VQEError", "energy", "energy_grad",
     "state", "apply_hamiltonian", "apply_hamiltonian_sector", "jordan_wigner", "hcb_hamiltonian", "fold_frozen", "workspace_bytes", "alloc_workspace",
     "work_estimate", "work_counts", "set_flags", "VQEEnergy", "vqe_energy", "VQE_WS_ENERGY", "VQE_WS_GRAD",
-    "VQE_WS_COMPLEX", "VQE_FLAG_FORCE_COMPLEX", "VQE_FLAG_FORCE_STREAMING", "VQE_FLAG_NO_CLUSTER", "VQE_FLAG_FP64_SWEEPS", "VQE_FLAG_NO_STRINGS", "VQE_FLAG_PERSISTENT_SWEEPS",
+    "VQE_WS_COMPLEX", "VQE_FLAG_FORCE_COMPLEX", "VQE_FLAG_FORCE_STREAMING", "VQE_FLAG_NO_CLUSTER", "VQE_FLAG_FP64_SWEEPS", "VQE_FLAG_NO_STRINGS", "VQE_FLAG_PERSISTENT_SWEEPS", "VQE_FLAG_NO_PHI_STORE",
     "probe_fp64",
     "GraphEnergyGrad", "batched_workspace_bytes", "energy_grad_batched",
     "pool_workspace_bytes", "pool_gradients",

@@ -18,7 +18,7 @@ LIB_PATH = os.path.join(_BUILD_DIR, "libvqe.so")
 HEADER = os.path.join(_ROOT, "include", "vqe.h")
 
 SOURCES = ["vqe_kernels.cu", "vqe_batch.cu", "vqe_host.cpp", "vqe_static.cu", "vqe_mlp.cu", "vqe_probe.cu",
-           "vqe_aux.cu", "vqe_pool.cu"]
+           "vqe_aux.cu", "vqe_pool.cu", "vqe_phi.cu"]
 DEPS = SOURCES + ["vqe_internal.h", "vqe_device.cuh"]
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 CFLAGS = ARCH + ["-lineinfo", "-O3", "-std=c++17", "-Xcompiler", "-fPIC"]

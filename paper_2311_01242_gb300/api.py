@@ -14,6 +14,7 @@ VQE_WS_ENERGY, VQE_WS_GRAD, VQE_WS_COMPLEX = 0, 1, 2
 VQE_FLAG_FORCE_COMPLEX, VQE_FLAG_FORCE_STREAMING, VQE_FLAG_NO_CLUSTER, VQE_FLAG_FP64_SWEEPS = 1, 2, 4, 8
 VQE_FLAG_NO_STRINGS = 16
 VQE_FLAG_PERSISTENT_SWEEPS = 32
+VQE_FLAG_NO_PHI_STORE = 64
 
 
 class VQEError(RuntimeError):

@@ -981,8 +981,13 @@ bool resident_fit(vqe_ansatz_t a, const vqe_hamiltonian_s::Ell* e, bool real, In
 }
 
 struct WsLayout {
-  size_t psi, lam, psi_am, lam_am, cs, epart, ctr, gpart, total;
+  size_t psi, lam, psi_am, lam_am, cs, epart, ctr, gpart, phi, total;
 };
+
+// Real sectors from this size keep the forward sweep's pair outputs for the
+// reverse sweep: psi and lambda (16 bytes per state together) no longer share
+// the L2, and the reverse step's gathers of both would miss it.
+constexpr size_t kKeepPhiMinStates = 6000000;
 
 WsLayout ws_layout(vqe_ansatz_t a, bool complex_amp, bool with_grad) {
   WsLayout L;
@@ -996,7 +1001,10 @@ WsLayout ws_layout(vqe_ansatz_t a, bool complex_amp, bool with_grad) {
   L.epart = L.cs + align256(size_t(std::max(a->M, 1)) * 16);
   L.ctr = L.epart + align256(size_t(vqe::kMaxPartials) * 8);  // task counters of the persistent sweeps
   L.gpart = L.ctr + 256;
-  L.total = L.gpart + (with_grad ? align256(size_t(std::max(a->M, 1)) * vqe::kMaxPartials * 8) : 0);
+  L.phi = L.gpart + (with_grad ? align256(size_t(std::max(a->M, 1)) * vqe::kMaxPartials * 8) : 0);
+  const bool keep = !complex_amp && with_grad && a->sector.size() >= kKeepPhiMinStates;
+  L.total = L.phi + (keep ? align256(size_t(a->pair_off.empty() ? 0 : a->pair_off.back()) * 16) : 0);
+  if (!keep) L.phi = 0;
   return L;
 }
 
@@ -1010,6 +1018,7 @@ vqe::StreamBuffers buffers(void* ws, const WsLayout& L) {
   s.cs = reinterpret_cast<double2*>(b + L.cs);
   s.epart = reinterpret_cast<double*>(b + L.epart);
   s.gpart = reinterpret_cast<double*>(b + L.gpart);
+  s.phi = L.phi ? reinterpret_cast<double2*>(b + L.phi) : nullptr;
   return s;
 }
 
@@ -1143,6 +1152,16 @@ int ctas_per_instance(bool real, int n_inst) {
   return 2 * n_inst <= sms ? 2 : 1;
 }
 
+// One streamed instance: with its forward outputs kept when the workspace layout
+// has room for them (large real sectors) and no flag asks for the un-applying
+// reverse sweep, else the plain streaming path.
+cudaError_t stream_eval(const InstDesc& d, const vqe::StreamPlan& sp, const vqe::StreamBuffers& b, bool real,
+                        bool with_grad, const double* theta, double* energy, double* grad, cudaStream_t stream) {
+  if (real && with_grad && b.phi && !sp.sweep && !(g_flags & VQE_FLAG_NO_PHI_STORE))
+    return vqe::stream_energy_grad_kept(d, sp, b, theta, energy, grad, stream);
+  return vqe::stream_energy_grad(d, sp, b, real, with_grad, theta, energy, grad, stream);
+}
+
 int run_single(vqe_hamiltonian_t h, vqe_ansatz_t a, const double* theta, double* energy, double* grad,
                void* ws, size_t ws_bytes, cudaStream_t stream, bool with_grad) {
   int rc = check_pair(h, a);
@@ -1163,8 +1182,7 @@ int run_single(vqe_hamiltonian_t h, vqe_ansatz_t a, const double* theta, double*
   }
   const WsLayout L = ws_layout(a, !real, with_grad);
   if ((rc = check_ws(ws, ws_bytes, L.total))) return rc;
-  cudaError_t ce = vqe::stream_energy_grad(d, plan(a, e), buffers(ws, L), real, with_grad, theta, energy,
-                                           grad, stream);
+  cudaError_t ce = stream_eval(d, plan(a, e), buffers(ws, L), real, with_grad, theta, energy, grad, stream);
   if (ce != cudaSuccess) return cuda_fail(ce, "streaming launch");
   return VQE_OK;
 }
@@ -2365,9 +2383,9 @@ static int run_one_by_one(vqe_batch_t b, const std::vector<int>& which, bool rea
     if (!e) return rc2;
     const WsLayout L = ws_layout(a, !real, with_grad);
     if ((rc2 = check_ws(ws, ws_bytes, L.total))) return rc2;
-    cudaError_t ce = vqe::stream_energy_grad(b->descs[i], plan(a, e), buffers(ws, L), real, with_grad,
-                                             theta + int64_t(i) * ld_theta, energies + i,
-                                             with_grad ? grads + int64_t(i) * ld_grad : nullptr, stream);
+    cudaError_t ce = stream_eval(b->descs[i], plan(a, e), buffers(ws, L), real, with_grad,
+                                 theta + int64_t(i) * ld_theta, energies + i,
+                                 with_grad ? grads + int64_t(i) * ld_grad : nullptr, stream);
     if (ce != cudaSuccess) return cuda_fail(ce, "batched streaming launch");
   }
   return VQE_OK;

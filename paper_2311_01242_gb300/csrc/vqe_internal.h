@@ -262,6 +262,9 @@ struct StreamBuffers {
   void* lam = nullptr;     // D amplitudes
   void* psi_am = nullptr;  // D amplitudes, alpha-major (string-driven H psi)
   void* lam_am = nullptr;  // D amplitudes, alpha-major
+  // large real instances: the forward sweep's outputs {phi(k), phi(k ^ flip)} of
+  // every pair, in pair order (null: the reverse sweep un-applies the gates to psi)
+  double2* phi = nullptr;
   double2* cs;    // [M] (cos, sin)
   double* epart;  // [kMaxPartials]
   double* gpart;  // [M * kMaxPartials]
@@ -296,6 +299,10 @@ cudaError_t stream_apply_h(const InstDesc& d, const StreamPlan& sp, const Stream
                            const double* psi_in, double* lam_out, double* energy,
                            cudaStream_t stream);
 // lambda = H psi with real amplitudes compressed to the sector (b.psi in, b.lam out).
+// Real amplitudes, b.phi set: energy and gradient with the forward outputs kept
+// (vqe_phi.cu); psi, lambda and the energy are those of stream_energy_grad.
+cudaError_t stream_energy_grad_kept(const InstDesc& d, const StreamPlan& sp, const StreamBuffers& b,
+                                    const double* theta, double* energy, double* grad, cudaStream_t stream);
 cudaError_t stream_apply_h_real(const InstDesc& d, const StreamPlan& sp, const StreamBuffers& b, double* energy,
                                 cudaStream_t stream);
 

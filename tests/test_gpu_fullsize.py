@@ -4,7 +4,8 @@
 Hartree-Fock energy, whose closed form comes from the integrals; at a random
 theta, sampled gradient components equal the four-point shift rule evaluated
 with the library's own energies (exact for rotations generated by T - T^dagger,
-whose spectrum is {0, +-i}); one H psi pass on a random sector vector equals
+whose spectrum is {0, +-i}), and the gradient from the kept forward outputs
+equals the one from un-applying the gates to rounding; one H psi pass on a random sector vector equals
 the oracle's explicit Pauli action at sampled rows; psi(theta) after 512 gates
 has unit norm and no weight outside the sector. 256 uneven instances (14-20 qubits): the batched
 launch agrees with single-instance calls on sampled instances, and with the
@@ -55,13 +56,23 @@ def test_30_qubits_hf_energy_and_shift_rule_gradient():
     assert abs(e0 - _slater_condon(p)) <= 1e-10 + dropped
     e, g = vq.energy_grad(H, A, th, workspace=ws)
     g = g.cpu().numpy()
-    # persistent sweeps instead of one launch per gate: the same bits
+    # the reverse sweep un-applying each gate to psi instead of reading the kept
+    # forward outputs: the same energy bits, the gradient to rounding
+    old = vq.set_flags(vq.VQE_FLAG_NO_PHI_STORE)
+    try:
+        e1, g1 = vq.energy_grad(H, A, th, workspace=ws)
+    finally:
+        vq.set_flags(old)
+    g1 = g1.cpu().numpy()
+    assert float(e1) == float(e)
+    assert np.abs(g1 - g).max() <= 1e-11
+    # persistent sweeps instead of one launch per gate: the same bits as the un-applying path
     old = vq.set_flags(vq.VQE_FLAG_PERSISTENT_SWEEPS)
     try:
         e2, g2 = vq.energy_grad(H, A, th, workspace=ws)
     finally:
         vq.set_flags(old)
-    assert float(e2) == float(e) and np.array_equal(g2.cpu().numpy(), g)
+    assert float(e2) == float(e) and np.array_equal(g2.cpu().numpy(), g1)
     w_ = (np.sqrt(2.0) - 1.0) / 2.0
     for k in (0, 255, 511):
         def e_at(shift):
